@@ -1,0 +1,159 @@
+/*
+ * gbgemm -- single-precision GEMM for one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The operation (Section III-A of Tasende, "Generation of the Single
+ * Precision BLAS library for the Parallella platform ...", 2016, the problem
+ * the BLIS-generated sgemm solves):
+ *
+ *     C_out = alpha * op(A) * op(B) + beta * C_in
+ *
+ * with A, B, C in column-major storage with leading dimensions, op(X) = X or
+ * X^T, and M, N, K arbitrary.  Element by element, for 0 <= i < m, 0 <= j < n:
+ *
+ *     C[i + j*ldc] = alpha * sum_{p<k} opA(i,p) * opB(p,j) + beta * C[i + j*ldc]
+ *     opA(i,p) = A[i + p*lda] (transa = 'N'/'n')  or  A[p + i*lda] ('T','t','C','c')
+ *     opB(p,j) = B[p + j*ldb] (transb = 'N'/'n')  or  B[j + p*ldb] ('T','t','C','c')
+ *
+ * For real data the conjugate letters equal their plain ones: 'C' (conjugate
+ * transpose, BLAS argument letter) behaves as 'T'.  Argument order and
+ * conventions follow reference BLAS sgemm: beta == 0 never reads C (NaN in C
+ * does not propagate); alpha == 0 or k == 0 never reads A or B; m == 0 or
+ * n == 0, or (alpha == 0 or k == 0) with beta == 1, returns without work.
+ * Entries of C outside rows 0..m-1 of each column are never written.
+ *
+ * Two paths compute the same result within the componentwise bound
+ *     |C - C_exact|_ij <= 2 * max(k,1) * 2^-24 * (|alpha| sum_p |opA(i,p)||opB(p,j)| + |beta| |C_in,ij|)
+ *   GBGEMM_PATH_SIMT        plain FP32 fused multiply-add on the CUDA cores.
+ *   GBGEMM_PATH_SPLIT_BF16  each operand row (of op(A)) and column (of op(B))
+ *                           is scaled by a power of two so its largest entry
+ *                           lies in [0.5, 1), every entry x becomes
+ *                           hi + lo (two BF16 values, hi = bf16(x),
+ *                           lo = bf16(x - hi)), and the tensor cores
+ *                           accumulate hi*hi + hi*lo + lo*hi in FP32.  The
+ *                           bound is guaranteed for k >= 128; below that
+ *                           GBGEMM_PATH_AUTO uses the SIMT path.
+ *   GBGEMM_PATH_AUTO        SPLIT_BF16 when k >= 128, else SIMT.
+ *
+ * Memory and streams.  All matrix pointers are DEVICE pointers owned by the
+ * caller, who keeps them alive until the work queued on the handle's stream
+ * has completed.  Calls are asynchronous on that stream: no call in this
+ * header synchronises the host except where stated.  The handle owns a
+ * device workspace (split panels and row maxima) that grows on demand with
+ * cudaMalloc; gbgemm_reserve_workspace() pre-sizes it so that later calls do
+ * not allocate.
+ *
+ * Errors.  Every call returns GBGEMM_OK (0) or a negative status.  Argument
+ * errors of gbgemm_sgemm return minus the 1-based position of the argument
+ * in the BLAS argument list (transa = 1 ... ldc = 13), checked in that order
+ * (see gbgemm_sgemm).  No call aborts the process.  Device-side failures (a
+ * bounded wait that ran out) are recorded in a device status word read by
+ * gbgemm_get_device_status().
+ */
+#ifndef GBGEMM_H
+#define GBGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GBGEMM_OK = 0,
+  GBGEMM_ERR_NOT_INITIALIZED = -100,  /* null handle or plan */
+  GBGEMM_ERR_ALLOC = -101,            /* device or host allocation failed */
+  GBGEMM_ERR_CUDA = -102,             /* a CUDA runtime call failed */
+  GBGEMM_ERR_UNSUPPORTED_DEVICE = -103, /* split path requested on a device that is not sm_103 */
+  GBGEMM_ERR_DEVICE_TIMEOUT = -104,   /* a kernel's bounded wait ran out (see gbgemm_get_device_status) */
+  GBGEMM_ERR_BAD_PLAN = -105,         /* plan inputs invalid (bad problem index in *bad_index) */
+  GBGEMM_ERR_INVALID_VALUE = -106     /* other invalid argument (path code, size, pointer) */
+} gbgemm_status;
+
+typedef enum {
+  GBGEMM_PATH_AUTO = 0,
+  GBGEMM_PATH_SIMT = 1,
+  GBGEMM_PATH_SPLIT_BF16 = 2
+} gbgemm_path;
+
+typedef struct gbgemm_handle gbgemm_handle;
+
+/* Create a handle bound to CUDA device `device` (made current for the call).
+ * The handle starts on the legacy default stream (NULL) with path AUTO.
+ * Errors: GBGEMM_ERR_INVALID_VALUE (h NULL), GBGEMM_ERR_CUDA (bad device),
+ * GBGEMM_ERR_ALLOC. */
+int gbgemm_create(gbgemm_handle** h, int device);
+
+/* Destroy a handle and free its workspace.  Synchronises the handle's stream
+ * first.  A NULL handle returns GBGEMM_ERR_NOT_INITIALIZED. */
+int gbgemm_destroy(gbgemm_handle* h);
+
+/* Set the cudaStream_t (passed as void*) that later calls queue work on. */
+int gbgemm_set_stream(gbgemm_handle* h, void* cuda_stream);
+
+/* Force a path (gbgemm_path).  SPLIT_BF16 forced with k < 128 still runs but
+ * the error bound is then not guaranteed.  Bad code: GBGEMM_ERR_INVALID_VALUE. */
+int gbgemm_set_path(gbgemm_handle* h, int path);
+
+/* Path taken by the handle's most recent gbgemm_sgemm (0 when it returned
+ * early without launching the product kernels). */
+int gbgemm_last_path(gbgemm_handle* h, int* path);
+
+/* Grow the workspace to at least `bytes` now (cudaMalloc; synchronous). */
+int gbgemm_reserve_workspace(gbgemm_handle* h, size_t bytes);
+
+/* Workspace bytes the split path needs for (m, n, k). */
+size_t gbgemm_split_workspace_bytes(int64_t m, int64_t n, int64_t k);
+
+/* BLAS-convention sgemm (Section III-A problem statement).
+ * transa, transb: 'N','n','T','t','C','c'.  m, n, k >= 0.
+ * A: device, stored (transa N ? m x k : k x m) with lda >= max(1, rows).
+ * B: device, stored (transb N ? k x n : n x k) with ldb >= max(1, rows).
+ * C: device, m x n with ldc >= max(1, m); read only when beta != 0.
+ * Argument errors, in this order: transa -1, transb -2, m -3, n -4, k -5,
+ * lda -8, ldb -10, ldc -13; then null A (when read) -7, null B -9,
+ * null C (m*n > 0) -12.  Then GBGEMM_ERR_NOT_INITIALIZED for a NULL handle.
+ * Queues kernels on the handle's stream and returns without waiting. */
+int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                 float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                 float beta, float* C, int64_t ldc);
+
+/* Synchronise the handle's stream, then read and clear the device status
+ * word: *status = 0 when no kernel reported a failure since the last read,
+ * else the first failing kernel's code (GBGEMM_ERR_DEVICE_TIMEOUT).  Returns
+ * GBGEMM_ERR_CUDA if the stream reported a CUDA error. */
+int gbgemm_get_device_status(gbgemm_handle* h, int* status);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* gbgemm_status_string(int status);
+
+/* ---------------------------------------------------------------------- */
+/* Split-panel inspection (tests): runs the split path's scaling and packing
+ * kernels alone on one operand.
+ *
+ * which = 'A': the K-vectors are the m rows of op(A) (rows = m, trans = transa,
+ *              X = A, ldx = lda).
+ * which = 'B': the K-vectors are the n columns of op(B) (rows = n, trans =
+ *              transb, X = B, ldx = ldb).
+ * Outputs (device, caller-owned):
+ *   amax_bits[r] = bit pattern of max_p |x(r,p)| (NaN/Inf patterns kept), rows entries.
+ *   panel: BF16 hi/lo panel of gbgemm_panel_bytes(rows, k) bytes.  It is a
+ *   sequence of 16 KiB blocks, block (kc, rb) at byte offset
+ *   (kc * RB + rb) * 16384 with RB = ceil(rows/256)*2 and kc = p / 32.  A
+ *   block holds rows 128*rb .. 128*rb+127 and k indices 32*kc .. 32*kc+31.
+ *   Row r of the block occupies bytes r*128 .. r*128+127 as eight 16-byte
+ *   chunks; logical chunk c is stored at chunk position c XOR (r mod 8).
+ *   Chunks 0-3 hold hi of k offsets 0-31 (8 per chunk, ascending), chunks
+ *   4-7 hold lo of the same offsets.  Rows >= rows and k >= k are zero.
+ * hi/lo of x are those of x * 2^-e with e the frexp exponent of the row's
+ * max |x| (e = 0 when that max is 0 or not finite).
+ * Asynchronous on the handle's stream. */
+size_t gbgemm_panel_bytes(int64_t rows, int64_t k);
+int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,
+                      const float* X, int64_t ldx, uint32_t* amax_bits, void* panel);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBGEMM_H */

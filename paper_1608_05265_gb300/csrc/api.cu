@@ -1,0 +1,255 @@
+// C-ABI front end: argument checks in BLAS order, quick returns, path choice,
+// workspace management and kernel dispatch (the BLIS driver layer of
+// Section III-A, which hands fixed-shape pieces of the problem to the
+// micro-kernel).  One handle holds the per-device state the paper keeps in
+// its long-lived service process (Section III-B): device properties, the
+// stream and a persistent workspace, set up once instead of on every call.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+struct gbgemm_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int path = GBGEMM_PATH_AUTO;
+  int last_path = 0;
+  int num_sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* d_status = nullptr;
+};
+
+namespace {
+
+int trans_code(char t) {
+  switch (t) {
+    case 'N': case 'n': return 0;
+    case 'T': case 't': case 'C': case 'c': return 1;
+    default: return -1;
+  }
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ensure_workspace(gbgemm_handle* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return GBGEMM_OK;
+  // The old buffer may still be in use by queued work on the stream.
+  if (h->ws) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GBGEMM_ERR_ALLOC;
+  }
+  h->ws = p;
+  h->ws_bytes = bytes;
+  return GBGEMM_OK;
+}
+
+bool split_supported(const gbgemm_handle* h) { return h->cc_major == 10 && h->cc_minor == 3; }
+
+}  // namespace
+
+extern "C" {
+
+size_t gbgemm_panel_bytes(int64_t rows, int64_t k) {
+  if (rows <= 0 || k <= 0) return 0;
+  return gbg::panel_bytes(rows, k);
+}
+
+size_t gbgemm_split_workspace_bytes(int64_t m, int64_t n, int64_t k) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  return align_up(gbg::panel_bytes(m, k), 256) + align_up(gbg::panel_bytes(n, k), 256) +
+         align_up((size_t)m * 4, 256) + align_up((size_t)n * 4, 256);
+}
+
+int gbgemm_create(gbgemm_handle** out, int device) {
+  if (!out) return GBGEMM_ERR_INVALID_VALUE;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return GBGEMM_ERR_CUDA;
+  }
+  gbgemm_handle* h = new (std::nothrow) gbgemm_handle();
+  if (!h) return GBGEMM_ERR_ALLOC;
+  h->device = device;
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete h;
+    return GBGEMM_ERR_CUDA;
+  }
+  h->num_sms = prop.multiProcessorCount;
+  h->cc_major = prop.major;
+  h->cc_minor = prop.minor;
+  if (cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return GBGEMM_ERR_ALLOC;
+  }
+  *out = h;
+  return GBGEMM_OK;
+}
+
+int gbgemm_destroy(gbgemm_handle* h) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  DeviceGuard g(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return GBGEMM_OK;
+}
+
+int gbgemm_set_stream(gbgemm_handle* h, void* s) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  h->stream = static_cast<cudaStream_t>(s);
+  return GBGEMM_OK;
+}
+
+int gbgemm_set_path(gbgemm_handle* h, int path) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (path != GBGEMM_PATH_AUTO && path != GBGEMM_PATH_SIMT && path != GBGEMM_PATH_SPLIT_BF16)
+    return GBGEMM_ERR_INVALID_VALUE;
+  if (path == GBGEMM_PATH_SPLIT_BF16 && !split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
+  h->path = path;
+  return GBGEMM_OK;
+}
+
+int gbgemm_last_path(gbgemm_handle* h, int* path) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!path) return GBGEMM_ERR_INVALID_VALUE;
+  *path = h->last_path;
+  return GBGEMM_OK;
+}
+
+int gbgemm_reserve_workspace(gbgemm_handle* h, size_t bytes) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  DeviceGuard g(h->device);
+  return ensure_workspace(h, bytes);
+}
+
+int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                 float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                 float beta, float* C, int64_t ldc) {
+  const int ta = trans_code(transa), tb = trans_code(transb);
+  if (ta < 0) return -1;
+  if (tb < 0) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  const int64_t arows = ta ? k : m, brows = tb ? n : k;
+  if (lda < (arows > 1 ? arows : 1)) return -8;
+  if (ldb < (brows > 1 ? brows : 1)) return -10;
+  if (ldc < (m > 1 ? m : 1)) return -13;
+  const bool use_ab = (alpha != 0.0f) && (k > 0);
+  if (m > 0 && n > 0) {
+    if (use_ab && !A) return -7;
+    if (use_ab && !B) return -9;
+    if (!C) return -12;
+  }
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  h->last_path = 0;
+  if (m == 0 || n == 0) return GBGEMM_OK;
+  if (!use_ab && beta == 1.0f) return GBGEMM_OK;
+  DeviceGuard g(h->device);
+  if (!use_ab) {
+    return gbg::launch_scale_c(m, n, beta, C, ldc, h->stream) == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
+  }
+  int path = h->path;
+  if (path == GBGEMM_PATH_AUTO) path = (k >= gbg::kSplitMinK && split_supported(h)) ? GBGEMM_PATH_SPLIT_BF16 : GBGEMM_PATH_SIMT;
+  gbg::Problem p{ta, tb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
+  if (path == GBGEMM_PATH_SIMT) {
+    const int cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
+    if (gbg::launch_simt(p, cfg, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    h->last_path = GBGEMM_PATH_SIMT;
+    return GBGEMM_OK;
+  }
+  if (!split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
+  const size_t pa = align_up(gbg::panel_bytes(m, k), 256), pb = align_up(gbg::panel_bytes(n, k), 256);
+  const size_t xa = align_up((size_t)m * 4, 256);
+  int rc = ensure_workspace(h, gbgemm_split_workspace_bytes(m, n, k));
+  if (rc != GBGEMM_OK) return rc;
+  uint8_t* ws = static_cast<uint8_t*>(h->ws);
+  void* panelA = ws;
+  void* panelB = ws + pa;
+  uint32_t* amaxA = reinterpret_cast<uint32_t*>(ws + pa + pb);
+  uint32_t* amaxB = reinterpret_cast<uint32_t*>(ws + pa + pb + xa);
+  // Rows of op(A): element (i, p) at A[p + i*lda] when transposed (k contiguous).
+  if (gbg::launch_split_pack(m, k, A, lda, ta == 1, amaxA, panelA, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  // Columns of op(B): element (j, p) at B[p + j*ldb] when not transposed (k contiguous).
+  if (gbg::launch_split_pack(n, k, B, ldb, tb == 0, amaxB, panelB, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  gbg::SplitGemmArgs a;
+  a.panelA = panelA; a.panelB = panelB; a.amaxA = amaxA; a.amaxB = amaxB;
+  a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
+  a.status = h->d_status; a.num_sms = h->num_sms;
+  a.bn = 256; a.raster = 16;
+  if (gbg::launch_split_gemm(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  h->last_path = GBGEMM_PATH_SPLIT_BF16;
+  return GBGEMM_OK;
+}
+
+int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,
+                      const float* X, int64_t ldx, uint32_t* amax_bits, void* panel) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  const int t = trans_code(trans);
+  if (t < 0 || (which != 'A' && which != 'B') || rows < 0 || k < 0) return GBGEMM_ERR_INVALID_VALUE;
+  if (rows == 0 || k == 0) return GBGEMM_OK;
+  if (!X || !amax_bits || !panel) return GBGEMM_ERR_INVALID_VALUE;
+  // Stored rows of X: op(A) rows come from A (m x k or k x m); op(B) columns from B.
+  const bool kcontig = (which == 'A') ? (t == 1) : (t == 0);
+  const int64_t stored_rows = kcontig ? k : rows;
+  if (ldx < (stored_rows > 1 ? stored_rows : 1)) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard g(h->device);
+  return gbg::launch_split_pack(rows, k, X, ldx, kcontig, amax_bits, panel, h->stream) == cudaSuccess ? GBGEMM_OK
+                                                                                                      : GBGEMM_ERR_CUDA;
+}
+
+int gbgemm_get_device_status(gbgemm_handle* h, int* status) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!status) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard g(h->device);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (v != 0 && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  *status = v;
+  return GBGEMM_OK;
+}
+
+const char* gbgemm_status_string(int s) {
+  if (s > -100 && s < 0) return "GBGEMM_ERR_ARGUMENT (minus the 1-based position of the bad argument)";
+  switch (s) {
+    case GBGEMM_OK: return "GBGEMM_OK";
+    case GBGEMM_ERR_NOT_INITIALIZED: return "GBGEMM_ERR_NOT_INITIALIZED";
+    case GBGEMM_ERR_ALLOC: return "GBGEMM_ERR_ALLOC";
+    case GBGEMM_ERR_CUDA: return "GBGEMM_ERR_CUDA";
+    case GBGEMM_ERR_UNSUPPORTED_DEVICE: return "GBGEMM_ERR_UNSUPPORTED_DEVICE";
+    case GBGEMM_ERR_DEVICE_TIMEOUT: return "GBGEMM_ERR_DEVICE_TIMEOUT";
+    case GBGEMM_ERR_BAD_PLAN: return "GBGEMM_ERR_BAD_PLAN";
+    case GBGEMM_ERR_INVALID_VALUE: return "GBGEMM_ERR_INVALID_VALUE";
+    default: return "GBGEMM_UNKNOWN_STATUS";
+  }
+}
+
+}  // extern "C"

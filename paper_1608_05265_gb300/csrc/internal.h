@@ -1,0 +1,59 @@
+// Internal declarations shared by the gbgemm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gbgemm.h"
+
+namespace gbg {
+
+// Problem after argument checks; op letters reduced to 0 (N) / 1 (T).
+struct Problem {
+  int ta, tb;
+  int64_t m, n, k;
+  float alpha, beta;
+  const float* A; int64_t lda;
+  const float* B; int64_t ldb;
+  float* C; int64_t ldc;
+};
+
+// ---- SIMT path (simt.cu) ----
+// Tile configurations of the SIMT kernel, indexed by the autotuner.
+enum SimtConfig { SIMT_128x128 = 0, SIMT_64x64 = 1, SIMT_128x64 = 2, SIMT_NUM_CONFIGS = 3 };
+cudaError_t launch_simt(const Problem& p, int config, cudaStream_t s);
+// C := beta * C over m x n (beta == 0 writes zeros without reading C).
+cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t s);
+
+// ---- split path (split.cu) ----
+constexpr int kPanelRows = 128;     // rows per panel block
+constexpr int kPanelK = 32;         // k per panel block (hi and lo: 64 BF16 = 128 bytes per row)
+constexpr int kBlockBytes = kPanelRows * 128;  // 16 KiB
+constexpr int kSplitMinK = 128;     // AUTO uses the split path from this k upwards
+
+inline int64_t panel_row_blocks(int64_t rows) { return (rows + 255) / 256 * 2; }
+inline int64_t panel_k_chunks(int64_t k) { return (k + kPanelK - 1) / kPanelK; }
+inline size_t panel_bytes(int64_t rows, int64_t k) {
+  return (size_t)panel_row_blocks(rows) * (size_t)panel_k_chunks(k) * (size_t)kBlockBytes;
+}
+
+// Split one operand: amax pass then pack pass.  `kcontig` selects the view:
+// element (r, p) = X[r*ld + p] (kcontig) or X[r + p*ld] (!kcontig).
+// amax_bits must hold `rows` words; it is zeroed here.
+cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
+                              uint32_t* amax_bits, void* panel, cudaStream_t s);
+
+struct SplitGemmArgs {
+  const void* panelA; const void* panelB;
+  const uint32_t* amaxA; const uint32_t* amaxB;
+  int64_t m, n, k;
+  float alpha, beta;
+  float* C; int64_t ldc;
+  int* status;
+  int num_sms;
+  int bn;          // 256 or 128
+  int raster;      // tile-row group size of the tile order
+};
+cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s);
+
+}  // namespace gbg

@@ -1,0 +1,173 @@
+"""Thin ctypes binding over libgbgemm.so (argument marshalling only).
+
+Every function has the name and argument order of its C counterpart in
+``include/gbgemm.h``; torch tensors are passed by ``data_ptr()`` and the
+stream as ``torch.cuda.Stream.cuda_stream``.  Matrices are column-major: a
+column-major m x n matrix with leading dimension ld is a torch tensor whose
+storage holds n columns of ld floats (for example ``t.T`` of a row-major
+(n, ld) tensor).  There is no fallback: if the library is missing or cannot
+be loaded, ``lib()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbgemm.so")
+
+OK = 0
+ERR_NOT_INITIALIZED = -100
+ERR_ALLOC = -101
+ERR_CUDA = -102
+ERR_UNSUPPORTED_DEVICE = -103
+ERR_DEVICE_TIMEOUT = -104
+ERR_BAD_PLAN = -105
+ERR_INVALID_VALUE = -106
+
+PATH_AUTO = 0
+PATH_SIMT = 1
+PATH_SPLIT_BF16 = 2
+
+#: Symbols exported by libgbgemm.so, as declared in include/gbgemm.h.
+EXPORTS = [
+    "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
+    "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_get_device_status",
+    "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GbgemmError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} returned {status} ({status_string(status)})")
+        self.status = status
+
+
+def lib():
+    """Load libgbgemm.so (built by paper_1608_05265_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_1608_05265_gb300.build.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, f32, c = ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_char
+            L.gbgemm_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+            L.gbgemm_destroy.argtypes = [vp]
+            L.gbgemm_set_stream.argtypes = [vp, vp]
+            L.gbgemm_set_path.argtypes = [vp, ctypes.c_int]
+            L.gbgemm_last_path.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            L.gbgemm_reserve_workspace.argtypes = [vp, ctypes.c_size_t]
+            L.gbgemm_split_workspace_bytes.argtypes = [i64, i64, i64]
+            L.gbgemm_split_workspace_bytes.restype = ctypes.c_size_t
+            L.gbgemm_sgemm.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64]
+            L.gbgemm_get_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            L.gbgemm_status_string.argtypes = [ctypes.c_int]
+            L.gbgemm_status_string.restype = ctypes.c_char_p
+            L.gbgemm_panel_bytes.argtypes = [i64, i64]
+            L.gbgemm_panel_bytes.restype = ctypes.c_size_t
+            L.gbgemm_split_pack.argtypes = [vp, c, c, i64, i64, vp, i64, vp, vp]
+            for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
+                         "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
+                         "gbgemm_get_device_status", "gbgemm_split_pack"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().gbgemm_status_string(int(s)).decode()
+    except Exception:  # library not loadable: plain number
+        return str(s)
+
+
+def _check(fn: str, rc: int) -> int:
+    if rc != OK:
+        raise GbgemmError(fn, rc)
+    return rc
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+class Handle:
+    """Owns a gbgemm_handle; every method forwards to the C function of the same name."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check("gbgemm_create", lib().gbgemm_create(ctypes.byref(h), int(device)))
+        self._h = h
+        self.device = device
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().gbgemm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        _check("gbgemm_set_stream", lib().gbgemm_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_path(self, path: int):
+        _check("gbgemm_set_path", lib().gbgemm_set_path(self._h, int(path)))
+
+    def last_path(self) -> int:
+        v = ctypes.c_int()
+        _check("gbgemm_last_path", lib().gbgemm_last_path(self._h, ctypes.byref(v)))
+        return v.value
+
+    def reserve_workspace(self, nbytes: int):
+        _check("gbgemm_reserve_workspace", lib().gbgemm_reserve_workspace(self._h, int(nbytes)))
+
+    def sgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, check=True) -> int:
+        rc = lib().gbgemm_sgemm(self._h, transa.encode() if isinstance(transa, str) else transa,
+                                transb.encode() if isinstance(transb, str) else transb,
+                                int(m), int(n), int(k), float(alpha), _ptr(A), int(lda), _ptr(B), int(ldb),
+                                float(beta), _ptr(C), int(ldc))
+        if check:
+            _check("gbgemm_sgemm", rc)
+        return rc
+
+    def get_device_status(self) -> int:
+        v = ctypes.c_int()
+        _check("gbgemm_get_device_status", lib().gbgemm_get_device_status(self._h, ctypes.byref(v)))
+        return v.value
+
+    def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
+        return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),
+                                       _ptr(amax_bits), _ptr(panel))
+
+
+def split_workspace_bytes(m, n, k) -> int:
+    return int(lib().gbgemm_split_workspace_bytes(int(m), int(n), int(k)))
+
+
+def panel_bytes(rows, k) -> int:
+    return int(lib().gbgemm_panel_bytes(int(rows), int(k)))

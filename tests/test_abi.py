@@ -1,0 +1,85 @@
+"""The C-ABI library: builds, loads, exports every declared symbol, and
+rejects bad arguments in BLAS order without touching a GPU."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1608_05265_gb300 import build, gbgemm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return gbgemm.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "gbgemm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbgemm_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(gbgemm.EXPORTS) == names
+
+
+def test_argument_errors_in_blas_order(L):
+    a = ctypes.c_void_p(16)  # never dereferenced: argument checks run first
+    sg = L.gbgemm_sgemm
+    assert sg(None, b"X", b"N", 1, 1, 1, 1.0, a, 1, a, 1, 0.0, a, 1) == -1
+    assert sg(None, b"N", b"q", 1, 1, 1, 1.0, a, 1, a, 1, 0.0, a, 1) == -2
+    assert sg(None, b"N", b"N", -1, 1, 1, 1.0, a, 1, a, 1, 0.0, a, 1) == -3
+    assert sg(None, b"N", b"N", 1, -1, 1, 1.0, a, 1, a, 1, 0.0, a, 1) == -4
+    assert sg(None, b"N", b"N", 1, 1, -1, 1.0, a, 1, a, 1, 0.0, a, 1) == -5
+    assert sg(None, b"N", b"N", 5, 1, 3, 1.0, a, 4, a, 3, 0.0, a, 5) == -8
+    assert sg(None, b"T", b"N", 5, 1, 3, 1.0, a, 2, a, 3, 0.0, a, 5) == -8
+    assert sg(None, b"N", b"N", 5, 2, 3, 1.0, a, 5, a, 2, 0.0, a, 5) == -10
+    assert sg(None, b"N", b"T", 5, 2, 3, 1.0, a, 5, a, 1, 0.0, a, 5) == -10
+    assert sg(None, b"N", b"N", 5, 2, 3, 1.0, a, 5, a, 3, 0.0, a, 4) == -13
+    assert sg(None, b"N", b"N", 5, 2, 3, 1.0, None, 5, a, 3, 0.0, a, 5) == -7
+    assert sg(None, b"N", b"N", 5, 2, 3, 1.0, a, 5, None, 3, 0.0, a, 5) == -9
+    assert sg(None, b"N", b"N", 5, 2, 3, 1.0, a, 5, a, 3, 0.0, None, 5) == -12
+    # ld of 0 is invalid even for empty matrices (BLAS requires ld >= 1)
+    assert sg(None, b"N", b"N", 0, 0, 0, 1.0, a, 0, a, 1, 0.0, a, 1) == -8
+    # alpha == 0: A and B may be null; then the handle is checked
+    assert sg(None, b"N", b"N", 5, 2, 3, 0.0, None, 5, None, 3, 2.0, a, 5) == gbgemm.ERR_NOT_INITIALIZED
+    # every letter of the transpose alphabet is accepted
+    for ta in b"NnTtCc":
+        assert sg(None, bytes([ta]), b"n", 1, 1, 1, 1.0, a, 1, a, 1, 0.0, a, 1) == gbgemm.ERR_NOT_INITIALIZED
+
+
+def test_null_handle_and_status_strings(L):
+    assert L.gbgemm_destroy(None) == gbgemm.ERR_NOT_INITIALIZED
+    assert L.gbgemm_set_path(None, 0) == gbgemm.ERR_NOT_INITIALIZED
+    assert L.gbgemm_create(None, 0) == gbgemm.ERR_INVALID_VALUE
+    for s in (0, -3, -100, -101, -102, -103, -104, -105, -106, 7):
+        assert isinstance(gbgemm.status_string(s), str) and gbgemm.status_string(s)
+    assert gbgemm.status_string(-104) == "GBGEMM_ERR_DEVICE_TIMEOUT"
+
+
+def test_panel_and_workspace_sizes(L):
+    # 16 KiB blocks, rows rounded up to a multiple of 256, k to a multiple of 32
+    assert gbgemm.panel_bytes(1, 1) == 2 * 16384
+    assert gbgemm.panel_bytes(256, 32) == 2 * 16384
+    assert gbgemm.panel_bytes(257, 33) == 4 * 2 * 16384
+    assert gbgemm.panel_bytes(8192, 8192) == 64 * 256 * 16384
+    assert gbgemm.panel_bytes(0, 5) == 0
+    ws = gbgemm.split_workspace_bytes(8192, 8192, 8192)
+    assert ws == 2 * 64 * 256 * 16384 + 2 * 8192 * 4
+
+
+def test_no_cpu_fallback_without_gpu(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert L.gbgemm_create(ctypes.byref(h), 0) == gbgemm.ERR_CUDA
