@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark: sgemm TFLOP/s at m = n = k = 8192 on one GB300, split-BF16 tensor
+path (the headline) against the plain FP32 SIMT path, same inputs.
+
+Workload: the square sgemm sweep's 8192^3 point -- column-major, transa =
+transb = 'N', lda = ldb = ldc = 8200 (rows + 8), alpha = 1.5, beta = -0.25,
+A, B, C uniform[-1, 1) from seed 1 (SplitMix64 generator).  A step is one
+gbgemm_sgemm call on the split path: row maxima, hi/lo packing of both
+operands and the tcgen05 GEMM, everything the call does.  TFLOP/s =
+2 m n k / time (the paper's FLOP convention, Tables I-VI).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64 triple loop) on the host cores
+on bounded samples of the same workload: each step computes one 128 x 128
+block of C (k = 8192) with every core.
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
+rank runs its own replica of the workload (the path does not shard) and
+value = all ranks' FLOPs / the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sgemm TFLOP/s at 8192^3: 3xBF16 tensor vs FP32 SIMT, same GPU, same error bound"
+UNIT = "TFLOP/s"
+N = 8192
+LD = N + 8
+ALPHA, BETA = 1.5, -0.25
+SEED = 1
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", 0.0)), float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+def config(**extra):
+    c = {"workload": "sgemm m=n=k=8192 NN, ld=8200, alpha=1.5, beta=-0.25, uniform[-1,1) seed 1",
+         "m": N, "n": N, "k": N, "transa": "N", "transb": "N", "lda": LD, "ldb": LD, "ldc": LD,
+         "l2": "inputs larger than L2 (3 x 268 MB vs 126 MB L2); no flush"}
+    c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                r = [x.strip() for x in r]
+                if len(r) < 9:
+                    continue
+                if self.uuid and self.uuid not in r[0]:
+                    continue
+                rows.append(r)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the reference arm and the cpu_baseline field)
+# ---------------------------------------------------------------------------
+def oracle_sample(steps: int, block: int = 128, warmup: int = 0):
+    """Time the FP64 oracle on `steps` blocks of the 8192^3 product (all cores)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1608_05265_gb300 import synth
+
+    threads = O.max_threads()
+    times = []
+    flops = 0.0
+    for s in range(warmup + steps):
+        i0 = (s * 977) % (N - block)
+        j0 = (s * 1531) % (N - block)
+        # rows i0.. of A (m x k, N layout), columns j0.. of B (k x n) and the C block
+        A = synth.uniform_block(SEED, 0, N, i0, i0 + block, 0, N)
+        B = synth.uniform_block(SEED, 2, N, 0, N, j0, j0 + block)
+        C = synth.uniform_block(SEED, 4, N, i0, i0 + block, j0, j0 + block)
+        t0 = time.perf_counter()
+        O.gemm_f64("N", "N", block, block, N, ALPHA, A, block, B, N, BETA, C, block, want_bound=False)
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            times.append(dt)
+            flops += 2.0 * block * block * N
+    total = sum(times)
+    return {"value": flops / total / 1e12 if total > 0 else 0.0, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} blocks of {block}x{block} of C (k={N}), FP64 triple loop, {threads} threads",
+            "seconds": total}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    res = oracle_sample(args.steps, warmup=args.warmup)
+    secs = res.pop("seconds")
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1000.0 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(), "cpu_baseline": dict(res),
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1608_05265_gb300 import build as gbuild
+    from paper_1608_05265_gb300 import gbgemm, metrics, synth
+
+    gbuild.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    # Inputs: generated on the host (seeded), pinned for the end-to-end leg.
+    A_h = torch.from_numpy(synth.uniform_matrix(SEED, 0, N, N, LD)).pin_memory()
+    B_h = torch.from_numpy(synth.uniform_matrix(SEED, 2, N, N, LD)).pin_memory()
+    C_h = torch.from_numpy(synth.uniform_matrix(SEED, 4, N, N, LD)).pin_memory()
+    Cout_h = torch.empty_like(C_h).pin_memory()
+    A = A_h.to(dev)
+    B = B_h.to(dev)
+    C0 = C_h.to(dev)
+    C = C0.clone()
+
+    h = gbgemm.Handle(local_rank)
+    h.set_stream(stream)
+    h.reserve_workspace(gbgemm.split_workspace_bytes(N, N, N))
+    flop = metrics.gemm_flops(N, N, N)
+
+    def step(path):
+        h.set_path(path)
+        h.sgemm("N", "N", N, N, N, ALPHA, A, LD, B, LD, BETA, C, LD)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- split path (the headline) ----
+    for _ in range(args.warmup):
+        step(gbgemm.PATH_SPLIT_BF16)
+    barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    h.profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(gbgemm.PATH_SPLIT_BF16)
+    e1.record(stream)
+    barrier()
+    gemm_ms, gemm_launches, launches = h.profile_end()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms)
+    status = h.get_device_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} ({gbgemm.status_string(status)})")
+    value = world * args.steps * flop / (ms_max * 1e-3) / 1e12
+
+    # ---- SIMT path on the same inputs (comparison, not the headline) ----
+    simt_steps = max(2, min(args.steps, 5))
+    step(gbgemm.PATH_SIMT)
+    barrier()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(simt_steps):
+        step(gbgemm.PATH_SIMT)
+    s1.record(stream)
+    barrier()
+    simt_ms = max_over_ranks(s0.elapsed_time(s1)) / simt_steps
+    simt_tflops = flop / (simt_ms * 1e-3) / 1e12
+
+    # ---- end to end: pinned host buffers in, C back to the host, every step ----
+    e2e_steps = max(3, min(args.steps, 10))
+    h.set_path(gbgemm.PATH_SPLIT_BF16)
+    barrier()
+    x0 = torch.cuda.Event(enable_timing=True)
+    x1 = torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(e2e_steps):
+        A.copy_(A_h, non_blocking=True)
+        B.copy_(B_h, non_blocking=True)
+        C.copy_(C_h, non_blocking=True)
+        h.sgemm("N", "N", N, N, N, ALPHA, A, LD, B, LD, BETA, C, LD)
+        Cout_h.copy_(C, non_blocking=True)
+    x1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1)) / e2e_steps
+    e2e_value = world * flop / (e2e_ms * 1e-3) / 1e12
+    assert h.get_device_status() == 0
+    assert np.isfinite(Cout_h[:1000].numpy()).all()
+
+    # ---- roofline of the dominant kernel (the tcgen05 GEMM) ----
+    bf16_peak, bf16_sust, hbm, peak_src = load_peaks()
+    gemm_avg_ms = gemm_ms / max(gemm_launches, 1)
+    achieved = flop / (gemm_avg_ms * 1e-3) / 1e12
+    peak = bf16_peak / 3.0
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "split_gemm_kernel<256>",
+                "note": (f"sgemm-equivalent 2mnk per launch / launch time; peak = {peak_src} bf16 dense "
+                         f"{bf16_peak:.1f} TFLOP/s / 3 products (sustained {bf16_sust:.1f}/3 = "
+                         f"{bf16_sust / 3:.1f}: frac {achieved / (bf16_sust / 3) if bf16_sust else float('nan'):.3f})"),
+                "gemm_share_of_step": gemm_ms / ms if ms > 0 else None}
+
+    if rank == 0:
+        cpu = oracle_sample(steps=max(1, args.cpu_blocks)) if args.cpu_blocks > 0 else None
+        if cpu:
+            cpu.pop("seconds", None)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3-split (fp32 in/out, fp32 accumulate)",
+            "data": "synthetic", "config": config(parallelism=f"replicas x{world}"),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * N * LD * 4,
+                    "d2h_bytes_per_step": N * LD * 4, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "simt": {"value": simt_tflops, "unit": UNIT, "ms_per_step": simt_ms, "steps": simt_steps},
+            "split_over_simt": value / world / simt_tflops if simt_tflops > 0 else None,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-blocks", type=int, default=3, help="oracle blocks timed for cpu_baseline (0: skip)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,6 +124,16 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
  * GBGEMM_ERR_CUDA if the stream reported a CUDA error. */
 int gbgemm_get_device_status(gbgemm_handle* h, int* status);
 
+/* Profiling (benchmark use).  Between begin and end the handle records a
+ * pair of CUDA events on its stream around every launch of the split-path
+ * GEMM kernel, and counts every kernel the library launches.
+ * gbgemm_profile_end synchronises the stream and returns the summed GEMM
+ * kernel time in milliseconds, the number of GEMM launches and the number
+ * of kernels launched by the library (memsets not included).  Any output
+ * pointer may be NULL. */
+int gbgemm_profile_begin(gbgemm_handle* h);
+int gbgemm_profile_end(gbgemm_handle* h, double* gemm_ms, int64_t* gemm_launches, int64_t* kernel_launches);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char* gbgemm_status_string(int status);
 

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -20,6 +21,12 @@ struct gbgemm_handle {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* d_status = nullptr;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
+  size_t ev_used = 0;                // events recorded in this profiling window
+  int64_t gemm_launches = 0;
+  int64_t kernel_launches = 0;
 };
 
 namespace {
@@ -65,6 +72,18 @@ int ensure_workspace(gbgemm_handle* h, size_t bytes) {
 }
 
 bool split_supported(const gbgemm_handle* h) { return h->cc_major == 10 && h->cc_minor == 3; }
+
+// Record the next profiling event on the handle's stream (no-op when not profiling).
+cudaError_t prof_record(gbgemm_handle* h) {
+  if (!h->profiling) return cudaSuccess;
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    h->ev_pool.push_back(e);
+  }
+  return cudaEventRecord(h->ev_pool[h->ev_used++], h->stream);
+}
 
 }  // namespace
 
@@ -117,6 +136,7 @@ int gbgemm_destroy(gbgemm_handle* h) {
   cudaStreamSynchronize(h->stream);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return GBGEMM_OK;
 }
@@ -174,7 +194,9 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   if (!use_ab && beta == 1.0f) return GBGEMM_OK;
   DeviceGuard g(h->device);
   if (!use_ab) {
-    return gbg::launch_scale_c(m, n, beta, C, ldc, h->stream) == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
+    if (gbg::launch_scale_c(m, n, beta, C, ldc, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    h->kernel_launches += 1;
+    return GBGEMM_OK;
   }
   int path = h->path;
   if (path == GBGEMM_PATH_AUTO) path = (k >= gbg::kSplitMinK && split_supported(h)) ? GBGEMM_PATH_SPLIT_BF16 : GBGEMM_PATH_SIMT;
@@ -182,6 +204,7 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   if (path == GBGEMM_PATH_SIMT) {
     const int cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
     if (gbg::launch_simt(p, cfg, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    h->kernel_launches += 1;
     h->last_path = GBGEMM_PATH_SIMT;
     return GBGEMM_OK;
   }
@@ -204,7 +227,12 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
   a.status = h->d_status; a.num_sms = h->num_sms;
   a.bn = 256; a.raster = 16;
+  h->kernel_launches += 4;  // two row-maximum and two packing kernels
+  if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (gbg::launch_split_gemm(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  h->kernel_launches += 1;
+  h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;
   return GBGEMM_OK;
 }
@@ -234,6 +262,33 @@ int gbgemm_get_device_status(gbgemm_handle* h, int* status) {
   if (cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (v != 0 && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return GBGEMM_ERR_CUDA;
   *status = v;
+  return GBGEMM_OK;
+}
+
+int gbgemm_profile_begin(gbgemm_handle* h) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  h->profiling = true;
+  h->ev_used = 0;
+  h->gemm_launches = 0;
+  h->kernel_launches = 0;
+  return GBGEMM_OK;
+}
+
+int gbgemm_profile_end(gbgemm_handle* h, double* gemm_ms, int64_t* gemm_launches, int64_t* kernel_launches) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  DeviceGuard g(h->device);
+  h->profiling = false;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    total += ms;
+  }
+  if (gemm_ms) *gemm_ms = total;
+  if (gemm_launches) *gemm_launches = h->gemm_launches;
+  if (kernel_launches) *kernel_launches = h->kernel_launches;
+  h->ev_used = 0;
   return GBGEMM_OK;
 }
 

@@ -35,7 +35,8 @@ PATH_SPLIT_BF16 = 2
 EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_get_device_status",
-    "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack",
+    "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
+    "gbgemm_profile_end",
 ]
 
 _lock = threading.Lock()
@@ -72,9 +73,13 @@ def lib():
             L.gbgemm_panel_bytes.argtypes = [i64, i64]
             L.gbgemm_panel_bytes.restype = ctypes.c_size_t
             L.gbgemm_split_pack.argtypes = [vp, c, c, i64, i64, vp, i64, vp, vp]
+            L.gbgemm_profile_begin.argtypes = [vp]
+            L.gbgemm_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                             ctypes.POINTER(i64)]
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
-                         "gbgemm_get_device_status", "gbgemm_split_pack"):
+                         "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
+                         "gbgemm_profile_end"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -159,6 +164,16 @@ class Handle:
         v = ctypes.c_int()
         _check("gbgemm_get_device_status", lib().gbgemm_get_device_status(self._h, ctypes.byref(v)))
         return v.value
+
+    def profile_begin(self):
+        _check("gbgemm_profile_begin", lib().gbgemm_profile_begin(self._h))
+
+    def profile_end(self):
+        """(summed GEMM kernel ms, GEMM launches, kernels launched) since profile_begin."""
+        ms, g, k = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check("gbgemm_profile_end", lib().gbgemm_profile_end(self._h, ctypes.byref(ms), ctypes.byref(g),
+                                                              ctypes.byref(k)))
+        return ms.value, g.value, k.value
 
     def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
         return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),

@@ -100,6 +100,19 @@ def place_colmajor(vals_by_col: np.ndarray, rows: int, cols: int, ld: int) -> np
     return flat
 
 
+def uniform_block(seed: int, stream: int, rows: int, r0: int, r1: int, c0: int, c1: int) -> np.ndarray:
+    """Rows r0..r1-1, columns c0..c1-1 of the uniform matrix of ``rows`` rows
+    drawn by ``uniform_matrix(seed, stream, rows, ...)``, as a column-major
+    block with leading dimension r1 - r0 (flat float32 array)."""
+    r = np.arange(r0, r1, dtype=np.uint64)
+    c = np.arange(c0, c1, dtype=np.uint64)
+    idx = (c[:, None] * np.uint64(rows) + r[None, :]).reshape(-1)
+    base = stream_base(seed, stream)
+    with np.errstate(over="ignore"):
+        u = _mix(base + (idx + np.uint64(1)) * GAMMA)
+    return uniform_pm1(u)
+
+
 def uniform_matrix(seed: int, stream: int, rows: int, cols: int, ld: int) -> np.ndarray:
     v = uniform_pm1(draws(seed, stream, rows * cols))
     return place_colmajor(v, rows, cols, ld)

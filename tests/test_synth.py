@@ -66,3 +66,11 @@ def test_grouped_shapes_range():
     # log-uniform: the median is near sqrt(16*1025) ~ 128
     assert 100 < np.median(dims) < 165
     assert {x[0] for x in s} == {"N", "T"}
+
+
+def test_uniform_block_matches_full_matrix():
+    rows, cols, ld = 37, 23, 40
+    full = synth.uniform_matrix(9, 2, rows, cols, ld)
+    L = synth.logical(full, rows, cols, ld)
+    blk = synth.uniform_block(9, 2, rows, 5, 30, 3, 20)
+    assert np.array_equal(synth.logical(blk, 25, 17, 25), L[5:30, 3:20])
