@@ -505,11 +505,16 @@ cudaError_t launch_gemm_bn(const SplitGemmArgs& a, cudaStream_t s) {
   P.rbB = panel_row_blocks(a.n);
   P.timeout_ns = kTimeoutNs;
   constexpr int smem = gemm_smem_bytes<BN>();
-  static bool attr_set = false;  // one attribute call per kernel instance and process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // The shared-memory opt-in is a per-device function attribute: set it once
+  // for every device this kernel instance is launched on.
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(split_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   const int64_t tiles = tm * tn;
   const int grid = (int)(tiles < (int64_t)(a.num_sms > 0 ? a.num_sms : 148) ? tiles : (int64_t)(a.num_sms > 0 ? a.num_sms : 148));
