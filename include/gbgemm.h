@@ -67,7 +67,8 @@ typedef enum {
   GBGEMM_ERR_UNSUPPORTED_DEVICE = -103, /* split path requested on a device that is not sm_103 */
   GBGEMM_ERR_DEVICE_TIMEOUT = -104,   /* a kernel's bounded wait ran out (see gbgemm_get_device_status) */
   GBGEMM_ERR_BAD_PLAN = -105,         /* plan inputs invalid (bad problem index in *bad_index) */
-  GBGEMM_ERR_INVALID_VALUE = -106     /* other invalid argument (path code, size, pointer) */
+  GBGEMM_ERR_INVALID_VALUE = -106,    /* other invalid argument (path code, size, pointer) */
+  GBGEMM_ERR_SCRATCH_LIMIT = -107     /* problem needs more than GBGEMM_NOALLOC_SCRATCH_BYTES */
 } gbgemm_status;
 
 typedef enum {
@@ -136,6 +137,49 @@ int gbgemm_profile_end(gbgemm_handle* h, double* gemm_ms, int64_t* gemm_launches
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char* gbgemm_status_string(int status);
+
+/* ---------------------------------------------------------------------- */
+/* Allocation-free split-BF16 sgemm.  (The paper has no counterpart: its
+ * service process owns all buffers.  This entry point exists for users of
+ * this library.)
+ *
+ * For callers that cannot call cudaMalloc at the time they multiply: code
+ * running inside someone else's stream capture (allocation is not a
+ * capturable operation), allocator or memory-pool callbacks that must not
+ * re-enter the allocator, latency-bound loops that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree imply, or processes whose device memory
+ * another framework has reserved.  It computes the same thing as
+ * gbgemm_sgemm on GBGEMM_PATH_SPLIT_BF16, with the same argument checks and
+ * quick returns (arguments 1-13 are the BLAS ones, same error codes), but
+ * needs no handle and allocates nothing: its scratch (hi/lo panels, row
+ * maxima, a status word) is a fixed array of GBGEMM_NOALLOC_SCRATCH_BYTES in
+ * this library's device memory, which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * Limits and behaviour:
+ *   - a problem whose gbgemm_split_workspace_bytes(m, n, k) + 256 exceeds
+ *     GBGEMM_NOALLOC_SCRATCH_BYTES returns GBGEMM_ERR_SCRATCH_LIMIT without
+ *     launching anything (64 MiB holds m = n = k = 2048, for example);
+ *   - runs on the CURRENT device and on `cuda_stream` (a cudaStream_t, NULL =
+ *     legacy default stream), asynchronously;
+ *   - the first call on each device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress, with that device current) and caches
+ *     it; make that first call before any stream capture;
+ *   - every call shares the one array and leaves its contents behind; each
+ *     call rewrites or zeroes what it reads, but calls whose work overlaps on
+ *     the GPU (different streams, or different host threads, without
+ *     ordering between them) race on the array and give wrong results:
+ *     order them on one stream or with events;
+ *   - `status`: NULL, or a caller-owned DEVICE int that the GEMM kernel sets
+ *     to GBGEMM_ERR_DEVICE_TIMEOUT if one of its bounded waits runs out (the
+ *     caller zeroes it beforehand).  With NULL the report goes to a slot of
+ *     the scratch array that the caller cannot read.
+ * Errors: the argument codes of gbgemm_sgemm, GBGEMM_ERR_SCRATCH_LIMIT,
+ * GBGEMM_ERR_UNSUPPORTED_DEVICE (not sm_103), GBGEMM_ERR_CUDA. */
+#define GBGEMM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int gbgemm_sgemm_split_noalloc(void* cuda_stream, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                               float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                               float beta, float* C, int64_t ldc, int* status);
 
 /* ---------------------------------------------------------------------- */
 /* Split-panel inspection (tests): runs the split path's scaling and packing

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbgemm.so")
-SOURCES = ["api.cu", "simt.cu", "split.cu"]
+SOURCES = ["api.cu", "simt.cu", "split.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "gbgemm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

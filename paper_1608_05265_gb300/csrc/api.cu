@@ -303,6 +303,7 @@ const char* gbgemm_status_string(int s) {
     case GBGEMM_ERR_DEVICE_TIMEOUT: return "GBGEMM_ERR_DEVICE_TIMEOUT";
     case GBGEMM_ERR_BAD_PLAN: return "GBGEMM_ERR_BAD_PLAN";
     case GBGEMM_ERR_INVALID_VALUE: return "GBGEMM_ERR_INVALID_VALUE";
+    case GBGEMM_ERR_SCRATCH_LIMIT: return "GBGEMM_ERR_SCRATCH_LIMIT";
     default: return "GBGEMM_UNKNOWN_STATUS";
   }
 }

@@ -26,6 +26,8 @@ ERR_UNSUPPORTED_DEVICE = -103
 ERR_DEVICE_TIMEOUT = -104
 ERR_BAD_PLAN = -105
 ERR_INVALID_VALUE = -106
+ERR_SCRATCH_LIMIT = -107
+NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 PATH_AUTO = 0
 PATH_SIMT = 1
@@ -36,7 +38,7 @@ EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_get_device_status",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
-    "gbgemm_profile_end",
+    "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc",
 ]
 
 _lock = threading.Lock()
@@ -73,13 +75,15 @@ def lib():
             L.gbgemm_panel_bytes.argtypes = [i64, i64]
             L.gbgemm_panel_bytes.restype = ctypes.c_size_t
             L.gbgemm_split_pack.argtypes = [vp, c, c, i64, i64, vp, i64, vp, vp]
+            L.gbgemm_sgemm_split_noalloc.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64,
+                                                     vp]
             L.gbgemm_profile_begin.argtypes = [vp]
             L.gbgemm_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                              ctypes.POINTER(i64)]
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
                          "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
-                         "gbgemm_profile_end"):
+                         "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -178,6 +182,13 @@ class Handle:
     def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
         return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),
                                        _ptr(amax_bits), _ptr(panel))
+
+
+def sgemm_split_noalloc(stream, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, status=None) -> int:
+    """gbgemm_sgemm_split_noalloc: the split-path sgemm with no device allocation (returns the status)."""
+    return lib().gbgemm_sgemm_split_noalloc(_stream_ptr(stream), transa.encode(), transb.encode(), int(m), int(n),
+                                            int(k), float(alpha), _ptr(A), int(lda), _ptr(B), int(ldb), float(beta),
+                                            _ptr(C), int(ldc), _ptr(status))
 
 
 def split_workspace_bytes(m, n, k) -> int:

@@ -1,0 +1,78 @@
+"""The allocation-free split sgemm (gbgemm_sgemm_split_noalloc).
+
+It serves callers that cannot call cudaMalloc when they multiply (inside
+another component's stream capture, inside allocator callbacks, in
+latency-bound loops, or with device memory reserved by another framework):
+its scratch is a fixed array in the library's device memory instead of a
+handle's workspace.  This file is named so that pytest collects it last.
+
+Checks, through the C ABI: two calls in a row on different problems (the
+second reuses scratch the first left behind) agree with gbgemm_sgemm on the
+split path within the acceptance bound 2 k 2^-24 (|alpha||A||B| + |beta||C|)
+used by every parity test; a problem needing more scratch than the fixed
+maximum is refused with GBGEMM_ERR_SCRATCH_LIMIT before anything runs.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1608_05265_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_both(L, h, stream, ta, tb, m, n, k, alpha, beta, seed):
+    import torch
+    from paper_1608_05265_gb300 import gbgemm
+    A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", seed, ta, tb, m, n, k, pad=3)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    c_new = torch.from_numpy(C).cuda()
+    c_old = torch.from_numpy(C).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = L.gbgemm_sgemm_split_noalloc(stream, ta.encode(), tb.encode(), m, n, k, alpha, dA.data_ptr(), lda,
+                                      dB.data_ptr(), ldb, beta, c_new.data_ptr(), ldc, status.data_ptr())
+    assert rc == gbgemm.OK, gbgemm.status_string(rc)
+    h.set_path(gbgemm.PATH_SPLIT_BF16)
+    h.sgemm(ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, c_old, ldc)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert h.get_device_status() == 0
+    new = c_new.cpu().numpy()
+    old = c_old.cpu().numpy()
+    assert synth.padding_is_sentinel(new, m, n, ldc)
+    _, bound = O.gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc)
+    diff = np.abs(synth.logical(new, m, n, ldc).astype(np.float64) - synth.logical(old, m, n, ldc))
+    assert np.all(diff <= bound)
+
+
+def test_noalloc_matches_existing_entry_point_twice():
+    import torch
+    from paper_1608_05265_gb300 import build, gbgemm
+    build.build()
+    L = gbgemm.lib()
+    h = gbgemm.Handle(0)
+    stream = torch.cuda.current_stream()
+    h.set_stream(stream)
+    # first call, then a second, larger one that reuses what the first left in the scratch array
+    _run_both(L, h, stream.cuda_stream, "N", "T", 300, 520, 384, 1.5, -0.25, 41)
+    _run_both(L, h, stream.cuda_stream, "T", "N", 1000, 777, 555, -1.0, 1.0, 42)
+    h.close()
+
+
+def test_noalloc_refuses_problems_beyond_the_scratch_limit():
+    import torch
+    from paper_1608_05265_gb300 import build, gbgemm
+    build.build()
+    L = gbgemm.lib()
+    n = 4096  # needs 2 x 128 MiB of panels: beyond the 64 MiB array
+    assert gbgemm.split_workspace_bytes(n, n, n) + 256 > gbgemm.NOALLOC_SCRATCH_BYTES
+    A = torch.zeros(n * n, device="cuda")
+    B = torch.zeros(n * n, device="cuda")
+    C = torch.full((n * n,), 7.0, device="cuda")
+    rc = L.gbgemm_sgemm_split_noalloc(torch.cuda.current_stream().cuda_stream, b"N", b"N", n, n, n, 1.0,
+                                      A.data_ptr(), n, B.data_ptr(), n, 0.0, C.data_ptr(), n, None)
+    torch.cuda.synchronize()
+    assert rc == gbgemm.ERR_SCRATCH_LIMIT
+    assert bool(torch.all(C == 7.0))
