@@ -275,10 +275,12 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // ---------------------------------------------------------------------------
 // K3: persistent split-BF16 GEMM.
 // Warp 0 lane 0: producer.  Warp 1: TMEM owner, lane 0 issues the MMAs.
-// Warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4) .. +31).
+// Warps 2-9: epilogue; warp w reads TMEM lanes 32*(w%4) .. +31 (the rows it
+// owns) and columns [h*BN/2, (h+1)*BN/2) with h = (w-2)/4.
 // ---------------------------------------------------------------------------
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 192;
+constexpr int kEpiWarps = 8;                       // two per TMEM lane quadrant, each half of the columns
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 struct GemmParams {
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmP
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(accf_bar(b), 1); mbar_init(acce_bar(b), 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(accf_bar(b), 1); mbar_init(acce_bar(b), kEpiWarps); }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -425,6 +427,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmP
   } else {
     // ---------------- epilogue ----------------
     const int q = warp & 3;
+    const int c_begin = ((warp - 2) >> 2) * (BN / 2);
     int abuf = 0;
     uint32_t aphase = 0;
     for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
@@ -444,30 +447,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmP
       const int ea = row_ok ? scale_exp_from_bits(P.amaxA[i]) : 0;
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN);
       float* const crow = P.C + i;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = c_begin; c0 < c_begin + BN / 2; c0 += 32) {
         if (n0 + c0 >= P.n) break;  // warp-uniform
-        uint32_t r[32];
-        tmem_ld32(taddr + (uint32_t)c0, r);
-        const int64_t jl = n0 + c0 + lane;
-        const int eb_l = (jl < P.n) ? scale_exp_from_bits(P.amaxB[jl]) : 0;
-        const int jmax = (int)(P.n - (n0 + c0) < 32 ? P.n - (n0 + c0) : 32);
+        const int jmax = (P.n - (n0 + c0) < 32) ? (int)(P.n - (n0 + c0)) : 32;
         float* cp = crow + (n0 + c0) * P.ldc;
-        // Every lane runs every shuffle; only the stores are predicated.
+        // All loads of the chunk are issued before any result is formed, so
+        // the 32 column reads of C overlap instead of queueing one by one.
+        float cv[32];
         if (P.beta != 0.f) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const int eb = __shfl_sync(0xFFFFFFFFu, eb_l, jj);
-            if (row_ok && jj < jmax) {
-              const float v = scalbnf(__uint_as_float(r[jj]), ea + eb);
-              cp[jj * P.ldc] = fmaf(P.alpha, v, P.beta * cp[jj * P.ldc]);
-            }
-          }
-        } else {
+          for (int jj = 0; jj < 32; ++jj) cv[jj] = (row_ok && jj < jmax) ? __ldcs(cp + jj * P.ldc) : 0.f;
+        }
+        const int64_t jl = n0 + c0 + lane;
+        const int eb_l = (jl < P.n) ? scale_exp_from_bits(P.amaxB[jl]) : 0;
+        uint32_t r[32];
+        tmem_ld32(taddr + (uint32_t)c0, r);
+        // Every lane runs every shuffle; only the stores are predicated.
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const int eb = __shfl_sync(0xFFFFFFFFu, eb_l, jj);
-            if (row_ok && jj < jmax) cp[jj * P.ldc] = P.alpha * scalbnf(__uint_as_float(r[jj]), ea + eb);
-          }
+        for (int jj = 0; jj < 32; ++jj) {
+          const int s = ea + __shfl_sync(0xFFFFFFFFu, eb_l, jj);
+          const float acc = __uint_as_float(r[jj]);
+          // acc * 2^s: one multiply when 2^s is a normal float, else scalbnf.
+          const float v = (s >= -126 && s <= 127) ? acc * __int_as_float((s + 127) << 23) : scalbnf(acc, s);
+          const float out = (P.beta != 0.f) ? fmaf(P.alpha, v, P.beta * cv[jj]) : P.alpha * v;
+          if (row_ok && jj < jmax) __stcs(cp + jj * P.ldc, out);
         }
       }
       tc_fence_before();
