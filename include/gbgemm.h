@@ -24,9 +24,11 @@
  * Two paths compute the same result within the componentwise bound
  *     |C - C_exact|_ij <= 2 * max(k,1) * 2^-24 * (|alpha| sum_p |opA(i,p)||opB(p,j)| + |beta| |C_in,ij|)
  *   GBGEMM_PATH_SIMT        plain FP32 fused multiply-add on the CUDA cores.
- *   GBGEMM_PATH_SPLIT_BF16  each operand row (of op(A)) and column (of op(B))
- *                           is scaled by a power of two so its largest entry
- *                           lies in [0.5, 1), every entry x becomes
+ *   GBGEMM_PATH_SPLIT_BF16  each badly scaled operand row (of op(A)) or
+ *                           column (of op(B)) -- largest magnitude outside
+ *                           [2^-48, 2^48) -- is scaled by a power of two so
+ *                           its largest entry lies in [0.5, 1); every entry x
+ *                           becomes
  *                           hi + lo (two BF16 values, hi = bf16(x),
  *                           lo = bf16(x - hi)), and the tensor cores
  *                           accumulate hi*hi + hi*lo + lo*hi in FP32.  The
@@ -199,8 +201,9 @@ int gbgemm_sgemm_split_noalloc(void* cuda_stream, char transa, char transb, int6
  *   chunks; logical chunk c is stored at chunk position c XOR (r mod 8).
  *   Chunks 0-3 hold hi of k offsets 0-31 (8 per chunk, ascending), chunks
  *   4-7 hold lo of the same offsets.  Rows >= rows and k >= k are zero.
- * hi/lo of x are those of x * 2^-e with e the frexp exponent of the row's
- * max |x| (e = 0 when that max is 0 or not finite).
+ * hi/lo of x are those of x * 2^-e, where e = 0 when the row's max |x| is
+ * 0, not finite or in [2^-48, 2^48), and otherwise e is the frexp exponent
+ * of that max.
  * Asynchronous on the handle's stream. */
 size_t gbgemm_panel_bytes(int64_t rows, int64_t k);
 int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,

@@ -29,8 +29,10 @@
  * precision-recovery step): restated from the IEEE-754 definitions.
  *   bf16 RNE:   round the float's 32-bit pattern to its top 16 bits, ties to
  *               even; NaN stays NaN; values >= 2^128(1-2^-9) become Inf.
- *   exponent:   e = frexp exponent of the row's max |x| (max in [0.5,1) after
- *               scaling); 0 when the max is 0 or not finite.
+ *   exponent:   scaling is for badly scaled K-vectors only.  With M the
+ *               row's max |x|: e = 0 when M is 0, not finite, or in
+ *               [2^-48, 2^48) (well scaled); otherwise e = frexp exponent of
+ *               M, so that the scaled max lies in [0.5, 1).
  *   split:      x' = x * 2^-e (exact in double, one rounding to float),
  *               hi = bf16(x'), lo = bf16(x' - hi); non-finite x: lo = 0.
  *
@@ -170,9 +172,11 @@ uint16_t oracle_bf16_rne(float x) {
 
 float oracle_bf16_to_f32(uint16_t h) { return u2f((uint32_t)h << 16); }
 
-/* frexp exponent of a non-negative max magnitude; 0 for 0 or non-finite. */
+/* Scaling exponent of a K-vector from its max magnitude: 0 for 0, non-finite
+ * or well-scaled maxima (2^-48 <= amax < 2^48), else the frexp exponent. */
 int oracle_scale_exponent(float amax) {
   if (!(amax > 0.0f) || !isfinite(amax)) return 0;
+  if ((double)amax >= ldexp(1.0, -48) && (double)amax < ldexp(1.0, 48)) return 0;
   int e;
   (void)frexp((double)amax, &e);
   return e;

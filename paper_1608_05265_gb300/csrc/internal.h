@@ -37,9 +37,11 @@ inline size_t panel_bytes(int64_t rows, int64_t k) {
   return (size_t)panel_row_blocks(rows) * (size_t)panel_k_chunks(k) * (size_t)kBlockBytes;
 }
 
-// Split one operand: amax pass then pack pass.  `kcontig` selects the view:
-// element (r, p) = X[r*ld + p] (kcontig) or X[r + p*ld] (!kcontig).
-// amax_bits must hold `rows` words; it is zeroed here.
+// Split one operand: one pass packs the unscaled hi/lo panel and records
+// every K-vector's max |x|, a second pass re-packs the badly scaled vectors
+// (max outside [2^-48, 2^48)).  `kcontig` selects the view: element (r, p) =
+// X[r*ld + p] (kcontig) or X[r + p*ld] (!kcontig).  amax_bits must hold
+// `rows` words; it is zeroed here.
 cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
                               uint32_t* amax_bits, void* panel, cudaStream_t s);
 

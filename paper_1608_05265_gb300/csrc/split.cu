@@ -38,9 +38,14 @@ namespace {
 // Shared helpers
 // ---------------------------------------------------------------------------
 
-// frexp exponent of a non-negative float given by its bits; 0 for 0, Inf, NaN.
+// Scaling exponent of a K-vector from the bits of its max magnitude: 0 for
+// 0, Inf, NaN and for well-scaled maxima in [2^-48, 2^48); otherwise the
+// frexp exponent, which brings the max into [0.5, 1).
+constexpr uint32_t kWellScaledLo = (127u - 48u) << 23;  // bits of 2^-48
+constexpr uint32_t kWellScaledHi = (127u + 48u) << 23;  // bits of 2^48
 __device__ __forceinline__ int scale_exp_from_bits(uint32_t b) {
   if (b == 0u || b >= 0x7F800000u) return 0;
+  if (b >= kWellScaledLo && b < kWellScaledHi) return 0;
   const int E = (int)(b >> 23);
   if (E > 0) return E - 126;
   return (32 - __clz(b)) - 149;  // subnormal: value = b * 2^-149
@@ -64,96 +69,137 @@ __device__ __forceinline__ void split_bf16(float xs, uint32_t& h, uint32_t& l) {
 }
 
 // ---------------------------------------------------------------------------
-// K1a: max |x| per K-vector (bit patterns; NaN > Inf > finite as unsigned).
+// K1: split and pack.  One pass writes the hi/lo panel of the UNSCALED
+// operand and the max |x| of every K-vector (bit patterns; NaN > Inf >
+// finite as unsigned).  Well-scaled vectors (the large majority) are then
+// final.  A second, usually empty pass re-packs the badly scaled ones with
+// their scaling exponent.  For a well-scaled vector the two definitions
+// give the same GEMM result: scaling by a power of two commutes with every
+// FP32 rounding as long as nothing leaves the normal range.
+//
+// Thread work item: one row r of a 128-row x 32-k block and one 8-wide
+// k-chunk cc (0..3) -> two 16-byte stores (hi chunk cc, lo chunk cc + 4) at
+// chunk positions XOR (r mod 8).
 // ---------------------------------------------------------------------------
 
-// Element (r, p) at X[r*ld + p]: one warp per row over a 4096-wide k segment.
-__global__ void __launch_bounds__(256) amax_kcontig_kernel(int64_t rows, int64_t k, const float* __restrict__ X,
-                                                           int64_t ld, uint32_t* __restrict__ amax) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * 8 + warp;
-  if (r >= rows) return;
-  const int64_t p0 = (int64_t)blockIdx.y * 4096;
-  const int64_t p1 = min(k, p0 + 4096);
-  const float* row = X + r * ld;
-  uint32_t mx = 0u;
-  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-  if (vec) {
-    const int64_t v1 = p0 + ((p1 - p0) & ~int64_t(127));
-    for (int64_t p = p0 + 4 * lane; p < v1; p += 128) {
-      const uint4 u = *reinterpret_cast<const uint4*>(row + p);
-      mx = max(mx, max(max(u.x & 0x7FFFFFFFu, u.y & 0x7FFFFFFFu), max(u.z & 0x7FFFFFFFu, u.w & 0x7FFFFFFFu)));
-    }
-    for (int64_t p = v1 + lane; p < p1; p += 32) mx = max(mx, __float_as_uint(row[p]) & 0x7FFFFFFFu);
-  } else {
-    for (int64_t p = p0 + lane; p < p1; p += 32) mx = max(mx, __float_as_uint(row[p]) & 0x7FFFFFFFu);
-  }
+// Split 8 values (already scaled) and store the hi and lo chunks of row rr.
+__device__ __forceinline__ void store_split8(uint8_t* blk, int rr, int cc, const float (&x)[8]) {
+  uint32_t hw[4], lw[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-  if (lane == 0) atomicMax(&amax[r], mx);
+  for (int q = 0; q < 4; ++q) {
+    uint32_t h0, l0, h1, l1;
+    split_bf16(x[2 * q], h0, l0);
+    split_bf16(x[2 * q + 1], h1, l1);
+    hw[q] = h0 | (h1 << 16);
+    lw[q] = l0 | (l1 << 16);
+  }
+  const int sw = rr & 7;
+  *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
-// Element (r, p) at X[r + p*ld]: one thread per row over a 256-deep k segment.
-__global__ void __launch_bounds__(256) amax_rcontig_kernel(int64_t rows, int64_t k, const float* __restrict__ X,
-                                                           int64_t ld, uint32_t* __restrict__ amax) {
-  const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (r >= rows) return;
-  const int64_t p0 = (int64_t)blockIdx.y * 256;
-  const int64_t p1 = min(k, p0 + 256);
-  uint32_t mx = 0u;
-#pragma unroll 8
-  for (int64_t p = p0; p < p1; ++p) mx = max(mx, __float_as_uint(X[r + p * ld]) & 0x7FFFFFFFu);
-  atomicMax(&amax[r], mx);
+// Item mapping inside a 256-thread CTA, two items per thread.
+// KCONTIG (element (r,p) at X[r*ld + p]): four lanes per row, eight rows per
+//   warp, so a warp reads eight 128-byte row segments.
+// !KCONTIG (element (r,p) at X[r + p*ld]): 32 consecutive rows per warp and
+//   one chunk per warp, so every load instruction reads 128 contiguous bytes.
+template <bool KCONTIG>
+__device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
+  if (KCONTIG) {
+    const int idx = tid + 256 * it;
+    rr = idx >> 2;
+    cc = idx & 3;
+  } else {
+    const int w = tid >> 5;
+    cc = w & 3;
+    rr = ((w >> 2) + 2 * it) * 32 + (tid & 31);
+  }
 }
 
-// ---------------------------------------------------------------------------
-// K1b: scale, split and pack one 128-row x 32-k block into its 16 KiB panel
-// block (layout documented with gbgemm_split_pack in gbgemm.h).
-// ---------------------------------------------------------------------------
+template <bool KCONTIG>
+__device__ __forceinline__ void load8(const float* __restrict__ X, int64_t ld, int64_t r, int64_t p, int64_t rows,
+                                      int64_t k, bool vec, float (&x)[8]) {
+  if (KCONTIG) {
+    if (r < rows && vec && p + 8 <= k) {
+      const float4 a = *reinterpret_cast<const float4*>(X + r * ld + p);
+      const float4 b = *reinterpret_cast<const float4*>(X + r * ld + p + 4);
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = (r < rows && p + q < k) ? X[r * ld + p + q] : 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = (r < rows && p + q < k) ? X[r + (p + q) * ld] : 0.f;
+  }
+}
+
 template <bool KCONTIG>
 __global__ void __launch_bounds__(256) pack_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
-                                                   const uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
+                                                   uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
                                                    int64_t rb_count) {
-  __shared__ float T[128 * 33];
+  __shared__ uint32_t smax[128];
   const int64_t rb = blockIdx.x, kc = blockIdx.y;
   const int64_t r0 = rb * 128, p0 = kc * 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (KCONTIG) {
-#pragma unroll 4
-    for (int rr = warp; rr < 128; rr += 8) {
-      const int64_t r = r0 + rr, p = p0 + lane;
-      T[rr * 33 + lane] = (r < rows && p < k) ? X[r * ld + p] : 0.f;
-    }
-  } else {
-#pragma unroll 4
-    for (int q = warp; q < 128; q += 8) {
-      const int pp = q >> 2, rr = (q & 3) * 32 + lane;
-      const int64_t r = r0 + rr, p = p0 + pp;
-      T[rr * 33 + pp] = (r < rows && p < k) ? X[r + p * ld] : 0.f;
-    }
+  const int tid = threadIdx.x;
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  if (tid < 128) smax[tid] = 0u;
+  float x[2][8];
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {  // all loads first: 16 (or 4 vector) loads in flight per thread
+    int rr, cc;
+    item_of<KCONTIG>(tid, it, rr, cc);
+    load8<KCONTIG>(X, ld, r0 + rr, p0 + cc * 8, rows, k, vec, x[it]);
   }
   __syncthreads();
   uint8_t* blk = panel + (size_t)(kc * rb_count + rb) * kBlockBytes;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const int idx = tid + it * 256;
-    const int rr = idx >> 2, cc = idx & 3;
-    const int64_t r = r0 + rr;
-    const int e = (r < rows) ? scale_exp_from_bits(amax[r]) : 0;
-    uint32_t hw[4], lw[4];
+    int rr, cc;
+    item_of<KCONTIG>(tid, it, rr, cc);
+    uint32_t mx = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float x0 = T[rr * 33 + cc * 8 + 2 * q];
-      const float x1 = T[rr * 33 + cc * 8 + 2 * q + 1];
-      uint32_t h0, l0, h1, l1;
-      split_bf16(isfinite(x0) ? scale_pow2(x0, e) : x0, h0, l0);
-      split_bf16(isfinite(x1) ? scale_pow2(x1, e) : x1, h1, l1);
-      hw[q] = h0 | (h1 << 16);
-      lw[q] = l0 | (l1 << 16);
+    for (int q = 0; q < 8; ++q) mx = max(mx, __float_as_uint(x[it][q]) & 0x7FFFFFFFu);
+    store_split8(blk, rr, cc, x[it]);
+    if (KCONTIG) {
+      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
+      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
+      if (cc == 0 && mx != 0u) atomicMax(&smax[rr], mx);
+    } else if (mx != 0u) {
+      atomicMax(&smax[rr], mx);
     }
-    const int sw = rr & 7;
-    *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+  __syncthreads();
+  if (tid < 128 && r0 + tid < rows && smax[tid] != 0u) atomicMax(&amax[r0 + tid], smax[tid]);
+}
+
+// Re-pack the badly scaled K-vectors of one 128-row block over all k chunks
+// with x' = x * 2^-e.  A block without such rows returns at once.
+__global__ void __launch_bounds__(256) rescale_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
+                                                      bool kcontig, const uint32_t* __restrict__ amax,
+                                                      uint8_t* __restrict__ panel, int64_t rb_count, int64_t nkc) {
+  __shared__ int se[128];
+  const int64_t rb = blockIdx.x, r0 = rb * 128;
+  const int tid = threadIdx.x;
+  int e = 0;
+  if (tid < 128 && r0 + tid < rows) e = scale_exp_from_bits(amax[r0 + tid]);
+  if (tid < 128) se[tid] = e;
+  if (!__syncthreads_or(e != 0)) return;
+  for (int64_t kc = 0; kc < nkc; ++kc) {
+    uint8_t* blk = panel + (size_t)(kc * rb_count + rb) * kBlockBytes;
+    for (int it = 0; it < 2; ++it) {
+      const int idx = tid + 256 * it, rr = idx >> 2, cc = idx & 3;
+      const int er = se[rr];
+      if (er == 0) continue;
+      const int64_t r = r0 + rr, p = kc * 32 + cc * 8;
+      float x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float v = (r < rows && p + q < k) ? (kcontig ? X[r * ld + p + q] : X[r + (p + q) * ld]) : 0.f;
+        x[q] = isfinite(v) ? scale_pow2(v, er) : v;
+      }
+      store_split8(blk, rr, cc, x);
+    }
   }
 }
 
@@ -532,20 +578,16 @@ cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t l
   if (rows <= 0 || k <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(amax_bits, 0, (size_t)rows * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  if (kcontig) {
-    dim3 g((unsigned)((rows + 7) / 8), (unsigned)((k + 4095) / 4096));
-    amax_kcontig_kernel<<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits);
-  } else {
-    dim3 g((unsigned)((rows + 255) / 256), (unsigned)((k + 255) / 256));
-    amax_rcontig_kernel<<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits);
-  }
+  const int64_t rbc = panel_row_blocks(rows);
+  const int64_t nkc = panel_k_chunks(k);
+  dim3 g((unsigned)rbc, (unsigned)nkc);
+  if (g.y > 65535u) return cudaErrorInvalidConfiguration;
+  uint8_t* pn = static_cast<uint8_t*>(panel);
+  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, rbc);
+  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, rbc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t rbc = panel_row_blocks(rows);
-  dim3 g((unsigned)rbc, (unsigned)panel_k_chunks(k));
-  if (g.y > 65535u) return cudaErrorInvalidConfiguration;
-  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, static_cast<uint8_t*>(panel), rbc);
-  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, static_cast<uint8_t*>(panel), rbc);
+  rescale_kernel<<<(unsigned)rbc, 256, 0, s>>>(rows, k, X, ld, kcontig, amax_bits, pn, rbc, nkc);
   return cudaGetLastError();
 }
 

@@ -67,10 +67,15 @@ def test_split_worked_values(x, hi, lo):
         assert (int(H[0, 0]), int(L[0, 0])) == (hi, lo)
 
 
-def test_scale_exponent_matches_frexp():
-    vals = [1.0, 0.5, 0.75, 3.0, 1e-30, 3.4e38, f32(0x00000001), f32(0x007FFFFF), f32(0x00800000), 2.0**-127]
+def test_scale_exponent_matches_frexp_outside_the_well_scaled_band():
+    # badly scaled maxima (outside [2^-48, 2^48)) take the frexp exponent
+    vals = [1e-30, 3.4e38, f32(0x00000001), f32(0x007FFFFF), f32(0x00800000), 2.0**-127,
+            2.0**48, 2.0**-48 * (1 - 2.0**-24), 1e20]
     for v in vals:
-        assert O.scale_exponent(v) == math.frexp(float(np.float32(v)))[1]
+        assert O.scale_exponent(v) == math.frexp(float(np.float32(v)))[1], v
+    # well scaled maxima are not scaled
+    for v in [1.0, 0.5, 0.75, 3.0, 2.0**-48, 2.0**48 * (1 - 2.0**-24), 1e-14, 1e14]:
+        assert O.scale_exponent(v) == 0, v
     assert O.scale_exponent(0.0) == 0
     assert O.scale_exponent(float("inf")) == 0
     assert O.scale_exponent(float("nan")) == 0
@@ -83,13 +88,20 @@ def test_split_rows_reconstructs_and_normalises():
     L = synth.logical(X, rows, k, rows).astype(np.float64)
     hf = (hi.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     lf = (lo.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    scaled = 0
     for r in range(rows):
         amax = np.abs(L[r]).max()
-        assert e[r] == math.frexp(amax)[1]
+        if 2.0**-48 <= amax < 2.0**48:
+            assert e[r] == 0
+        else:
+            assert e[r] == math.frexp(amax)[1]
+            scaled += 1
         xs = L[r] * 2.0 ** (-int(e[r]))
-        assert 0.5 <= np.abs(xs).max() < 1.0
+        if e[r] != 0:
+            assert 0.5 <= np.abs(xs).max() < 1.0
         big = np.abs(xs) >= 2.0**-100
         assert np.all(np.abs(xs - hf[r] - lf[r])[big] <= 2.0**-17 * np.abs(xs)[big])
+    assert 0 < scaled < rows
 
 
 def test_split_operand_layouts_agree():
