@@ -141,6 +141,81 @@ int gbgemm_profile_end(gbgemm_handle* h, double* gemm_ms, int64_t* gemm_launches
 const char* gbgemm_status_string(int status);
 
 /* ---------------------------------------------------------------------- */
+/* Grouped sgemm: many independent problems, one captured CUDA graph.
+ *
+ * The BLIS driver of Section III-A divides one sgemm into small predefined
+ * multiplications for its micro-kernel; the grouped call applies the same
+ * division across problems: every problem is cut into tiles, the tiles of
+ * all problems form one work list per kernel, and persistent thread blocks
+ * drain it.  Each problem has the arguments of gbgemm_sgemm and its own
+ * configuration (path and tile shape):
+ *
+ *   GBGEMM_CFG_SIMT_128x128, _64x64, _128x64   FP32 SIMT path, CTA tile shape
+ *   GBGEMM_CFG_SPLIT_BN64, _BN128, _BN256      split-BF16 tensor path, 128 x BN
+ *                                              tiles (needs k >= 128, alpha != 0)
+ *
+ * Plan creation checks every problem (in problem order; *bad_index = the
+ * first bad problem and the return value is GBGEMM_ERR_BAD_PLAN), chooses the
+ * configurations, allocates the plan's device memory (hi/lo panels, row
+ * maxima, descriptors, work lists) and captures the graph on a private
+ * stream; it synchronises the device.  Running the plan is one
+ * cudaGraphLaunch on the caller's stream and allocates nothing.
+ *
+ * Ownership: the plan captures the A, B, C pointers given at creation; to
+ * run again on new data, write it into the same buffers.  The problems'
+ * buffers and the handle must outlive the plan.  Problems must not write
+ * overlapping parts of C (undefined otherwise).  Problems with m or n = 0,
+ * or with (alpha = 0 or k = 0) and beta = 1, are skipped; (alpha = 0 or
+ * k = 0) with another beta scales C on the SIMT path. */
+typedef struct {
+  char transa, transb;
+  int64_t m, n, k;
+  float alpha, beta;
+  const float* A; int64_t lda;
+  const float* B; int64_t ldb;
+  float* C; int64_t ldc;
+} gbgemm_problem;
+
+typedef enum {
+  GBGEMM_CFG_SIMT_128x128 = 0,
+  GBGEMM_CFG_SIMT_64x64 = 1,
+  GBGEMM_CFG_SIMT_128x64 = 2,
+  GBGEMM_CFG_SPLIT_BN64 = 3,
+  GBGEMM_CFG_SPLIT_BN128 = 4,
+  GBGEMM_CFG_SPLIT_BN256 = 5,
+  GBGEMM_NUM_CONFIGS = 6
+} gbgemm_config;
+
+typedef enum {
+  GBGEMM_CONFIG_PREDICTED = 0,  /* learned predictor, tuner as fallback */
+  GBGEMM_CONFIG_TUNED = 1,      /* exhaustive autotuner (timed on the GPU) */
+  GBGEMM_CONFIG_DEFAULT = 2     /* fixed heuristic, no timing */
+} gbgemm_config_source;
+
+typedef struct gbgemm_grouped_plan gbgemm_grouped_plan;
+
+/* probs: host array of `count` problems (device matrix pointers).
+ * config_source: a gbgemm_config_source.  On success *plan owns the plan. */
+int gbgemm_grouped_plan_create(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, int config_source,
+                               gbgemm_grouped_plan** plan, int64_t* bad_index);
+/* As gbgemm_grouped_plan_create with the configuration of every problem
+ * given (host array of `count` gbgemm_config values).  An illegal
+ * configuration for its problem is a bad problem. */
+int gbgemm_grouped_plan_create_with_configs(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count,
+                                            const int* configs, gbgemm_grouped_plan** plan, int64_t* bad_index);
+/* One cudaGraphLaunch on cuda_stream (a cudaStream_t; NULL = legacy default). */
+int gbgemm_grouped_plan_run(gbgemm_grouped_plan* plan, void* cuda_stream);
+/* Copy the configuration chosen for every problem (count ints; -1 for a
+ * skipped problem) into configs (host). */
+int gbgemm_grouped_plan_configs(const gbgemm_grouped_plan* plan, int* configs);
+/* Plan statistics (host outputs, any may be NULL): problems on the split and
+ * SIMT paths, their FLOPs (2mnk), kernels per run, device bytes held. */
+int gbgemm_grouped_plan_stats(const gbgemm_grouped_plan* plan, int64_t* n_split, int64_t* n_simt, double* flops_split,
+                              double* flops_simt, int* kernels_per_run, size_t* device_bytes);
+/* Free the plan (synchronises the device first). */
+int gbgemm_grouped_plan_destroy(gbgemm_grouped_plan* plan);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free split-BF16 sgemm.  (The paper has no counterpart: its
  * service process owns all buffers.  This entry point exists for users of
  * this library.)

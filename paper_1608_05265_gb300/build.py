@@ -19,8 +19,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbgemm.so")
-SOURCES = ["api.cu", "simt.cu", "split.cu", "noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "gbgemm.h")]
+SOURCES = ["api.cu", "simt.cu", "split.cu", "noalloc.cu", "grouped.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("internal.h", "split_device.cuh", "simt_device.cuh", "gemm_kernel.cuh",
+                                            "grouped.h")] + \
+    [os.path.join(ROOT, "include", "gbgemm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
@@ -37,7 +39,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS + [os.path.abspath(__file__)]
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [h for h in HEADERS if os.path.exists(h)] + \
+        [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -9,7 +9,10 @@
 #include <new>
 #include <vector>
 
+#include "grouped.h"
 #include "internal.h"
+
+struct gbgemm_grouped_plan : gbg::GroupedPlan {};
 
 struct gbgemm_handle {
   int device = 0;
@@ -251,6 +254,127 @@ int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, in
   DeviceGuard g(h->device);
   return gbg::launch_split_pack(rows, k, X, ldx, kcontig, amax_bits, panel, h->stream) == cudaSuccess ? GBGEMM_OK
                                                                                                       : GBGEMM_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped sgemm plans
+// ---------------------------------------------------------------------------
+namespace {
+
+int create_plan(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, const int* configs,
+                gbgemm_grouped_plan** out) {
+  gbgemm_grouped_plan* P = new (std::nothrow) gbgemm_grouped_plan();
+  if (!P) return GBGEMM_ERR_ALLOC;
+  P->device = h->device;
+  P->num_sms = h->num_sms;
+  P->status = h->d_status;
+  P->count = count;
+  P->configs = new (std::nothrow) int[count > 0 ? count : 1];
+  if (!P->configs) {
+    delete P;
+    return GBGEMM_ERR_ALLOC;
+  }
+  for (int64_t g = 0; g < count; ++g) {
+    const gbgemm_problem& q = probs[g];
+    const bool skip = q.m == 0 || q.n == 0 || (!((q.alpha != 0.0f) && (q.k > 0)) && q.beta == 1.0f);
+    P->configs[g] = skip ? -1 : configs[g];
+  }
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete[] P->configs;
+    delete P;
+    return GBGEMM_ERR_CUDA;
+  }
+  const int rc = gbg::build_grouped_plan(P, probs, count, configs, cs);
+  cudaStreamDestroy(cs);
+  if (rc != GBGEMM_OK) {
+    delete[] P->configs;
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return GBGEMM_OK;
+}
+
+int check_problems(const gbgemm_problem* probs, int64_t count, const int* configs, int64_t* bad_index) {
+  for (int64_t g = 0; g < count; ++g) {
+    if (gbg::validate_problem(probs[g]) != 0 || (configs && !gbg::config_legal(probs[g], configs[g]))) {
+      if (bad_index) *bad_index = g;
+      return GBGEMM_ERR_BAD_PLAN;
+    }
+  }
+  return GBGEMM_OK;
+}
+
+}  // namespace
+
+int gbgemm_grouped_plan_create_with_configs(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count,
+                                            const int* configs, gbgemm_grouped_plan** plan, int64_t* bad_index) {
+  if (bad_index) *bad_index = -1;
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!plan || count < 0 || (count > 0 && (!probs || !configs))) return GBGEMM_ERR_INVALID_VALUE;
+  *plan = nullptr;
+  int rc = check_problems(probs, count, configs, bad_index);
+  if (rc != GBGEMM_OK) return rc;
+  for (int64_t g = 0; g < count; ++g)
+    if (configs[g] >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
+  DeviceGuard dg(h->device);
+  return create_plan(h, probs, count, configs, plan);
+}
+
+int gbgemm_grouped_plan_create(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, int config_source,
+                               gbgemm_grouped_plan** plan, int64_t* bad_index) {
+  if (bad_index) *bad_index = -1;
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!plan || count < 0 || (count > 0 && !probs)) return GBGEMM_ERR_INVALID_VALUE;
+  if (config_source != GBGEMM_CONFIG_DEFAULT) return GBGEMM_ERR_INVALID_VALUE;
+  *plan = nullptr;
+  int rc = check_problems(probs, count, nullptr, bad_index);
+  if (rc != GBGEMM_OK) return rc;
+  std::vector<int> cfg((size_t)(count > 0 ? count : 1));
+  for (int64_t g = 0; g < count; ++g) {
+    cfg[g] = gbg::default_config(probs[g]);
+    if (cfg[g] >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h)) cfg[g] = GBGEMM_CFG_SIMT_64x64;
+  }
+  DeviceGuard dg(h->device);
+  return create_plan(h, probs, count, cfg.data(), plan);
+}
+
+int gbgemm_grouped_plan_run(gbgemm_grouped_plan* plan, void* cuda_stream) {
+  if (!plan) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!plan->exec) return GBGEMM_ERR_BAD_PLAN;
+  DeviceGuard dg(plan->device);
+  return cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? GBGEMM_OK
+                                                                                            : GBGEMM_ERR_CUDA;
+}
+
+int gbgemm_grouped_plan_configs(const gbgemm_grouped_plan* plan, int* configs) {
+  if (!plan) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!configs && plan->count > 0) return GBGEMM_ERR_INVALID_VALUE;
+  for (int64_t g = 0; g < plan->count; ++g) configs[g] = plan->configs[g];
+  return GBGEMM_OK;
+}
+
+int gbgemm_grouped_plan_stats(const gbgemm_grouped_plan* plan, int64_t* n_split, int64_t* n_simt, double* flops_split,
+                              double* flops_simt, int* kernels_per_run, size_t* device_bytes) {
+  if (!plan) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (n_split) *n_split = plan->n_split;
+  if (n_simt) *n_simt = plan->n_simt;
+  if (flops_split) *flops_split = plan->flops_split;
+  if (flops_simt) *flops_simt = plan->flops_simt;
+  if (kernels_per_run) *kernels_per_run = plan->kernels_per_run;
+  if (device_bytes) *device_bytes = plan->dbytes;
+  return GBGEMM_OK;
+}
+
+int gbgemm_grouped_plan_destroy(gbgemm_grouped_plan* plan) {
+  if (!plan) return GBGEMM_ERR_NOT_INITIALIZED;
+  DeviceGuard dg(plan->device);
+  cudaDeviceSynchronize();
+  delete[] plan->configs;
+  delete plan;
+  return GBGEMM_OK;
 }
 
 int gbgemm_get_device_status(gbgemm_handle* h, int* status) {

@@ -1,0 +1,302 @@
+// Device helpers of the split-BF16 path, shared by the single-problem
+// kernels (split.cu) and the grouped kernels (grouped.cu): scaling and
+// hi/lo splitting, panel-chunk stores, and the PTX wrappers for mbarriers,
+// bulk asynchronous copies and tcgen05 (MMA, commit, TMEM loads).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace gbg {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Shared helpers
+// ---------------------------------------------------------------------------
+
+// Scaling exponent of a K-vector from the bits of its max magnitude: 0 for
+// 0, Inf, NaN and for well-scaled maxima in [2^-48, 2^48); otherwise the
+// frexp exponent, which brings the max into [0.5, 1).
+constexpr uint32_t kWellScaledLo = (127u - 48u) << 23;  // bits of 2^-48
+constexpr uint32_t kWellScaledHi = (127u + 48u) << 23;  // bits of 2^48
+__device__ __forceinline__ int scale_exp_from_bits(uint32_t b) {
+  if (b == 0u || b >= 0x7F800000u) return 0;
+  if (b >= kWellScaledLo && b < kWellScaledHi) return 0;
+  const int E = (int)(b >> 23);
+  if (E > 0) return E - 126;
+  return (32 - __clz(b)) - 149;  // subnormal: value = b * 2^-149
+}
+
+// x * 2^-e with a single rounding (exact unless the product is subnormal).
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+  const int s = -e;  // s in [-128, 148]
+  if (s >= -126 && s <= 127) return x * __int_as_float((s + 127) << 23);
+  if (s < -126) return x * __int_as_float(1 << (s + 149));  // 2^-127, 2^-128: subnormal powers of two
+  // s > 127 only when the whole row is subnormal: both steps are exact.
+  return (x * 0x1p127f) * __int_as_float((s - 127 + 127) << 23);
+}
+
+__device__ __forceinline__ void split_bf16(float xs, uint32_t& h, uint32_t& l) {
+  const __nv_bfloat16 hb = __float2bfloat16_rn(xs);
+  h = (uint32_t)__bfloat16_as_ushort(hb);
+  if (!isfinite(xs)) { l = 0u; return; }
+  const float r = xs - __bfloat162float(hb);
+  l = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(r));
+}
+
+// ---------------------------------------------------------------------------
+// K1: split and pack.  One pass writes the hi/lo panel of the UNSCALED
+// operand and the max |x| of every K-vector (bit patterns; NaN > Inf >
+// finite as unsigned).  Well-scaled vectors (the large majority) are then
+// final.  A second, usually empty pass re-packs the badly scaled ones with
+// their scaling exponent.  For a well-scaled vector the two definitions
+// give the same GEMM result: scaling by a power of two commutes with every
+// FP32 rounding as long as nothing leaves the normal range.
+//
+// Thread work item: one row r of a 128-row x 32-k block and one 8-wide
+// k-chunk cc (0..3) -> two 16-byte stores (hi chunk cc, lo chunk cc + 4) at
+// chunk positions XOR (r mod 8).
+// ---------------------------------------------------------------------------
+
+// Split 8 values (already scaled) and store the hi and lo chunks of row rr.
+__device__ __forceinline__ void store_split8(uint8_t* blk, int rr, int cc, const float (&x)[8]) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t h0, l0, h1, l1;
+    split_bf16(x[2 * q], h0, l0);
+    split_bf16(x[2 * q + 1], h1, l1);
+    hw[q] = h0 | (h1 << 16);
+    lw[q] = l0 | (l1 << 16);
+  }
+  const int sw = rr & 7;
+  *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// Item mapping inside a 256-thread CTA, two items per thread.
+// KCONTIG (element (r,p) at X[r*ld + p]): four lanes per row, eight rows per
+//   warp, so a warp reads eight 128-byte row segments.
+// !KCONTIG (element (r,p) at X[r + p*ld]): 32 consecutive rows per warp and
+//   one chunk per warp, so every load instruction reads 128 contiguous bytes.
+template <bool KCONTIG>
+__device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
+  if (KCONTIG) {
+    const int idx = tid + 256 * it;
+    rr = idx >> 2;
+    cc = idx & 3;
+  } else {
+    const int w = tid >> 5;
+    cc = w & 3;
+    rr = ((w >> 2) + 2 * it) * 32 + (tid & 31);
+  }
+}
+
+template <bool KCONTIG>
+__device__ __forceinline__ void load8(const float* __restrict__ X, int64_t ld, int64_t r, int64_t p, int64_t rows,
+                                      int64_t k, bool vec, float (&x)[8]) {
+  if (KCONTIG) {
+    if (r < rows && vec && p + 8 <= k) {
+      const float4 a = *reinterpret_cast<const float4*>(X + r * ld + p);
+      const float4 b = *reinterpret_cast<const float4*>(X + r * ld + p + 4);
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = (r < rows && p + q < k) ? X[r * ld + p + q] : 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = (r < rows && p + q < k) ? X[r + (p + q) * ld] : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers (tcgen05, bulk copy, mbarrier)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Wait for the phase of parity `parity` to complete.  Gives up (returns
+// false) once `timeout_ns` has passed or another role raised the abort flag.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t timeout_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 31u) == 0u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > timeout_ns) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile whose rows are
+// 128 bytes, 8-row groups 1024 bytes apart, 128-byte swizzle.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4)   // start address
+         | ((uint64_t)1 << 16)                 // leading byte offset (unused for swizzled K-major)
+         | ((uint64_t)(1024 >> 4) << 32)       // stride byte offset: 8 rows x 128 B
+         | ((uint64_t)1 << 46)                 // descriptor version
+         | ((uint64_t)2 << 61);                // 128-byte swizzle
+}
+
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N) {
+  return (1u << 4)                 // D format FP32
+         | (1u << 7)               // A format BF16
+         | (1u << 10)              // B format BF16
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void raise_status(int* status, volatile int* abort_flag) {
+  *abort_flag = 1;
+  atomicCAS(status, 0, (int)GBGEMM_ERR_DEVICE_TIMEOUT);
+}
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group, int& tm, int& tn) {
+  const int per_group = group * tiles_n;
+  const int g = t / per_group;
+  const int first_m = g * group;
+  const int gm = min(group, tiles_m - first_m);
+  const int r = t - g * per_group;
+  tm = first_m + r % gm;
+  tn = r / gm;
+}
+
+// Pack rows 128*rb .. +127 of k chunk kc of one operand (256 threads).  The
+// panel holds `rows_alloc` rows (a multiple of 8) per k chunk: row r of
+// chunk kc is the 128 bytes at (kc*rows_alloc + r)*128.  Rows from `rows`
+// up to rows_alloc are written as zeros, rows past rows_alloc not at all.
+// smax: 128 words of shared memory.
+template <bool KCONTIG>
+__device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
+                                           uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
+                                           int64_t rows_alloc, int64_t rb, int64_t kc, uint32_t* smax) {
+  const int64_t r0 = rb * 128, p0 = kc * 32;
+  const int tid = threadIdx.x;
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  if (tid < 128) smax[tid] = 0u;
+  float x[2][8];
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {  // all loads first: 16 (or 4 vector) loads in flight per thread
+    int rr, cc;
+    item_of<KCONTIG>(tid, it, rr, cc);
+    load8<KCONTIG>(X, ld, r0 + rr, p0 + cc * 8, rows, k, vec, x[it]);
+  }
+  __syncthreads();
+  uint8_t* blk = panel + ((size_t)kc * rows_alloc + r0) * 128;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    int rr, cc;
+    item_of<KCONTIG>(tid, it, rr, cc);
+    uint32_t mx = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) mx = max(mx, __float_as_uint(x[it][q]) & 0x7FFFFFFFu);
+    if (r0 + rr < rows_alloc) store_split8(blk, rr, cc, x[it]);
+    if (KCONTIG) {
+      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
+      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
+      if (cc == 0 && mx != 0u) atomicMax(&smax[rr], mx);
+    } else if (mx != 0u) {
+      atomicMax(&smax[rr], mx);
+    }
+  }
+  __syncthreads();
+  if (tid < 128 && r0 + tid < rows && smax[tid] != 0u) atomicMax(&amax[r0 + tid], smax[tid]);
+}
+
+// Re-pack the badly scaled K-vectors of one 128-row block over all k chunks
+// with x' = x * 2^-e.  A block without such rows returns at once.
+__device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
+                                              bool kcontig, const uint32_t* __restrict__ amax,
+                                              uint8_t* __restrict__ panel, int64_t rows_alloc, int64_t nkc,
+                                              int64_t rb, int* se) {
+  const int64_t r0 = rb * 128;
+  const int tid = threadIdx.x;
+  int e = 0;
+  if (tid < 128 && r0 + tid < rows) e = scale_exp_from_bits(amax[r0 + tid]);
+  if (tid < 128) se[tid] = e;
+  if (!__syncthreads_or(e != 0)) return;
+  for (int64_t kc = 0; kc < nkc; ++kc) {
+    uint8_t* blk = panel + ((size_t)kc * rows_alloc + r0) * 128;
+    for (int it = 0; it < 2; ++it) {
+      const int idx = tid + 256 * it, rr = idx >> 2, cc = idx & 3;
+      const int er = se[rr];
+      if (er == 0) continue;
+      const int64_t r = r0 + rr, p = kc * 32 + cc * 8;
+      float x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float v = (r < rows && p + q < k) ? (kcontig ? X[r * ld + p + q] : X[r + (p + q) * ld]) : 0.f;
+        x[q] = isfinite(v) ? scale_pow2(v, er) : v;
+      }
+      store_split8(blk, rr, cc, x);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace gbg

@@ -33,12 +33,36 @@ PATH_AUTO = 0
 PATH_SIMT = 1
 PATH_SPLIT_BF16 = 2
 
+CFG_SIMT_128x128 = 0
+CFG_SIMT_64x64 = 1
+CFG_SIMT_128x64 = 2
+CFG_SPLIT_BN64 = 3
+CFG_SPLIT_BN128 = 4
+CFG_SPLIT_BN256 = 5
+NUM_CONFIGS = 6
+
+CONFIG_PREDICTED = 0
+CONFIG_TUNED = 1
+CONFIG_DEFAULT = 2
+
+
+class Problem(ctypes.Structure):
+    """gbgemm_problem (include/gbgemm.h)."""
+    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
 #: Symbols exported by libgbgemm.so, as declared in include/gbgemm.h.
 EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_get_device_status",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
-    "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc",
+    "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
+    "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run", "gbgemm_grouped_plan_configs",
+    "gbgemm_grouped_plan_stats", "gbgemm_grouped_plan_destroy",
 ]
 
 _lock = threading.Lock()
@@ -77,13 +101,27 @@ def lib():
             L.gbgemm_split_pack.argtypes = [vp, c, c, i64, i64, vp, i64, vp, vp]
             L.gbgemm_sgemm_split_noalloc.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64,
                                                      vp]
+            PP = ctypes.POINTER(Problem)
+            L.gbgemm_grouped_plan_create.argtypes = [vp, PP, i64, ctypes.c_int, ctypes.POINTER(vp),
+                                                     ctypes.POINTER(i64)]
+            L.gbgemm_grouped_plan_create_with_configs.argtypes = [vp, PP, i64, ctypes.POINTER(ctypes.c_int),
+                                                                  ctypes.POINTER(vp), ctypes.POINTER(i64)]
+            L.gbgemm_grouped_plan_run.argtypes = [vp, vp]
+            L.gbgemm_grouped_plan_configs.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            L.gbgemm_grouped_plan_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
+            L.gbgemm_grouped_plan_destroy.argtypes = [vp]
             L.gbgemm_profile_begin.argtypes = [vp]
             L.gbgemm_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                              ctypes.POINTER(i64)]
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
                          "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
-                         "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc"):
+                         "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
+                         "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
+                         "gbgemm_grouped_plan_configs", "gbgemm_grouped_plan_stats",
+                         "gbgemm_grouped_plan_destroy"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -182,6 +220,78 @@ class Handle:
     def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
         return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),
                                        _ptr(amax_bits), _ptr(panel))
+
+
+class GroupedPlan:
+    """Owns a gbgemm_grouped_plan; methods forward to the C functions of the same name."""
+
+    def __init__(self, handle: "Handle", problems, config_source: int = CONFIG_DEFAULT, configs=None):
+        arr = (Problem * max(len(problems), 1))(*problems)
+        p = ctypes.c_void_p()
+        bad = ctypes.c_int64(-1)
+        if configs is not None:
+            carr = (ctypes.c_int * max(len(configs), 1))(*configs)
+            rc = lib().gbgemm_grouped_plan_create_with_configs(handle.ptr, arr, len(problems), carr, ctypes.byref(p),
+                                                               ctypes.byref(bad))
+        else:
+            rc = lib().gbgemm_grouped_plan_create(handle.ptr, arr, len(problems), int(config_source), ctypes.byref(p),
+                                                  ctypes.byref(bad))
+        self.bad_index = bad.value
+        _check("gbgemm_grouped_plan_create", rc)
+        self._p = p
+        self.count = len(problems)
+
+    def run(self, stream=None):
+        _check("gbgemm_grouped_plan_run", lib().gbgemm_grouped_plan_run(self._p, _stream_ptr(stream)))
+
+    def configs(self):
+        arr = (ctypes.c_int * max(self.count, 1))()
+        _check("gbgemm_grouped_plan_configs", lib().gbgemm_grouped_plan_configs(self._p, arr))
+        return list(arr)[: self.count]
+
+    def stats(self):
+        ns, nm = ctypes.c_int64(), ctypes.c_int64()
+        fs, fm = ctypes.c_double(), ctypes.c_double()
+        kr, db = ctypes.c_int(), ctypes.c_size_t()
+        _check("gbgemm_grouped_plan_stats", lib().gbgemm_grouped_plan_stats(
+            self._p, ctypes.byref(ns), ctypes.byref(nm), ctypes.byref(fs), ctypes.byref(fm), ctypes.byref(kr),
+            ctypes.byref(db)))
+        return {"n_split": ns.value, "n_simt": nm.value, "flops_split": fs.value, "flops_simt": fm.value,
+                "kernels_per_run": kr.value, "device_bytes": db.value}
+
+    def close(self):
+        if getattr(self, "_p", None) is not None and self._p.value:
+            lib().gbgemm_grouped_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_plan_status(handle, problems, config_source=CONFIG_DEFAULT, configs=None):
+    """(status, bad_index) of a plan creation attempt; the plan, if any, is destroyed at once."""
+    arr = (Problem * max(len(problems), 1))(*problems)
+    p = ctypes.c_void_p()
+    bad = ctypes.c_int64(-1)
+    if configs is not None:
+        carr = (ctypes.c_int * max(len(configs), 1))(*configs)
+        rc = lib().gbgemm_grouped_plan_create_with_configs(handle.ptr, arr, len(problems), carr, ctypes.byref(p),
+                                                           ctypes.byref(bad))
+    else:
+        rc = lib().gbgemm_grouped_plan_create(handle.ptr, arr, len(problems), int(config_source), ctypes.byref(p),
+                                              ctypes.byref(bad))
+    if rc == OK and p.value:
+        lib().gbgemm_grouped_plan_destroy(p)
+    return rc, bad.value
+
+
+def problem(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc) -> Problem:
+    """A gbgemm_problem from tensors (or raw device addresses)."""
+    return Problem(transa.encode(), transb.encode(), int(m), int(n), int(k), float(alpha), float(beta),
+                   _ptr(A), int(lda), _ptr(B), int(ldb), _ptr(C), int(ldc))
 
 
 def sgemm_split_noalloc(stream, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, status=None) -> int:
