@@ -216,6 +216,75 @@ int gbgemm_grouped_plan_stats(const gbgemm_grouped_plan* plan, int64_t* n_split,
 int gbgemm_grouped_plan_destroy(gbgemm_grouped_plan* plan);
 
 /* ---------------------------------------------------------------------- */
+/* Autotuner.  The paper fixes its micro-kernel sizes at compile time
+ * (Sections III-C, III-D); here every legal configuration (gbgemm_config) of
+ * a problem shape is timed on the GPU -- CUDA events, one warm-up, the median
+ * of `reps` runs -- on scratch buffers owned by the handle (same leading
+ * dimensions and 16-byte alignment as the problem; the problem's own data is
+ * never touched), and the result is cached in the handle under the key
+ * (m, n, k, transposes, alignment classes of A, B, C).
+ *
+ * Two figures per configuration (microseconds, -1 when illegal):
+ *   latency  one call on that problem alone;
+ *   cost     GPU time per problem inside a grouped batch: a grouped plan of
+ *            R copies of the problem (enough to fill every SM twice, at most
+ *            256) is replayed and cost = replay time / R.  Used to rank
+ *            configurations for grouped plans.
+ * gbgemm_autotune synchronises the handle's stream; it must not run during
+ * stream capture.  Any output pointer may be NULL. */
+int gbgemm_autotune(gbgemm_handle* h, const gbgemm_problem* prob, int reps, float* latency_us, float* cost_us,
+                    int* best_by_latency, int* best_by_cost);
+/* Cache persistence: a text file, one line per shape key. */
+int gbgemm_tuning_save(gbgemm_handle* h, const char* path);
+int gbgemm_tuning_load(gbgemm_handle* h, const char* path);
+int gbgemm_tuning_clear(gbgemm_handle* h);
+/* mode 0 (default): gbgemm_sgemm picks its tile configuration by a fixed
+ * heuristic.  mode 1: by the tuner's lowest latency among the legal
+ * configurations of the handle's path (tuning a new shape on first use,
+ * which synchronises; do it before any stream capture). */
+int gbgemm_set_tuning(gbgemm_handle* h, int mode);
+
+/* ---------------------------------------------------------------------- */
+/* Learned configuration predictor: a 3-layer MLP (8 -> 64 -> 64 -> 6, ReLU,
+ * FP32) trained on the autotuner's timings, so that grouped plans can choose
+ * configurations without timing every problem (GBGEMM_CONFIG_PREDICTED).  The
+ * paper picks its micro-kernel parameters by hand (Section III-C).
+ *
+ * Inputs (gbgemm_predictor_features): log2(m)/14, log2(n)/14, log2(k)/14,
+ * transa, transb (0 = N, 1 = T), and the 16-byte alignment class of A, B, C
+ * (1 when ld % 4 == 0 and the pointer is 16-byte aligned).  Outputs: the
+ * predicted log2(cost_c / cost_best) of each gbgemm_config c.  Parameters,
+ * one FP32 array of GBGEMM_MLP_PARAMS: W1[64][8], b1[64], W2[64][64], b2[64],
+ * W3[6][64], b3[6] (row = output unit).  Loss: mean over samples and legal
+ * configurations of (output - target)^2.
+ *
+ * x, y, mask, legal, scores, configs, grad below are DEVICE arrays:
+ *   x[n][8] features, y[n][6] targets, mask[n][6] (1 legal / 0 illegal),
+ *   legal[n] bit c set when configuration c may be chosen.
+ * Grouped plans predict only for shapes inside the training range (every
+ * dimension in [8, 16384]); other shapes, or a handle without parameters,
+ * use the tuner. */
+#define GBGEMM_MLP_PARAMS 5126
+int gbgemm_predictor_set(gbgemm_handle* h, const float* params /* host */);
+int gbgemm_predictor_get(gbgemm_handle* h, float* params /* host */);
+int gbgemm_predictor_features(const gbgemm_problem* prob, float* x /* host, 8 floats */);
+/* Batched inference on the handle's stream: scores (n x 6, may be NULL) and
+ * the lowest-scoring legal configuration per sample (-1 if none). */
+int gbgemm_predictor_predict(gbgemm_handle* h, const float* x, const uint8_t* legal, int64_t n, float* scores,
+                             int* configs);
+/* Loss and gradient of the mean loss (GBGEMM_MLP_PARAMS floats into grad)
+ * for n <= 256 samples; synchronises. */
+int gbgemm_predictor_loss_grad(gbgemm_handle* h, const float* x, const float* y, const float* mask, int64_t n,
+                               float* loss /* host */, float* grad);
+/* Train the handle's predictor with Adam (beta1 0.9, beta2 0.999, eps 1e-8)
+ * on mini-batches of `batch` <= 256 samples, reshuffled every epoch from
+ * `seed`; starts from He-uniform weights when none are set.  *final_loss
+ * (host, may be NULL) = loss of the final parameters on all n samples.
+ * Synchronises. */
+int gbgemm_predictor_train(gbgemm_handle* h, const float* x, const float* y, const float* mask, int64_t n, int epochs,
+                           int batch, float lr, uint64_t seed, float* final_loss);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free split-BF16 sgemm.  (The paper has no counterpart: its
  * service process owns all buffers.  This entry point exists for users of
  * this library.)

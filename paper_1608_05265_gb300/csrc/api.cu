@@ -11,6 +11,8 @@
 
 #include "grouped.h"
 #include "internal.h"
+#include "mlp.h"
+#include "tuner.h"
 
 struct gbgemm_grouped_plan : gbg::GroupedPlan {};
 
@@ -30,6 +32,10 @@ struct gbgemm_handle {
   size_t ev_used = 0;                // events recorded in this profiling window
   int64_t gemm_launches = 0;
   int64_t kernel_launches = 0;
+  // tuning
+  int tuning = 0;
+  gbg::Tuner tuner;
+  gbg::Predictor predictor;
 };
 
 namespace {
@@ -204,8 +210,32 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   int path = h->path;
   if (path == GBGEMM_PATH_AUTO) path = (k >= gbg::kSplitMinK && split_supported(h)) ? GBGEMM_PATH_SPLIT_BF16 : GBGEMM_PATH_SIMT;
   gbg::Problem p{ta, tb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
+  int simt_cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
+  int split_bn = 256;
+  if (h->tuning == 1) {
+    const gbgemm_problem q{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
+    gbg::TuneResult r;
+    h->tuner.bind(h->stream, h->d_status, h->num_sms);
+    if (h->tuner.measure(q, 3, &r) != GBGEMM_OK) return GBGEMM_ERR_CUDA;
+    int best = -1;
+    for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c) {
+      if (r.latency_us[c] < 0.f) continue;
+      const bool is_split = c >= GBGEMM_CFG_SPLIT_BN64;
+      if (h->path == GBGEMM_PATH_SIMT && is_split) continue;
+      if (h->path == GBGEMM_PATH_SPLIT_BF16 && !is_split) continue;
+      if (is_split && !split_supported(h)) continue;
+      if (best < 0 || r.latency_us[c] < r.latency_us[best]) best = c;
+    }
+    if (best >= GBGEMM_CFG_SPLIT_BN64) {
+      path = GBGEMM_PATH_SPLIT_BF16;
+      split_bn = best == GBGEMM_CFG_SPLIT_BN64 ? 64 : best == GBGEMM_CFG_SPLIT_BN128 ? 128 : 256;
+    } else if (best >= 0) {
+      path = GBGEMM_PATH_SIMT;
+      simt_cfg = best;
+    }
+  }
   if (path == GBGEMM_PATH_SIMT) {
-    const int cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
+    const int cfg = simt_cfg;
     if (gbg::launch_simt(p, cfg, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
     h->kernel_launches += 1;
     h->last_path = GBGEMM_PATH_SIMT;
@@ -229,8 +259,8 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   a.panelA = panelA; a.panelB = panelB; a.amaxA = amaxA; a.amaxB = amaxB;
   a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
   a.status = h->d_status; a.num_sms = h->num_sms;
-  a.bn = 256; a.raster = 16;
-  h->kernel_launches += 4;  // two row-maximum and two packing kernels
+  a.bn = split_bn; a.raster = 16;
+  h->kernel_launches += 4;  // two packing and two re-packing kernels
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (gbg::launch_split_gemm(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
@@ -297,6 +327,93 @@ int create_plan(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, co
   return GBGEMM_OK;
 }
 
+// Configuration of every problem: the default heuristic, the tuner's lowest
+// cost, or the learned predictor (falling back to the tuner).
+uint8_t legal_mask(const gbgemm_handle* h, const gbgemm_problem& q) {
+  uint8_t m = 0;
+  for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c)
+    if (gbg::config_legal(q, c) && !(c >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h))) m |= (uint8_t)(1u << c);
+  return m;
+}
+
+bool in_training_range(const gbgemm_problem& q) {
+  auto ok = [](int64_t v) { return v >= 8 && v <= 16384; };
+  return ok(q.m) && ok(q.n) && ok(q.k);
+}
+
+// Predicted configurations of the problems flagged in `want` (-1 where the
+// predictor is not used).
+int predict_configs(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, std::vector<char>& want,
+                    std::vector<int>& out) {
+  std::vector<float> x;
+  std::vector<uint8_t> legal;
+  std::vector<int64_t> which;
+  for (int64_t g = 0; g < count; ++g) {
+    if (!want[g]) continue;
+    float f[8];
+    gbg::predictor_features(probs[g], f);
+    x.insert(x.end(), f, f + 8);
+    legal.push_back(legal_mask(h, probs[g]));
+    which.push_back(g);
+  }
+  out.assign((size_t)count, -1);
+  const int64_t n = (int64_t)which.size();
+  if (n == 0) return GBGEMM_OK;
+  void* d = nullptr;
+  const size_t bx = (size_t)n * 8 * sizeof(float), bl = ((size_t)n + 255) / 256 * 256, bc = (size_t)n * sizeof(int);
+  if (cudaMalloc(&d, bx + bl + bc) != cudaSuccess) {
+    cudaGetLastError();
+    return GBGEMM_ERR_ALLOC;
+  }
+  float* dx = static_cast<float*>(d);
+  uint8_t* dl = reinterpret_cast<uint8_t*>(static_cast<char*>(d) + bx);
+  int* dc = reinterpret_cast<int*>(static_cast<char*>(d) + bx + bl);
+  std::vector<int> cfg((size_t)n);
+  int rc = GBGEMM_ERR_CUDA;
+  if (cudaMemcpy(dx, x.data(), bx, cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaMemcpy(dl, legal.data(), (size_t)n, cudaMemcpyHostToDevice) == cudaSuccess) {
+    rc = h->predictor.predict(dx, dl, n, nullptr, dc, h->stream);
+    if (rc == GBGEMM_OK && (cudaMemcpyAsync(cfg.data(), dc, bc, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+                            cudaStreamSynchronize(h->stream) != cudaSuccess))
+      rc = GBGEMM_ERR_CUDA;
+  }
+  cudaFree(d);
+  if (rc != GBGEMM_OK) return rc;
+  for (int64_t i = 0; i < n; ++i) out[(size_t)which[i]] = cfg[(size_t)i];
+  return GBGEMM_OK;
+}
+
+int choose_configs(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, int source, int* cfg) {
+  std::vector<int> predicted;
+  if (source == GBGEMM_CONFIG_PREDICTED && h->predictor.ready()) {
+    std::vector<char> want((size_t)count, 0);
+    for (int64_t g = 0; g < count; ++g) {
+      const gbgemm_problem& q = probs[g];
+      const bool skip = q.m == 0 || q.n == 0 || !((q.alpha != 0.0f) && (q.k > 0));
+      want[g] = !skip && in_training_range(q);
+    }
+    const int rc = predict_configs(h, probs, count, want, predicted);
+    if (rc != GBGEMM_OK) return rc;
+  }
+  for (int64_t g = 0; g < count; ++g) {
+    const gbgemm_problem& q = probs[g];
+    const bool skip = q.m == 0 || q.n == 0 || !((q.alpha != 0.0f) && (q.k > 0));
+    cfg[g] = gbg::default_config(q);
+    if (!skip && source == GBGEMM_CONFIG_PREDICTED && !predicted.empty() && predicted[g] >= 0) {
+      cfg[g] = predicted[g];
+    } else if (!skip && source != GBGEMM_CONFIG_DEFAULT) {
+      gbg::TuneResult r;
+      h->tuner.bind(h->stream, h->d_status, h->num_sms);
+      const int rc = h->tuner.measure(q, 3, &r);
+      if (rc != GBGEMM_OK) return rc;
+      const int b = gbg::best_config(r, true);
+      if (b >= 0) cfg[g] = b;
+    }
+    if (cfg[g] >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h)) cfg[g] = GBGEMM_CFG_SIMT_128x128;
+  }
+  return GBGEMM_OK;
+}
+
 int check_problems(const gbgemm_problem* probs, int64_t count, const int* configs, int64_t* bad_index) {
   for (int64_t g = 0; g < count; ++g) {
     if (gbg::validate_problem(probs[g]) != 0 || (configs && !gbg::config_legal(probs[g], configs[g]))) {
@@ -328,16 +445,16 @@ int gbgemm_grouped_plan_create(gbgemm_handle* h, const gbgemm_problem* probs, in
   if (bad_index) *bad_index = -1;
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!plan || count < 0 || (count > 0 && !probs)) return GBGEMM_ERR_INVALID_VALUE;
-  if (config_source != GBGEMM_CONFIG_DEFAULT) return GBGEMM_ERR_INVALID_VALUE;
+  if (config_source != GBGEMM_CONFIG_DEFAULT && config_source != GBGEMM_CONFIG_TUNED &&
+      config_source != GBGEMM_CONFIG_PREDICTED)
+    return GBGEMM_ERR_INVALID_VALUE;
   *plan = nullptr;
   int rc = check_problems(probs, count, nullptr, bad_index);
   if (rc != GBGEMM_OK) return rc;
-  std::vector<int> cfg((size_t)(count > 0 ? count : 1));
-  for (int64_t g = 0; g < count; ++g) {
-    cfg[g] = gbg::default_config(probs[g]);
-    if (cfg[g] >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h)) cfg[g] = GBGEMM_CFG_SIMT_64x64;
-  }
   DeviceGuard dg(h->device);
+  std::vector<int> cfg((size_t)(count > 0 ? count : 1));
+  rc = choose_configs(h, probs, count, config_source, cfg.data());
+  if (rc != GBGEMM_OK) return rc;
   return create_plan(h, probs, count, cfg.data(), plan);
 }
 
@@ -374,6 +491,95 @@ int gbgemm_grouped_plan_destroy(gbgemm_grouped_plan* plan) {
   cudaDeviceSynchronize();
   delete[] plan->configs;
   delete plan;
+  return GBGEMM_OK;
+}
+
+int gbgemm_autotune(gbgemm_handle* h, const gbgemm_problem* prob, int reps, float* latency_us, float* cost_us,
+                    int* best_by_latency, int* best_by_cost) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!prob || reps < 1) return GBGEMM_ERR_INVALID_VALUE;
+  if (gbg::validate_problem(*prob) != 0 || prob->m == 0 || prob->n == 0) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  gbg::TuneResult r;
+  h->tuner.bind(h->stream, h->d_status, h->num_sms);
+  const int rc = h->tuner.measure(*prob, reps, &r);
+  if (rc != GBGEMM_OK) return rc;
+  for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c) {
+    const bool usable = !(c >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h));
+    if (latency_us) latency_us[c] = usable ? r.latency_us[c] : -1.f;
+    if (cost_us) cost_us[c] = usable ? r.cost_us[c] : -1.f;
+  }
+  if (best_by_latency) *best_by_latency = gbg::best_config(r, false);
+  if (best_by_cost) *best_by_cost = gbg::best_config(r, true);
+  return GBGEMM_OK;
+}
+
+int gbgemm_predictor_set(gbgemm_handle* h, const float* params) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!params) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  return h->predictor.set(params);
+}
+
+int gbgemm_predictor_get(gbgemm_handle* h, float* params) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!params) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  return h->predictor.get(params);
+}
+
+int gbgemm_predictor_features(const gbgemm_problem* prob, float* x) {
+  if (!prob || !x) return GBGEMM_ERR_INVALID_VALUE;
+  gbg::predictor_features(*prob, x);
+  return GBGEMM_OK;
+}
+
+int gbgemm_predictor_predict(gbgemm_handle* h, const float* x, const uint8_t* legal, int64_t n, float* scores,
+                             int* configs) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (n < 0 || (n > 0 && !x)) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  return h->predictor.predict(x, legal, n, scores, configs, h->stream);
+}
+
+int gbgemm_predictor_loss_grad(gbgemm_handle* h, const float* x, const float* y, const float* mask, int64_t n,
+                               float* loss, float* grad) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!x || !y || !mask || !grad) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  return h->predictor.loss_grad(x, y, mask, n, loss, grad, h->stream);
+}
+
+int gbgemm_predictor_train(gbgemm_handle* h, const float* x, const float* y, const float* mask, int64_t n, int epochs,
+                           int batch, float lr, uint64_t seed, float* final_loss) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!x || !y || !mask) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  return h->predictor.train(x, y, mask, n, epochs, batch, lr, seed, final_loss, h->stream);
+}
+
+int gbgemm_tuning_save(gbgemm_handle* h, const char* path) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!path) return GBGEMM_ERR_INVALID_VALUE;
+  return h->tuner.save(path);
+}
+
+int gbgemm_tuning_load(gbgemm_handle* h, const char* path) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!path) return GBGEMM_ERR_INVALID_VALUE;
+  return h->tuner.load(path);
+}
+
+int gbgemm_tuning_clear(gbgemm_handle* h) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  h->tuner.cache.clear();
+  return GBGEMM_OK;
+}
+
+int gbgemm_set_tuning(gbgemm_handle* h, int mode) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (mode != 0 && mode != 1) return GBGEMM_ERR_INVALID_VALUE;
+  h->tuning = mode;
   return GBGEMM_OK;
 }
 

@@ -298,8 +298,33 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   // ---- capture the graph ----
   if (blocks > 0x7FFFFFFF || rowblocks > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
   if (!gdev.empty() && ensure_gemm_smem_attr<GroupedSched>() != cudaSuccess) return GBGEMM_ERR_CUDA;
-  if (cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  cudaError_t e = cudaSuccess;
+  // The SIMT launches run on side branches of the graph, concurrently with
+  // the (memory-bound) split-path chain on the main branch.
+  constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, joins[kSide] = {};
+  bool res_ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < kSide && res_ok; ++i)
+    res_ok = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming) == cudaSuccess;
+  auto release = [&]() {
+    for (int i = 0; i < kSide; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (joins[i]) cudaEventDestroy(joins[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  };
+  if (!res_ok) {
+    cudaGetLastError();
+    release();
+    return GBGEMM_ERR_CUDA;
+  }
+  if (cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    release();
+    return GBGEMM_ERR_CUDA;
+  }
+  cudaError_t e = cudaEventRecord(fork, capture_stream);
+  for (int i = 0; i < kSide && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[i], fork, 0);
   if (!gdev.empty()) {
     const PackTask* dt = reinterpret_cast<const PackTask*>(base + tasks_r.off);
     e = cudaMemsetAsync(amax_base, 0, (size_t)amax_words * 4, capture_stream);
@@ -327,14 +352,20 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     const int4* di = reinterpret_cast<const int4*>(base + simt_items_r[cv].off);
     const int per_sm = (c == GBGEMM_CFG_SIMT_128x128) ? 2 : 4;
     const int grid = (int)std::min<int64_t>(n, (int64_t)P->num_sms * per_sm);
-    if (c == GBGEMM_CFG_SIMT_128x128) launch_grouped_simt<128, 128>(variant, grid, capture_stream, di, n, dprobs);
-    else if (c == GBGEMM_CFG_SIMT_64x64) launch_grouped_simt<64, 64>(variant, grid, capture_stream, di, n, dprobs);
-    else launch_grouped_simt<128, 64>(variant, grid, capture_stream, di, n, dprobs);
+    cudaStream_t st = side[P->kernels_per_run % kSide];
+    if (c == GBGEMM_CFG_SIMT_128x128) launch_grouped_simt<128, 128>(variant, grid, st, di, n, dprobs);
+    else if (c == GBGEMM_CFG_SIMT_64x64) launch_grouped_simt<64, 64>(variant, grid, st, di, n, dprobs);
+    else launch_grouped_simt<128, 64>(variant, grid, st, di, n, dprobs);
     P->kernels_per_run += 1;
+  }
+  for (int i = 0; i < kSide && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(joins[i], side[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(capture_stream, joins[i], 0);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(capture_stream, &g);
+  release();
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();

@@ -28,6 +28,7 @@ ERR_BAD_PLAN = -105
 ERR_INVALID_VALUE = -106
 ERR_SCRATCH_LIMIT = -107
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+MLP_PARAMS = 5126
 
 PATH_AUTO = 0
 PATH_SIMT = 1
@@ -62,7 +63,10 @@ EXPORTS = [
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
     "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
     "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run", "gbgemm_grouped_plan_configs",
-    "gbgemm_grouped_plan_stats", "gbgemm_grouped_plan_destroy",
+    "gbgemm_grouped_plan_stats", "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
+    "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
+    "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
+    "gbgemm_predictor_loss_grad", "gbgemm_predictor_train",
 ]
 
 _lock = threading.Lock()
@@ -112,6 +116,20 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
             L.gbgemm_grouped_plan_destroy.argtypes = [vp]
+            fp = ctypes.POINTER(ctypes.c_float)
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.gbgemm_autotune.argtypes = [vp, PP, ctypes.c_int, fp, fp, ip, ip]
+            L.gbgemm_tuning_save.argtypes = [vp, ctypes.c_char_p]
+            L.gbgemm_tuning_load.argtypes = [vp, ctypes.c_char_p]
+            L.gbgemm_tuning_clear.argtypes = [vp]
+            L.gbgemm_set_tuning.argtypes = [vp, ctypes.c_int]
+            L.gbgemm_predictor_set.argtypes = [vp, vp]
+            L.gbgemm_predictor_get.argtypes = [vp, vp]
+            L.gbgemm_predictor_features.argtypes = [PP, fp]
+            L.gbgemm_predictor_predict.argtypes = [vp, vp, vp, i64, vp, vp]
+            L.gbgemm_predictor_loss_grad.argtypes = [vp, vp, vp, vp, i64, fp, vp]
+            L.gbgemm_predictor_train.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                                 ctypes.c_uint64, fp]
             L.gbgemm_profile_begin.argtypes = [vp]
             L.gbgemm_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                              ctypes.POINTER(i64)]
@@ -121,7 +139,10 @@ def lib():
                          "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
                          "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
                          "gbgemm_grouped_plan_configs", "gbgemm_grouped_plan_stats",
-                         "gbgemm_grouped_plan_destroy"):
+                         "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
+                         "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
+                         "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
+                         "gbgemm_predictor_loss_grad", "gbgemm_predictor_train"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -217,6 +238,58 @@ class Handle:
                                                               ctypes.byref(k)))
         return ms.value, g.value, k.value
 
+    def autotune(self, prob: "Problem", reps: int = 3):
+        """(latency_us[6], cost_us[6], best_by_latency, best_by_cost); -1 marks illegal configurations."""
+        lat = (ctypes.c_float * NUM_CONFIGS)()
+        cost = (ctypes.c_float * NUM_CONFIGS)()
+        bl, bc = ctypes.c_int(), ctypes.c_int()
+        _check("gbgemm_autotune", lib().gbgemm_autotune(self._h, ctypes.byref(prob), int(reps), lat, cost,
+                                                        ctypes.byref(bl), ctypes.byref(bc)))
+        return list(lat), list(cost), bl.value, bc.value
+
+    def tuning_save(self, path: str):
+        _check("gbgemm_tuning_save", lib().gbgemm_tuning_save(self._h, path.encode()))
+
+    def tuning_load(self, path: str):
+        _check("gbgemm_tuning_load", lib().gbgemm_tuning_load(self._h, path.encode()))
+
+    def tuning_clear(self):
+        _check("gbgemm_tuning_clear", lib().gbgemm_tuning_clear(self._h))
+
+    def set_tuning(self, mode: int):
+        _check("gbgemm_set_tuning", lib().gbgemm_set_tuning(self._h, int(mode)))
+
+    def predictor_set(self, params):
+        import numpy as np
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        assert arr.size == MLP_PARAMS
+        _check("gbgemm_predictor_set", lib().gbgemm_predictor_set(self._h, arr.ctypes.data))
+
+    def predictor_get(self):
+        import numpy as np
+        arr = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check("gbgemm_predictor_get", lib().gbgemm_predictor_get(self._h, arr.ctypes.data))
+        return arr
+
+    def predictor_predict(self, x, legal, scores=None, configs=None):
+        """Device tensors: x (n x 8 float32), legal (n uint8); fills scores (n x 6) and configs (n int32)."""
+        n = int(x.shape[0])
+        _check("gbgemm_predictor_predict", lib().gbgemm_predictor_predict(
+            self._h, _ptr(x), _ptr(legal), n, _ptr(scores), _ptr(configs)))
+
+    def predictor_loss_grad(self, x, y, mask, grad) -> float:
+        loss = ctypes.c_float()
+        _check("gbgemm_predictor_loss_grad", lib().gbgemm_predictor_loss_grad(
+            self._h, _ptr(x), _ptr(y), _ptr(mask), int(x.shape[0]), ctypes.byref(loss), _ptr(grad)))
+        return loss.value
+
+    def predictor_train(self, x, y, mask, epochs, batch=256, lr=1e-3, seed=0) -> float:
+        loss = ctypes.c_float()
+        _check("gbgemm_predictor_train", lib().gbgemm_predictor_train(
+            self._h, _ptr(x), _ptr(y), _ptr(mask), int(x.shape[0]), int(epochs), int(batch), float(lr),
+            int(seed), ctypes.byref(loss)))
+        return loss.value
+
     def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
         return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),
                                        _ptr(amax_bits), _ptr(panel))
@@ -299,6 +372,12 @@ def sgemm_split_noalloc(stream, transa, transb, m, n, k, alpha, A, lda, B, ldb, 
     return lib().gbgemm_sgemm_split_noalloc(_stream_ptr(stream), transa.encode(), transb.encode(), int(m), int(n),
                                             int(k), float(alpha), _ptr(A), int(lda), _ptr(B), int(ldb), float(beta),
                                             _ptr(C), int(ldc), _ptr(status))
+
+
+def predictor_features(prob: "Problem"):
+    arr = (ctypes.c_float * 8)()
+    _check("gbgemm_predictor_features", lib().gbgemm_predictor_features(ctypes.byref(prob), arr))
+    return list(arr)
 
 
 def split_workspace_bytes(m, n, k) -> int:
