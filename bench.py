@@ -5,8 +5,9 @@ path (the headline) against the plain FP32 SIMT path, same inputs.
 Workload: the square sgemm sweep's 8192^3 point -- column-major, transa =
 transb = 'N', lda = ldb = ldc = 8200 (rows + 8), alpha = 1.5, beta = -0.25,
 A, B, C uniform[-1, 1) from seed 1 (SplitMix64 generator).  A step is one
-gbgemm_sgemm call on the split path: row maxima, hi/lo packing of both
-operands and the tcgen05 GEMM, everything the call does.  TFLOP/s =
+gbgemm_sgemm call on the split path: hi/lo packing of both operands (with
+their row maxima), the re-pack of badly scaled rows and the tcgen05 GEMM,
+everything the call does.  TFLOP/s =
 2 m n k / time (the paper's FLOP convention, Tables I-VI).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -287,6 +288,20 @@ def run_ours(args, rank, world, local_rank):
                          f"{bf16_sust / 3:.1f}: frac {achieved / (bf16_sust / 3) if bf16_sust else float('nan'):.3f})"),
                 "gemm_share_of_step": gemm_ms / ms if ms > 0 else None}
 
+    # ---- accuracy of one call, FP64 on the GPU (outside the timed region) ----
+    C.copy_(C0)
+    h.set_path(gbgemm.PATH_SPLIT_BF16)
+    h.sgemm("N", "N", N, N, N, ALPHA, A, LD, B, LD, BETA, C, LD)
+    torch.cuda.synchronize()
+    err = {"max_error_ratio": max(
+        h.check_error("N", "N", N, N, N, ALPHA, A, LD, B, LD, BETA, C0, C, LD, rows=(i0, i0 + 512), cols=(j0, j0 + 512))
+        for (i0, j0) in ((0, 0), (N - 512, N - 512), (3584, 1024))),
+        "blocks": "3 blocks of 512x512 (corner, corner, interior), FP64 on the GPU",
+        "bound": "|C - C64| <= 2 k 2^-24 (|alpha||A||B| + |beta||C|)"}
+    extras = {}
+    if args.extras and rank == 0:
+        extras = run_extras(h, stream, flop)
+
     if rank == 0:
         cpu = oracle_sample(steps=max(1, args.cpu_blocks)) if args.cpu_blocks > 0 else None
         if cpu:
@@ -304,11 +319,115 @@ def run_ours(args, rank, world, local_rank):
             "split_over_simt": value / world / simt_tflops if simt_tflops > 0 else None,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "error_check": err,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _time(fn, stream, reps):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_extras(h, stream, flop8192):
+    """Linpack-shaped update, grouped uneven batch and the 4096^3 rates they are
+    compared with.  Inputs generated on the device (seeded torch generators)."""
+    import torch
+
+    from paper_1608_05265_gb300 import gbgemm, metrics, synth
+
+    out = {}
+    _, _, hbm, peak_src = load_peaks()
+    g = torch.Generator(device="cuda")
+    # -- 4096^3 NN, ld 4104: the equivalent single-GEMM rates of both paths --
+    n4, ld4 = 4096, 4104
+    g.manual_seed(11)
+    A4 = torch.rand(n4 * ld4, device="cuda", generator=g) * 2 - 1
+    B4 = torch.rand(n4 * ld4, device="cuda", generator=g) * 2 - 1
+    C4 = torch.rand(n4 * ld4, device="cuda", generator=g) * 2 - 1
+    rates = {}
+    for path, name in ((gbgemm.PATH_SPLIT_BF16, "split"), (gbgemm.PATH_SIMT, "simt")):
+        h.set_path(path)
+        ms = _time(lambda: h.sgemm("N", "N", n4, n4, n4, 1.5, A4, ld4, B4, ld4, -0.25, C4, ld4), stream,
+                   20 if name == "split" else 5)
+        rates[name] = metrics.gemm_flops(n4, n4, n4) / (ms * 1e-3) / 1e12
+    del A4, B4, C4
+    out["square_4096"] = {"split": rates["split"], "simt": rates["simt"], "unit": "TFLOP/s"}
+    # -- Linpack-shaped trailing update: C(16384^2) -= A(16384 x nb) B(nb x 16384) --
+    lp = {}
+    m = 16384
+    for nb in (128, 256):
+        g.manual_seed(20 + nb)
+        def rowscaled(rows, cols):
+            x = torch.randn(cols, rows, device="cuda", generator=g)
+            e = torch.randint(-20, 21, (rows,), device="cuda", generator=g).float()
+            return (x * torch.exp2(e)[None, :]).reshape(-1).contiguous()
+        A = rowscaled(m, nb)
+        B = rowscaled(nb, m)
+        C = rowscaled(m, m)
+        h.set_path(gbgemm.PATH_AUTO)
+        ms = _time(lambda: h.sgemm("N", "N", m, m, nb, -1.0, A, m, B, nb, 1.0, C, m), stream, 20)
+        fl = metrics.gemm_flops(m, m, nb)
+        by = 8.0 * m * m + 4.0 * (2 * m) * nb
+        tf = fl / (ms * 1e-3) / 1e12
+        gbs = by / (ms * 1e-3) / 1e9
+        lp[f"nb{nb}"] = {"ms": ms, "tflops": tf, "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
+                         "roofline_tflops": min(642.6, fl / by * hbm / 1e3),
+                         "path": "split" if h.last_path() == 2 else "simt"}
+        del A, B, C
+    out["linpack_update_16384"] = dict(lp, note=f"bytes = 8 m n + 4 (m + n) nb; HBM peak {hbm:.0f} GB/s ({peak_src})")
+    # -- grouped uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024] (seed 3) --
+    shapes = synth.grouped_shapes(3, 4096)
+    bufs, probs = [], []
+    fl_total = 0.0
+    g.manual_seed(3)
+    for (ta, tb, mm, nn, kk) in shapes:
+        ar, ac = synth.op_shape(ta, mm, kk)
+        br, bc = synth.op_shape(tb, kk, nn)
+        Ag = torch.rand(ar * ac, device="cuda", generator=g) * 2 - 1
+        Bg = torch.rand(br * bc, device="cuda", generator=g) * 2 - 1
+        Cg = torch.empty(mm * nn, device="cuda")
+        bufs.append((Ag, Bg, Cg))
+        probs.append(gbgemm.problem(ta, tb, mm, nn, kk, 1.0, Ag, ar, Bg, br, 0.0, Cg, mm))
+        fl_total += metrics.gemm_flops(mm, nn, kk)
+    grouped = {}
+    sources = [("default", gbgemm.CONFIG_DEFAULT)]
+    weights = os.path.join(ROOT, "paper_1608_05265_gb300", "data", "predictor_gb300.bin")
+    if os.path.exists(weights):
+        from paper_1608_05265_gb300 import predictor
+        h.predictor_set(predictor.load_weights(weights)[0])
+        sources.append(("predicted", gbgemm.CONFIG_PREDICTED))
+    for name, src in sources:
+        t0 = time.time()
+        plan = gbgemm.GroupedPlan(h, probs, config_source=src)
+        t_plan = time.time() - t0
+        ms = _time(lambda: plan.run(stream), stream, 20)
+        st = plan.stats()
+        fs = st["flops_split"] / max(st["flops_split"] + st["flops_simt"], 1.0)
+        equiv = 1.0 / (fs / rates["split"] + (1 - fs) / rates["simt"])
+        tf = fl_total / (ms * 1e-3) / 1e12
+        grouped[name] = {"ms": ms, "tflops": tf, "plan_seconds": t_plan, "split_flop_share": fs,
+                         "equivalent_single_gemm_tflops": equiv, "fraction_of_equivalent": tf / equiv,
+                         "kernels_per_run": st["kernels_per_run"]}
+        plan.close()
+    out["grouped_4096"] = dict(grouped, problems=4096, flops=fl_total,
+                               note="equivalent rate = flop-weighted harmonic mean of the 4096^3 split and SIMT rates")
+    assert h.get_device_status() == 0
+    return out
 
 
 def main():
@@ -318,6 +437,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-blocks", type=int, default=3, help="oracle blocks timed for cpu_baseline (0: skip)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the Linpack-shaped, grouped and 4096^3 measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -137,6 +137,21 @@ int gbgemm_get_device_status(gbgemm_handle* h, int* status);
 int gbgemm_profile_begin(gbgemm_handle* h);
 int gbgemm_profile_end(gbgemm_handle* h, double* gemm_ms, int64_t* gemm_launches, int64_t* kernel_launches);
 
+/* FP64 error check on the GPU (tests and benchmarks; the sgemm paths never
+ * use FP64).  For the block rows [i0, i1) x columns [j0, j1) of an m x n
+ * result it recomputes C64 = alpha * sum_p opA(i,p) opB(p,j) + beta * C_in
+ * (Section III-A) with FP64 products and sums in p order, and the
+ * acceptance bound
+ *   bound_ij = 2 max(k,1) 2^-24 (|alpha| sum_p |opA(i,p)||opB(p,j)| + |beta||C_in,ij|),
+ * then returns *max_ratio = max |C_out,ij - C64_ij| / bound_ij (+inf when a
+ * zero bound is exceeded or a difference is NaN).  C_in is the C the sgemm
+ * started from (caller keeps a copy), C_out its result; both use ldc.  All
+ * matrix pointers are device pointers.  Synchronises the handle's stream. */
+int gbgemm_check_error(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta, const float* C_in,
+                       const float* C_out, int64_t ldc, int64_t i0, int64_t i1, int64_t j0, int64_t j1,
+                       double* max_ratio);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char* gbgemm_status_string(int status);
 

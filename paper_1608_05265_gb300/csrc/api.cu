@@ -583,6 +583,16 @@ int gbgemm_set_tuning(gbgemm_handle* h, int mode) {
   return GBGEMM_OK;
 }
 
+int gbgemm_check_error(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta, const float* C_in,
+                       const float* C_out, int64_t ldc, int64_t i0, int64_t i1, int64_t j0, int64_t j1,
+                       double* max_ratio) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  DeviceGuard dg(h->device);
+  return gbg::run_error_check(h->stream, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C_in, C_out, ldc, i0,
+                              i1, j0, j1, max_ratio);
+}
+
 int gbgemm_get_device_status(gbgemm_handle* h, int* status) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!status) return GBGEMM_ERR_INVALID_VALUE;

@@ -58,4 +58,11 @@ struct SplitGemmArgs {
 };
 cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s);
 
+// FP64 error check of C_out against alpha op(A) op(B) + beta C_in over a
+// block (check.cu); synchronises s.
+int run_error_check(cudaStream_t s, char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                    const float* A, int64_t lda, const float* B, int64_t ldb, float beta, const float* C_in,
+                    const float* C_out, int64_t ldc, int64_t i0, int64_t i1, int64_t j0, int64_t j1,
+                    double* max_ratio);
+
 }  // namespace gbg

@@ -66,7 +66,7 @@ EXPORTS = [
     "gbgemm_grouped_plan_stats", "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
     "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
     "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
-    "gbgemm_predictor_loss_grad", "gbgemm_predictor_train",
+    "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error",
 ]
 
 _lock = threading.Lock()
@@ -130,6 +130,8 @@ def lib():
             L.gbgemm_predictor_loss_grad.argtypes = [vp, vp, vp, vp, i64, fp, vp]
             L.gbgemm_predictor_train.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                                  ctypes.c_uint64, fp]
+            L.gbgemm_check_error.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, vp, i64, i64,
+                                             i64, i64, i64, ctypes.POINTER(ctypes.c_double)]
             L.gbgemm_profile_begin.argtypes = [vp]
             L.gbgemm_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                              ctypes.POINTER(i64)]
@@ -142,7 +144,7 @@ def lib():
                          "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
                          "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
                          "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
-                         "gbgemm_predictor_loss_grad", "gbgemm_predictor_train"):
+                         "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -289,6 +291,18 @@ class Handle:
             self._h, _ptr(x), _ptr(y), _ptr(mask), int(x.shape[0]), int(epochs), int(batch), float(lr),
             int(seed), ctypes.byref(loss)))
         return loss.value
+
+    def check_error(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C_in, C_out, ldc,
+                    rows=None, cols=None) -> float:
+        """Max FP64 error ratio of C_out over a block (gbgemm_check_error)."""
+        i0, i1 = rows if rows is not None else (0, m)
+        j0, j1 = cols if cols is not None else (0, n)
+        r = ctypes.c_double()
+        _check("gbgemm_check_error", lib().gbgemm_check_error(
+            self._h, transa.encode(), transb.encode(), int(m), int(n), int(k), float(alpha), _ptr(A), int(lda),
+            _ptr(B), int(ldb), float(beta), _ptr(C_in), _ptr(C_out), int(ldc), int(i0), int(i1), int(j0), int(j1),
+            ctypes.byref(r)))
+        return r.value
 
     def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
         return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),
