@@ -61,6 +61,12 @@ def lib():
             L.oracle_split_rows.argtypes = [i64, i64, vp, i64, i64, vp, vp, vp]
             L.oracle_split_rows.restype = None
             L.oracle_split_exhaustive.argtypes = [ctypes.c_uint64, ctypes.c_uint64, vp, ctypes.c_int]
+            L.oracle_split3_exhaustive.argtypes = [ctypes.c_uint64, ctypes.c_uint64, vp, ctypes.c_int]
+            L.oracle_split3_exhaustive.restype = None
+            L.oracle_split_rows3.argtypes = [i64, i64, vp, i64, i64, vp, vp, vp, vp]
+            L.oracle_split_rows3.restype = None
+            L.oracle_split_third.argtypes = [f32]
+            L.oracle_split_third.restype = ctypes.c_uint16
             L.oracle_split_exhaustive.restype = None
             L.oracle_max_threads.restype = ctypes.c_int
             L.oracle_trans_code.argtypes = [ctypes.c_char]
@@ -138,6 +144,40 @@ def split_rows(X: np.ndarray, rows: int, k: int, sr: int, sp: int):
         lo = np.zeros_like(hi)
         lib().oracle_split_rows(rows, k, _ptr(X), sr, sp, _ptr(e), _ptr(hi), _ptr(lo))
     return e[:rows], hi[:rows, :k], lo[:rows, :k]
+
+
+def split_rows3(X: np.ndarray, rows: int, k: int, sr: int, sp: int):
+    """(e, hi, mid, lo3): the three-part split; hi and mid equal split_rows' hi and lo."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    e = np.zeros(max(rows, 1), dtype=np.int32)
+    hi = np.zeros((max(rows, 1), max(k, 1)), dtype=np.uint16)
+    mid = np.zeros_like(hi)
+    lo3 = np.zeros_like(hi)
+    if rows > 0 and k > 0:
+        lib().oracle_split_rows3(rows, k, _ptr(X), sr, sp, _ptr(e), _ptr(hi), _ptr(mid), _ptr(lo3))
+    return e[:rows], hi[:rows, :k], mid[:rows, :k], lo3[:rows, :k]
+
+
+def split_third(x: float) -> int:
+    return int(lib().oracle_split_third(float(x)))
+
+
+def split3_exhaustive(u0: int = 0, u1: int = 1 << 32, nthreads: int = 0) -> np.ndarray:
+    counts = np.zeros(3, dtype=np.int64)
+    lib().oracle_split3_exhaustive(u0, u1, _ptr(counts), int(nthreads))
+    return counts
+
+
+def split_operand3(which: str, trans: str, rows_op: int, k: int, X: np.ndarray, ld: int):
+    """(e, hi, mid, lo3) of op(A) rows (which='A') or op(B) columns (which='B')."""
+    t = lib().oracle_trans_code(trans.encode())
+    if t < 0:
+        raise ValueError("bad transpose flag")
+    if which == "A":
+        sr, sp = (ld, 1) if t else (1, ld)
+    else:
+        sr, sp = (1, ld) if t else (ld, 1)
+    return split_rows3(X, rows_op, k, sr, sp)
 
 
 def split_operand(which: str, trans: str, rows_op: int, k: int, X: np.ndarray, ld: int):

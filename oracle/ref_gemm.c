@@ -35,6 +35,10 @@
  *               M, so that the scaled max lies in [0.5, 1).
  *   split:      x' = x * 2^-e (exact in double, one rounding to float),
  *               hi = bf16(x'), lo = bf16(x' - hi); non-finite x: lo = 0.
+ *   three parts (for short k): hi and mid as hi and lo above, then
+ *               lo3 = bf16(x' - hi - mid) (both subtractions exact in
+ *               float); x' = hi + mid + lo3 exactly for normal x'; non-finite
+ *               x: mid = lo3 = 0.
  *
  * Work is split across threads over output columns only; the arithmetic of
  * every output element is the plain loop above.
@@ -193,10 +197,59 @@ void oracle_split(float xs, uint16_t* hi, uint16_t* lo) {
   *lo = oracle_bf16_rne(r);
 }
 
+/* Third BF16 part of a scaled value: bf16((xs - hi) - mid). */
+uint16_t oracle_split_third(float xs) {
+  if (!isfinite(xs)) return 0;
+  uint16_t h, m;
+  oracle_split(xs, &h, &m);
+  float r1 = xs - oracle_bf16_to_f32(h);
+  float r2 = r1 - oracle_bf16_to_f32(m);
+  return oracle_bf16_rne(r2);
+}
+
+/* Exhaustive check of the three-part split over [u0, u1): counts[0] finite
+ * patterns with |x| >= 2^-100, counts[1] those where x != hi + mid + lo3
+ * exactly (evaluated in double), counts[2] where xs - hi - mid is not exact
+ * in float. */
+void oracle_split3_exhaustive(uint64_t u0, uint64_t u1, int64_t* counts, int nthreads) {
+  int64_t c0 = 0, c1 = 0, c2 = 0;
+  const double tiny = ldexp(1.0, -100);
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(static) reduction(+ : c0, c1, c2) num_threads(nthreads)
+#else
+  (void)nthreads;
+#endif
+  for (int64_t ui = (int64_t)u0; ui < (int64_t)u1; ++ui) {
+    float x = u2f((uint32_t)ui);
+    if (!isfinite(x) || fabs((double)x) < tiny) continue;
+    if (fabs((double)x) >= ldexp(1.0, 128) * (1.0 - ldexp(1.0, -9))) continue; /* hi overflows */
+    c0++;
+    uint16_t h, m;
+    oracle_split(x, &h, &m);
+    uint16_t l = oracle_split_third(x);
+    double hd = oracle_bf16_to_f32(h), md = oracle_bf16_to_f32(m), ld = oracle_bf16_to_f32(l);
+    if (hd + md + ld != (double)x) c1++;
+    float r1 = x - (float)hd;
+    float r2 = r1 - (float)md;
+    if ((double)r2 != (double)x - hd - md) c2++;
+  }
+  counts[0] = c0; counts[1] = c1; counts[2] = c2;
+}
+
 /* Split `rows` K-vectors of length k.  Element (r, p) of the operand is
  * X[r*sr + p*sp].  Writes e[r], hi[r*k + p], lo[r*k + p]. */
+void oracle_split_rows3(int64_t rows, int64_t k, const float* X, int64_t sr, int64_t sp,
+                        int32_t* e, uint16_t* hi, uint16_t* lo, uint16_t* lo3);
+
 void oracle_split_rows(int64_t rows, int64_t k, const float* X, int64_t sr, int64_t sp,
                        int32_t* e, uint16_t* hi, uint16_t* lo) {
+  oracle_split_rows3(rows, k, X, sr, sp, e, hi, lo, NULL);
+}
+
+/* As oracle_split_rows, plus the third part lo3[r*k + p] when lo3 != NULL. */
+void oracle_split_rows3(int64_t rows, int64_t k, const float* X, int64_t sr, int64_t sp,
+                        int32_t* e, uint16_t* hi, uint16_t* lo, uint16_t* lo3) {
   for (int64_t r = 0; r < rows; ++r) {
     float amax = 0.0f;
     int nonfinite = 0;
@@ -211,6 +264,7 @@ void oracle_split_rows(int64_t rows, int64_t k, const float* X, int64_t sr, int6
       float x = X[r * sr + p * sp];
       float xs = isfinite(x) ? oracle_scaled(x, ex) : x;
       oracle_split(xs, &hi[r * k + p], &lo[r * k + p]);
+      if (lo3) lo3[r * k + p] = oracle_split_third(xs);
     }
   }
 }

@@ -144,3 +144,38 @@ def test_split_exhaustive_invariants():
     assert c[0] == (1 << 32) - 2 * (1 << 23)  # every pattern whose exponent field is not all ones
     assert list(c[1:7]) == [0, 0, 0, 0, 0, 0]
     assert c[7] <= 2**23  # max relative residual <= 2^-17
+
+
+@pytest.mark.parametrize("x", [1.0 + 2.0**-8 + 2.0**-12 + 2.0**-20, -3.14159265, 1.0 / 3.0, 2.0**-90 * 1.2345,
+                               float(np.float32(1e30)), 0.1])
+def test_three_part_split_is_exact(x):
+    x = float(np.float32(x))
+    h = O.bf16_rne(x)
+    hf = float(np.array([h << 16], dtype=np.uint32).view(np.float32)[0])
+    r1 = float(np.float32(x) - np.float32(hf))
+    m = O.bf16_rne(r1)
+    mf = float(np.array([m << 16], dtype=np.uint32).view(np.float32)[0])
+    lo = O.split_third(x)
+    lf = float(np.array([lo << 16], dtype=np.uint32).view(np.float32)[0])
+    assert hf + mf + lf == x  # exact in double
+    # the third part is a BF16 rounding of an exact float remainder
+    assert lo == O.bf16_rne(float(np.float32(r1) - np.float32(mf)))
+
+
+def test_three_part_split_exhaustive():
+    c = O.split3_exhaustive()
+    assert c[0] > 3_000_000_000
+    assert c[1] == 0 and c[2] == 0
+
+
+def test_split_rows3_matches_two_part_split():
+    rows, k = 9, 77
+    X = synth.normal_rowscaled_matrix(6, 0, rows, k, rows, elo=-70, ehi=70)
+    e, hi, lo = O.split_rows(X, rows, k, 1, rows)
+    e3, hi3, mid3, lo3 = O.split_rows3(X, rows, k, 1, rows)
+    assert np.array_equal(e, e3) and np.array_equal(hi, hi3) and np.array_equal(lo, mid3)
+    L = synth.logical(X, rows, k, rows).astype(np.float64)
+    f = lambda a: (a.astype(np.uint32) << 16).view(np.float32).astype(np.float64)  # noqa: E731
+    xs = L * np.ldexp(1.0, -e3.astype(np.int64))[:, None]
+    big = np.abs(xs) >= 2.0**-100
+    assert np.array_equal((f(hi3) + f(mid3) + f(lo3))[big], xs[big])
