@@ -27,13 +27,15 @@
  *   GBGEMM_PATH_SPLIT_BF16  each badly scaled operand row (of op(A)) or
  *                           column (of op(B)) -- largest magnitude outside
  *                           [2^-48, 2^48) -- is scaled by a power of two so
- *                           its largest entry lies in [0.5, 1); every entry x
- *                           becomes
- *                           hi + lo (two BF16 values, hi = bf16(x),
- *                           lo = bf16(x - hi)), and the tensor cores
- *                           accumulate hi*hi + hi*lo + lo*hi in FP32.  The
- *                           bound is guaranteed for k >= 128; below that
- *                           GBGEMM_PATH_AUTO uses the SIMT path.
+ *                           its largest entry lies in [0.5, 1).  For
+ *                           k >= 512 every entry x becomes hi + lo (two
+ *                           BF16 values, hi = bf16(x), lo = bf16(x - hi))
+ *                           and the tensor cores accumulate hi*hi + hi*lo +
+ *                           lo*hi in FP32; for k < 512 it becomes hi + mid +
+ *                           lo3 (lo3 = bf16(x - hi - mid), the sum is exact)
+ *                           and six products are accumulated (hi*hi, hi*mid,
+ *                           mid*hi, hi*lo3, mid*mid, lo3*hi).  Either way
+ *                           the bound holds for every k.
  *   GBGEMM_PATH_AUTO        SPLIT_BF16 when k >= 128, else SIMT.
  *
  * Memory and streams.  All matrix pointers are DEVICE pointers owned by the
@@ -105,7 +107,7 @@ int gbgemm_last_path(gbgemm_handle* h, int* path);
 /* Grow the workspace to at least `bytes` now (cudaMalloc; synchronous). */
 int gbgemm_reserve_workspace(gbgemm_handle* h, size_t bytes);
 
-/* Workspace bytes the split path needs for (m, n, k). */
+/* Workspace bytes the split path needs for (m, n, k) (twice the panels when k < 512). */
 size_t gbgemm_split_workspace_bytes(int64_t m, int64_t n, int64_t k);
 
 /* BLAS-convention sgemm (Section III-A problem statement).
@@ -352,6 +354,9 @@ int gbgemm_sgemm_split_noalloc(void* cuda_stream, char transa, char transb, int6
  *              transb, X = B, ldx = ldb).
  * Outputs (device, caller-owned):
  *   amax_bits[r] = bit pattern of max_p |x(r,p)| (NaN/Inf patterns kept), rows entries.
+ *   panel2 (needed when k < 512, else ignored and may be NULL): a second
+ *   panel of the same size and layout holding lo3 in chunks 0-3 and zeros in
+ *   chunks 4-7; the first panel then holds hi and mid (= the two-part lo).
  *   panel: BF16 hi/lo panel of gbgemm_panel_bytes(rows, k) bytes.  It is a
  *   sequence of 16 KiB blocks, block (kc, rb) at byte offset
  *   (kc * RB + rb) * 16384 with RB = ceil(rows/256)*2 and kc = p / 32.  A
@@ -366,7 +371,7 @@ int gbgemm_sgemm_split_noalloc(void* cuda_stream, char transa, char transb, int6
  * Asynchronous on the handle's stream. */
 size_t gbgemm_panel_bytes(int64_t rows, int64_t k);
 int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,
-                      const float* X, int64_t ldx, uint32_t* amax_bits, void* panel);
+                      const float* X, int64_t ldx, uint32_t* amax_bits, void* panel, void* panel2);
 
 #ifdef __cplusplus
 }

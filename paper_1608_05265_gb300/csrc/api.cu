@@ -105,7 +105,8 @@ size_t gbgemm_panel_bytes(int64_t rows, int64_t k) {
 
 size_t gbgemm_split_workspace_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  return align_up(gbg::panel_bytes(m, k), 256) + align_up(gbg::panel_bytes(n, k), 256) +
+  const size_t parts = (size_t)gbg::split_parts(k);
+  return parts * (align_up(gbg::panel_bytes(m, k), 256) + align_up(gbg::panel_bytes(n, k), 256)) +
          align_up((size_t)m * 4, 256) + align_up((size_t)n * 4, 256);
 }
 
@@ -246,17 +247,25 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   const size_t xa = align_up((size_t)m * 4, 256);
   int rc = ensure_workspace(h, gbgemm_split_workspace_bytes(m, n, k));
   if (rc != GBGEMM_OK) return rc;
+  // workspace: [panel A | panel B | maxima A | maxima B | (three parts) panel A2 | panel B2]
   uint8_t* ws = static_cast<uint8_t*>(h->ws);
   void* panelA = ws;
   void* panelB = ws + pa;
   uint32_t* amaxA = reinterpret_cast<uint32_t*>(ws + pa + pb);
   uint32_t* amaxB = reinterpret_cast<uint32_t*>(ws + pa + pb + xa);
+  const size_t xb = align_up((size_t)n * 4, 256);
+  const bool three = gbg::split_parts(k) == 2;
+  void* panelA2 = three ? ws + pa + pb + xa + xb : nullptr;
+  void* panelB2 = three ? ws + pa + pb + xa + xb + pa : nullptr;
   // Rows of op(A): element (i, p) at A[p + i*lda] when transposed (k contiguous).
-  if (gbg::launch_split_pack(m, k, A, lda, ta == 1, amaxA, panelA, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (gbg::launch_split_pack(m, k, A, lda, ta == 1, amaxA, panelA, panelA2, h->stream) != cudaSuccess)
+    return GBGEMM_ERR_CUDA;
   // Columns of op(B): element (j, p) at B[p + j*ldb] when not transposed (k contiguous).
-  if (gbg::launch_split_pack(n, k, B, ldb, tb == 0, amaxB, panelB, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (gbg::launch_split_pack(n, k, B, ldb, tb == 0, amaxB, panelB, panelB2, h->stream) != cudaSuccess)
+    return GBGEMM_ERR_CUDA;
   gbg::SplitGemmArgs a;
   a.panelA = panelA; a.panelB = panelB; a.amaxA = amaxA; a.amaxB = amaxB;
+  a.panelA2 = panelA2; a.panelB2 = panelB2;
   a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
   a.status = h->d_status; a.num_sms = h->num_sms;
   a.bn = split_bn; a.raster = 16;
@@ -271,19 +280,20 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
 }
 
 int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,
-                      const float* X, int64_t ldx, uint32_t* amax_bits, void* panel) {
+                      const float* X, int64_t ldx, uint32_t* amax_bits, void* panel, void* panel2) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   const int t = trans_code(trans);
   if (t < 0 || (which != 'A' && which != 'B') || rows < 0 || k < 0) return GBGEMM_ERR_INVALID_VALUE;
   if (rows == 0 || k == 0) return GBGEMM_OK;
-  if (!X || !amax_bits || !panel) return GBGEMM_ERR_INVALID_VALUE;
+  if (!X || !amax_bits || !panel || (gbg::split_parts(k) == 2 && !panel2)) return GBGEMM_ERR_INVALID_VALUE;
   // Stored rows of X: op(A) rows come from A (m x k or k x m); op(B) columns from B.
   const bool kcontig = (which == 'A') ? (t == 1) : (t == 0);
   const int64_t stored_rows = kcontig ? k : rows;
   if (ldx < (stored_rows > 1 ? stored_rows : 1)) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard g(h->device);
-  return gbg::launch_split_pack(rows, k, X, ldx, kcontig, amax_bits, panel, h->stream) == cudaSuccess ? GBGEMM_OK
-                                                                                                      : GBGEMM_ERR_CUDA;
+  return gbg::launch_split_pack(rows, k, X, ldx, kcontig, amax_bits, panel, panel2, h->stream) == cudaSuccess
+             ? GBGEMM_OK
+             : GBGEMM_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------

@@ -49,6 +49,8 @@ struct TileJob {
   size_t b_kstride;         // bytes between k chunks of the B panel
   int nkc;                  // k chunks
   int bn;                   // tile width: 64, 128 or 256
+  int parts;                // 1: [hi | lo] panels, 3 products; 2: also [lo3 | 0] panels, 6 products
+  int64_t a_part, b_part;   // byte offsets from the [hi | mid] panels to the [lo3 | 0] panels
   int64_t m0, n0;           // tile origin in C
   int64_t m, n;             // problem extents
   const uint32_t* amaxA;
@@ -71,8 +73,9 @@ struct SingleSched {
   int64_t m, n;
   float alpha, beta;
   float* C; int64_t ldc;
-  int tiles_m, tiles_n, nkc, raster, bn;
+  int tiles_m, tiles_n, nkc, raster, bn, parts;
   int64_t rbA, rbB;
+  int64_t a_part, b_part;
   __device__ __forceinline__ int num_items() const { return tiles_m * tiles_n; }
   __device__ __forceinline__ TileJob job(int t) const {
     int tm, tn;
@@ -83,6 +86,7 @@ struct SingleSched {
     j.a_kstride = (size_t)rbA * kBlockBytes;
     j.b_kstride = (size_t)rbB * kBlockBytes;
     j.nkc = nkc; j.bn = bn;
+    j.parts = parts; j.a_part = a_part; j.b_part = b_part;
     j.m0 = (int64_t)tm * 128; j.n0 = (int64_t)tn * bn;
     j.m = m; j.n = n;
     j.amaxA = amaxA; j.amaxB = amaxB;
@@ -100,6 +104,8 @@ struct GroupDev {
   int nkc, bn;
   int64_t rowsA, rowsB;     // panel rows per k chunk
   float alpha, beta;
+  int parts, pad_;
+  int64_t a_part, b_part;   // byte offsets to the [lo3 | 0] panels (parts == 2)
 };
 
 // Many problems: item t = (group, tile row, tile column), items sorted by
@@ -118,6 +124,7 @@ struct GroupedSched {
     j.a_kstride = (size_t)g.rowsA * 128;
     j.b_kstride = (size_t)g.rowsB * 128;
     j.nkc = g.nkc; j.bn = g.bn;
+    j.parts = g.parts; j.a_part = g.a_part; j.b_part = g.b_part;
     j.m0 = (int64_t)it.y * 128; j.n0 = (int64_t)it.z * g.bn;
     j.m = g.m; j.n = g.n;
     j.amaxA = g.amaxA; j.amaxB = g.amaxB;
@@ -180,18 +187,23 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x) {
         const TileJob J = S.job(t);
         const uint32_t b_bytes = (uint32_t)J.bn * 128u;
-        for (int kc = 0; kc < J.nkc; ++kc) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, timeout_ns)) {
-            raise_status(status, abort_flag);
-            ok = false;
-            break;
+        // one ring slot per panel part and k chunk
+        for (int kc = 0; kc < J.nkc && ok; ++kc) {
+          for (int part = 0; part < J.parts; ++part) {
+            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, timeout_ns)) {
+              raise_status(status, abort_flag);
+              ok = false;
+              break;
+            }
+            const uint8_t* a = J.a_src + (part ? J.a_part : 0) + (size_t)kc * J.a_kstride;
+            const uint8_t* b = J.b_src + (part ? J.b_part : 0) + (size_t)kc * J.b_kstride;
+            mbar_arrive_expect_tx(full_bar(stage), A_BYTES + b_bytes);
+            bulk_copy_g2s(sA + stage * A_BYTES, a, A_BYTES, full_bar(stage));
+            bulk_copy_g2s(sB + stage * B_STAGE, b, b_bytes, full_bar(stage));
+            issued[stage] = true;
+            issued_phase[stage] = (int)phase;
+            if (++stage == kStages) { stage = 0; phase ^= 1u; }
           }
-          mbar_arrive_expect_tx(full_bar(stage), A_BYTES + b_bytes);
-          bulk_copy_g2s(sA + stage * A_BYTES, J.a_src + (size_t)kc * J.a_kstride, A_BYTES, full_bar(stage));
-          bulk_copy_g2s(sB + stage * B_STAGE, J.b_src + (size_t)kc * J.b_kstride, b_bytes, full_bar(stage));
-          issued[stage] = true;
-          issued_phase[stage] = (int)phase;
-          if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
       }
       // Let every copy this thread started land before the CTA can exit.
@@ -218,14 +230,30 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * kMaxBN);
         for (int kc = 0; kc < J.nkc; ++kc) {
-          if (!mbar_wait(full_bar(stage), phase, abort_flag, timeout_ns)) {
+          // the chunk's slots: s0 holds [hi | lo] (or [hi | mid]); s1, with three
+          // parts, holds [lo3 | 0]
+          const int s0 = stage;
+          const uint32_t ph0 = phase;
+          if (!mbar_wait(full_bar(s0), ph0, abort_flag, timeout_ns)) {
             raise_status(status, abort_flag);
             ok = false;
             break;
           }
+          int s1 = s0;
+          if (J.parts == 2) {
+            if (++stage == kStages) { stage = 0; phase ^= 1u; }
+            s1 = stage;
+            if (!mbar_wait(full_bar(s1), phase, abort_flag, timeout_ns)) {
+              raise_status(status, abort_flag);
+              ok = false;
+              break;
+            }
+          }
           tc_fence_after();
-          const uint32_t a_addr = sA + stage * A_BYTES;
-          const uint32_t b_addr = sB + stage * B_STAGE;
+          const uint32_t a_addr = sA + s0 * A_BYTES;
+          const uint32_t b_addr = sB + s0 * B_STAGE;
+          const uint32_t a3_addr = sA + s1 * A_BYTES;
+          const uint32_t b3_addr = sB + s1 * B_STAGE;
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             const uint64_t ah = make_desc_sw128(a_addr + 32u * kk);
@@ -235,8 +263,17 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
             mma_bf16(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
             mma_bf16(d_tmem, ah, bl, idesc, 1u);
             mma_bf16(d_tmem, al, bh, idesc, 1u);
+            if (J.parts == 2) {
+              // with three parts: hi*lo3 + mid*mid + lo3*hi (al, bl above are mid)
+              const uint64_t a3 = make_desc_sw128(a3_addr + 32u * kk);
+              const uint64_t b3 = make_desc_sw128(b3_addr + 32u * kk);
+              mma_bf16(d_tmem, ah, b3, idesc, 1u);
+              mma_bf16(d_tmem, al, bl, idesc, 1u);
+              mma_bf16(d_tmem, a3, bh, idesc, 1u);
+            }
           }
-          mma_commit(empty_bar(stage));  // frees the stage once these MMAs have read it
+          mma_commit(empty_bar(s0));  // frees the slots once these MMAs have read them
+          if (J.parts == 2) mma_commit(empty_bar(s1));
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;

@@ -35,22 +35,23 @@ namespace {
 template <bool KCONTIG>
 __global__ void __launch_bounds__(256) pack_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                                    uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
-                                                   int64_t rows_alloc) {
+                                                   uint8_t* __restrict__ panel2, int64_t rows_alloc) {
   __shared__ uint32_t smax[128];
-  pack_block<KCONTIG>(rows, k, X, ld, amax, panel, rows_alloc, blockIdx.x, blockIdx.y, smax);
+  pack_block<KCONTIG>(rows, k, X, ld, amax, panel, panel2, rows_alloc, blockIdx.x, blockIdx.y, smax);
 }
 
 __global__ void __launch_bounds__(256) rescale_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                                       bool kcontig, const uint32_t* __restrict__ amax,
-                                                      uint8_t* __restrict__ panel, int64_t rows_alloc, int64_t nkc) {
+                                                      uint8_t* __restrict__ panel, uint8_t* __restrict__ panel2,
+                                                      int64_t rows_alloc, int64_t nkc) {
   __shared__ int se[128];
-  rescale_block(rows, k, X, ld, kcontig, amax, panel, rows_alloc, nkc, blockIdx.x, se);
+  rescale_block(rows, k, X, ld, kcontig, amax, panel, panel2, rows_alloc, nkc, blockIdx.x, se);
 }
 
 }  // namespace
 
 cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
-                              uint32_t* amax_bits, void* panel, cudaStream_t s) {
+                              uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s) {
   if (rows <= 0 || k <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(amax_bits, 0, (size_t)rows * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
@@ -59,11 +60,13 @@ cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t l
   dim3 g((unsigned)rbc, (unsigned)nkc);
   if (g.y > 65535u) return cudaErrorInvalidConfiguration;
   uint8_t* pn = static_cast<uint8_t*>(panel);
-  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, rbc * 128);
-  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, rbc * 128);
+  uint8_t* pn2 = split_parts(k) == 2 ? static_cast<uint8_t*>(panel2) : nullptr;
+  if (split_parts(k) == 2 && !pn2) return cudaErrorInvalidValue;
+  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128);
+  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  rescale_kernel<<<(unsigned)rbc, 256, 0, s>>>(rows, k, X, ld, kcontig, amax_bits, pn, rbc * 128, nkc);
+  rescale_kernel<<<(unsigned)rbc, 256, 0, s>>>(rows, k, X, ld, kcontig, amax_bits, pn, pn2, rbc * 128, nkc);
   return cudaGetLastError();
 }
 
@@ -85,6 +88,10 @@ cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s) {
   S.bn = a.bn;
   S.rbA = panel_row_blocks(a.m);
   S.rbB = panel_row_blocks(a.n);
+  S.parts = split_parts(a.k);
+  if (S.parts == 2 && (!a.panelA2 || !a.panelB2)) return cudaErrorInvalidValue;
+  S.a_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelA2) - S.panelA) : 0;
+  S.b_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelB2) - S.panelB) : 0;
   cudaError_t e = ensure_gemm_smem_attr<SingleSched>();
   if (e != cudaSuccess) return e;
   const int64_t tiles = tm * tn;

@@ -75,6 +75,35 @@ __device__ __forceinline__ void store_split8(uint8_t* blk, int rr, int cc, const
   *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+// Three-part split of 8 values: [hi | mid] into blk (as store_split8, mid =
+// the two-part lo) and [lo3 | 0] into blk2, lo3 = bf16((x - hi) - mid).
+__device__ __forceinline__ void store_split8_3(uint8_t* blk, uint8_t* blk2, int rr, int cc, const float (&x)[8]) {
+  uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t hb[2], mb[2], lb[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float v = x[2 * q + u];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hb[u] = (uint32_t)__bfloat16_as_ushort(h);
+      if (!isfinite(v)) { mb[u] = 0u; lb[u] = 0u; continue; }
+      const float r1 = v - __bfloat162float(h);
+      const __nv_bfloat16 mdl = __float2bfloat16_rn(r1);
+      mb[u] = (uint32_t)__bfloat16_as_ushort(mdl);
+      lb[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(mdl)));
+    }
+    hw[q] = hb[0] | (hb[1] << 16);
+    mw[q] = mb[0] | (mb[1] << 16);
+    lw[q] = lb[0] | (lb[1] << 16);
+  }
+  const int sw = rr & 7;
+  *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+  *reinterpret_cast<uint4*>(blk2 + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  *reinterpret_cast<uint4*>(blk2 + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Item mapping inside a 256-thread CTA, two items per thread.
 // KCONTIG (element (r,p) at X[r*ld + p]): four lanes per row, eight rows per
 //   warp, so a warp reads eight 128-byte row segments.
@@ -231,10 +260,13 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // chunk kc is the 128 bytes at (kc*rows_alloc + r)*128.  Rows from `rows`
 // up to rows_alloc are written as zeros, rows past rows_alloc not at all.
 // smax: 128 words of shared memory.
+// With panel2 != NULL the three-part split is written ([hi | mid] into
+// panel, [lo3 | 0] into panel2 at the same offsets).
 template <bool KCONTIG>
 __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                            uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
-                                           int64_t rows_alloc, int64_t rb, int64_t kc, uint32_t* smax) {
+                                           uint8_t* __restrict__ panel2, int64_t rows_alloc, int64_t rb, int64_t kc,
+                                           uint32_t* smax) {
   const int64_t r0 = rb * 128, p0 = kc * 32;
   const int tid = threadIdx.x;
   const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -247,7 +279,8 @@ __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float*
     load8<KCONTIG>(X, ld, r0 + rr, p0 + cc * 8, rows, k, vec, x[it]);
   }
   __syncthreads();
-  uint8_t* blk = panel + ((size_t)kc * rows_alloc + r0) * 128;
+  const size_t boff = ((size_t)kc * rows_alloc + r0) * 128;
+  uint8_t* blk = panel + boff;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     int rr, cc;
@@ -255,7 +288,10 @@ __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float*
     uint32_t mx = 0u;
 #pragma unroll
     for (int q = 0; q < 8; ++q) mx = max(mx, __float_as_uint(x[it][q]) & 0x7FFFFFFFu);
-    if (r0 + rr < rows_alloc) store_split8(blk, rr, cc, x[it]);
+    if (r0 + rr < rows_alloc) {
+      if (panel2) store_split8_3(blk, panel2 + boff, rr, cc, x[it]);
+      else store_split8(blk, rr, cc, x[it]);
+    }
     if (KCONTIG) {
       mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
       mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
@@ -272,8 +308,8 @@ __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float*
 // with x' = x * 2^-e.  A block without such rows returns at once.
 __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                               bool kcontig, const uint32_t* __restrict__ amax,
-                                              uint8_t* __restrict__ panel, int64_t rows_alloc, int64_t nkc,
-                                              int64_t rb, int* se) {
+                                              uint8_t* __restrict__ panel, uint8_t* __restrict__ panel2,
+                                              int64_t rows_alloc, int64_t nkc, int64_t rb, int* se) {
   const int64_t r0 = rb * 128;
   const int tid = threadIdx.x;
   int e = 0;
@@ -281,7 +317,8 @@ __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const flo
   if (tid < 128) se[tid] = e;
   if (!__syncthreads_or(e != 0)) return;
   for (int64_t kc = 0; kc < nkc; ++kc) {
-    uint8_t* blk = panel + ((size_t)kc * rows_alloc + r0) * 128;
+    const size_t boff = ((size_t)kc * rows_alloc + r0) * 128;
+    uint8_t* blk = panel + boff;
     for (int it = 0; it < 2; ++it) {
       const int idx = tid + 256 * it, rr = idx >> 2, cc = idx & 3;
       const int er = se[rr];
@@ -293,7 +330,8 @@ __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const flo
         const float v = (r < rows && p + q < k) ? (kcontig ? X[r * ld + p + q] : X[r + (p + q) * ld]) : 0.f;
         x[q] = isfinite(v) ? scale_pow2(v, er) : v;
       }
-      store_split8(blk, rr, cc, x);
+      if (panel2) store_split8_3(blk, panel2 + boff, rr, cc, x);
+      else store_split8(blk, rr, cc, x);
     }
   }
 }

@@ -102,7 +102,7 @@ def lib():
             L.gbgemm_status_string.restype = ctypes.c_char_p
             L.gbgemm_panel_bytes.argtypes = [i64, i64]
             L.gbgemm_panel_bytes.restype = ctypes.c_size_t
-            L.gbgemm_split_pack.argtypes = [vp, c, c, i64, i64, vp, i64, vp, vp]
+            L.gbgemm_split_pack.argtypes = [vp, c, c, i64, i64, vp, i64, vp, vp, vp]
             L.gbgemm_sgemm_split_noalloc.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64,
                                                      vp]
             PP = ctypes.POINTER(Problem)
@@ -304,9 +304,9 @@ class Handle:
             ctypes.byref(r)))
         return r.value
 
-    def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel) -> int:
+    def split_pack(self, which, trans, rows, k, X, ldx, amax_bits, panel, panel2=None) -> int:
         return lib().gbgemm_split_pack(self._h, which.encode(), trans.encode(), int(rows), int(k), _ptr(X), int(ldx),
-                                       _ptr(amax_bits), _ptr(panel))
+                                       _ptr(amax_bits), _ptr(panel), _ptr(panel2))
 
 
 class GroupedPlan:

@@ -173,3 +173,35 @@ def test_grouped_uneven_batch_4096(h):
     assert st["n_split"] > 1000 and st["n_simt"] > 1000
     b.check()
     plan.close()
+
+
+def test_grouped_badly_scaled_rows_take_the_fallback(h):
+    """Problems whose rows of op(A) or columns of op(B) are badly scaled (max
+    |x| outside [2^-48, 2^48)): the split-on-load tiles touching them are
+    finished by the SIMT fallback; every result stays within the bound."""
+    import torch
+    from paper_1608_05265_gb300 import gbgemm
+    specs = [("N", "N", 300, 200, 256, 1.0, 0.5), ("T", "N", 200, 300, 384, 1.0, 0.0),
+             ("N", "T", 130, 129, 200, -1.0, 1.0), ("T", "T", 64, 64, 128, 2.0, 0.0)]
+    b = Batch(specs, 81)
+    # scale some stored rows of A by 2^60 and some of B by 2^-70
+    for g, (ta, tb, m, n, k, alpha, beta) in enumerate(specs):
+        A, lda, B, ldb, C, ldc = b.host[g]
+        ar, ac = synth.op_shape(ta, m, k)
+        br, bc = synth.op_shape(tb, k, n)
+        A = A.copy(); B = B.copy()
+        La = A[: lda * ac].reshape(ac, lda)
+        La[:, 3:ar:17] *= np.float32(2.0**60)
+        Lb = B[: ldb * bc].reshape(bc, ldb)
+        Lb[1:bc:23, :br] *= np.float32(2.0**-70)
+        b.host[g] = (A, lda, B, ldb, C, ldc)
+        b.dev[g][0].copy_(torch.from_numpy(A))
+        b.dev[g][1].copy_(torch.from_numpy(B))
+    for cfg in (gbgemm.CFG_SPLIT_BN64, gbgemm.CFG_SPLIT_BN128):
+        b.reset_c()
+        plan = gbgemm.GroupedPlan(h, b.probs, configs=[cfg] * len(specs))
+        plan.run(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert h.get_device_status() == 0
+        b.check()
+        plan.close()

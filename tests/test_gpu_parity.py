@@ -224,7 +224,7 @@ def unpack_panel(panel: np.ndarray, rows: int, k: int):
 
 
 @pytest.mark.parametrize("which,trans", [("A", "N"), ("A", "T"), ("B", "N"), ("B", "T")])
-@pytest.mark.parametrize("rows,k", [(1, 1), (130, 37), (300, 300), (257, 1000)])
+@pytest.mark.parametrize("rows,k", [(1, 1), (130, 37), (300, 300), (257, 1000), (200, 600)])
 def test_split_pack_bit_exact(h, which, trans, rows, k):
     import torch
     from paper_1608_05265_gb300 import gbgemm
@@ -235,14 +235,19 @@ def test_split_pack_bit_exact(h, which, trans, rows, k):
     dX = dev(X)
     amax = torch.zeros(rows, dtype=torch.int32, device="cuda")
     panel = torch.full((gbgemm.panel_bytes(rows, k),), 0x5A, dtype=torch.uint8, device="cuda")
-    assert h.split_pack(which, trans, rows, k, dX, ld, amax, panel) == 0
+    panel2 = torch.full((gbgemm.panel_bytes(rows, k),), 0x5A, dtype=torch.uint8, device="cuda")
+    assert h.split_pack(which, trans, rows, k, dX, ld, amax, panel, panel2) == 0
     torch.cuda.synchronize()
-    e, hi, lo = O.split_operand(which, trans, rows, k, X, ld)
+    e, hi, lo, lo3 = O.split_operand3(which, trans, rows, k, X, ld)
     ghi, glo = unpack_panel(panel.cpu().numpy(), rows, k)
     assert np.array_equal(ghi[:rows, :k], hi)
     assert np.array_equal(glo[:rows, :k], lo)
     assert np.all(ghi[rows:] == 0) and np.all(glo[rows:] == 0)
     assert np.all(ghi[:, k:] == 0) and np.all(glo[:, k:] == 0)
+    if k < 512:  # three-part split: [lo3 | 0] in the second panel
+        g3, gz = unpack_panel(panel2.cpu().numpy(), rows, k)
+        assert np.array_equal(g3[:rows, :k], lo3)
+        assert np.all(g3[rows:] == 0) and np.all(g3[:, k:] == 0) and np.all(gz == 0)
     am = amax.cpu().numpy().view(np.uint32)
     L = synth.logical(X, sr, sc, ld)
     vec = L.T if kcontig else L
