@@ -1,10 +1,9 @@
 // Grouped split-BF16 GEMM with the split done on load ("fused"): no hi/lo
-// panels in HBM.  Converter warps stream FP32 tiles of op(A) and op(B) from
-// the caller's matrices into a shared-memory staging ring with cp.async
-// (4-byte copies: any leading dimension and alignment), split every value
-// into BF16 hi and lo in shared memory in the tensor cores' swizzled K-major
-// layout, and hand each chunk to the MMA warp; the accumulator and epilogue
-// work as in split_gemm_kernel.
+// panels in HBM.  Converter warps copy FP32 slices of op(A) and op(B) from
+// the caller's matrices into shared memory with cp.async (4-byte copies: any
+// leading dimension and alignment), split every value into BF16 hi and lo in
+// the tensor cores' swizzled K-major layout, and hand each 32-deep k chunk to
+// the MMA warp; the accumulator and epilogue work as in split_gemm_kernel.
 //
 // Scaling.  A tile reads the whole k extent of its 128 rows of op(A) and its
 // BN columns of op(B), so by its last chunk it knows their exact max |x|.
@@ -15,12 +14,18 @@
 // SIMT path meets the acceptance bound at any scale).
 //
 // Roles (one CTA per SM, 416 threads):
-//   warps 0-3   converters: cp.async copies kFusedAhead chunks ahead of the
-//               chunk they convert; named barrier 1 among the 128 threads;
-//   warp 4      TMEM owner (256 columns: two 128 x 128 accumulators); lane 0
+//   warps 0-7   converters.  Warp w owns k sub-chunk cc = w % 4 (8 values)
+//               of the 32-row blocks w / 4 and w / 4 + 2 of op(A) and of
+//               op(B): it copies exactly the values it converts, through a
+//               private 4-stage cp.async ring, so the converter warps never
+//               wait for one another; each signals the MMA warp per chunk;
+//   warp 8      TMEM owner (256 columns: two 128 x 128 accumulators); lane 0
 //               issues the MMAs and commits;
-//   warps 5-12  epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 for half of
+//   warps 9-12  epilogue: warp w reads TMEM lanes 32*(w%4) .. +31, all of
 //               the tile's columns.
+// Row maxima of a tile are combined across the converter warps with 64-bit
+// shared-memory atomicMax on (tile epoch << 32 | max |x| bits), so a slot
+// needs no reset between tiles: a newer epoch always wins.
 #pragma once
 
 #include "split_device.cuh"
@@ -28,18 +33,28 @@
 namespace gbg {
 namespace {
 
-constexpr int kFusedConvThreads = 128;
-constexpr int kFusedEpiWarps = 8;
-constexpr int kFusedThreads = kFusedConvThreads + 32 + 32 * kFusedEpiWarps;
+constexpr int kFusedConvWarps = 8;
+constexpr int kFusedMmaWarp = kFusedConvWarps;
+constexpr int kFusedEpiWarps = 4;
+constexpr int kFusedThreads = 32 * kFusedConvWarps + 32 + 32 * kFusedEpiWarps;
 constexpr int kFusedMaxBN = 128;
-constexpr int kFusedStagesF = 4;                     // FP32 staging stages
+constexpr int kFusedStagesF = 4;                     // FP32 stages per converter warp
 constexpr int kFusedAhead = kFusedStagesF - 1;       // chunks of copies in flight ahead of conversion
 constexpr int kFusedStagesB = 2;                     // BF16 stages consumed by the MMA
-constexpr int kStagePitch = 33;                      // floats per staged row (32 + 1 against bank conflicts)
-constexpr uint32_t kFusedStageF = 2u * 128u * kStagePitch * 4u;          // A rows + B rows
+constexpr int kMaxSlots = 4;                         // tile slots of row maxima
+// One converter warp's FP32 stage: its 64 rows x 8 k of op(A) (2 KiB), then
+// of op(B).  A k-contiguous operand is staged [row][8 k], the two 16-byte
+// halves of a row swapped on rows with bit 2 set (so that 8 consecutive
+// rows read the same half from 8 distinct bank groups); a row-contiguous
+// operand is staged [k][64 rows].
+constexpr uint32_t kWarpPart = 2048;
+constexpr uint32_t kWarpStage = 2 * kWarpPart;
 constexpr uint32_t kFusedStageB = 2u * (uint32_t)kBlockBytes;            // A block + B block (128 rows each)
 constexpr uint32_t kFusedTmemCols = 2 * kFusedMaxBN;
-constexpr int kFusedSmemBytes = (int)(kFusedStagesB * kFusedStageB + kFusedStagesF * kFusedStageF) + 1024 + 2048;
+constexpr uint32_t kOffF32 = kFusedStagesB * kFusedStageB;
+constexpr uint32_t kOffSlots = kOffF32 + kFusedConvWarps * kFusedStagesF * kWarpStage;
+constexpr uint32_t kOffBars = kOffSlots + kMaxSlots * 256 * 8;
+constexpr int kFusedSmemBytes = (int)kOffBars + 256 + 1024;  // + barriers, TMEM holder; + 1024-byte alignment
 
 // One problem of the batch on the fused path.
 struct FusedGroup {
@@ -62,62 +77,118 @@ struct FusedSched {
   int4* fb_items;             // fallback list: (SIMT problem, 128-row tile, 64-column tile, 0)
 };
 
-__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+// 4-byte asynchronous copy global -> shared; bytes = 0 writes a zero and
+// reads nothing.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void st_shared_zero(uint32_t dst) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(dst), "r"(0u) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Stage the FP32 rows [r0, r0 + nrows) x k [p0, p0 + 32) of an operand (128
-// threads, 32 copies each for 128 rows); out-of-range elements become zero.
-__device__ __forceinline__ void stage_rows(uint32_t dst, const float* X, int64_t ld, bool kcontig, int64_t rows,
-                                           int64_t k, int64_t r0, int64_t p0, int nrows, int t) {
-  const int w = t >> 5, lane = t & 31;
-  if (kcontig) {
-    // one row per warp instruction: 32 consecutive k of row r
-    for (int rr = w; rr < nrows; rr += 4) {
-      const int64_t r = r0 + rr, p = p0 + lane;
-      const bool ok = r < rows && p < k;
-      cp_async4(dst + (uint32_t)(rr * kStagePitch + lane) * 4u, ok ? X + r * ld + p : X, ok);
+// Word index of (row ri, k kk) in a k-contiguous part.
+__device__ __forceinline__ uint32_t kpart_word(int ri, int kk) {
+  return (uint32_t)(ri * 8 + ((((kk >> 2) ^ (ri >> 2)) & 1) << 2) + (kk & 3));
+}
+
+// Stage a converter warp's part of one operand: k [pb, pb + 8) of the rows
+// R + lane-row and R + 64 + lane-row (nb = 2), or only the first 32 (nb = 1).
+// Rows past the matrix are clamped into it and copied as zeros (bytes 0);
+// k past its end likewise.
+//   row-contiguous (element (r, p) at X[r + p*ld]): lane l takes row R + l
+//     (+ 64); one warp instruction reads 128 consecutive bytes;
+//   k-contiguous (element (r, p) at X[r*ld + p]): lane l takes row
+//     R + 4 j + l / 8, k pb + l % 8; one warp instruction reads 4 rows x 32
+//     consecutive bytes.
+__device__ __forceinline__ void stage_part(uint32_t dst, const float* X, int64_t ld, bool kcontig, int64_t rows,
+                                           int64_t k, int64_t R, int64_t pb, int nb, int lane) {
+  if (!kcontig) {
+    int64_t rc[2];
+    uint32_t sz[2];
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi) {
+      const int64_t r = R + 64 * bi + lane;
+      const bool rv = r < rows;
+      rc[bi] = rv ? r : rows - 1;
+      sz[bi] = rv ? 4u : 0u;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int64_t p = pb + kk;
+      const uint32_t d = dst + (uint32_t)(kk * 64 + lane) * 4u;
+      if (p < k) {  // warp-uniform
+        const float* col = X + p * ld;
+        cp_async4(d, col + rc[0], sz[0]);
+        if (nb == 2) cp_async4(d + 128u, col + rc[1], sz[1]);
+      } else {
+        st_shared_zero(d);
+        if (nb == 2) st_shared_zero(d + 128u);
+      }
     }
   } else {
-    // 32 consecutive rows of one k per warp instruction
-    for (int g = 0; g < nrows / 32; ++g) {
-      const int rr = g * 32 + lane;
-      const int64_t r = r0 + rr;
-#pragma unroll 4
-      for (int pp = w; pp < 32; pp += 4) {
-        const int64_t p = p0 + pp;
-        const bool ok = r < rows && p < k;
-        cp_async4(dst + (uint32_t)(rr * kStagePitch + pp) * 4u, ok ? X + r + p * ld : X, ok);
+    const int rs = lane >> 3, kk = lane & 7;
+    const int64_t p = pb + kk;
+    const bool pv = p < k;
+    const float* src = X + (pv ? p : k - 1);
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi) {
+      if (bi < nb) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int ri = bi * 32 + 4 * j + rs;
+          const int64_t r = R + 64 * bi + 4 * j + rs;
+          const bool rv = r < rows;
+          cp_async4(dst + kpart_word(ri, kk) * 4u, src + (rv ? r : rows - 1) * ld, (rv && pv) ? 4u : 0u);
+        }
       }
     }
   }
 }
 
-// Split 8 staged values of row rr (chunk cc) into the swizzled BF16 block;
-// returns their max |x| bit pattern.
-__device__ __forceinline__ uint32_t convert8(const float* srow, uint8_t* blk, int rr, int cc) {
-  uint32_t hw[4], lw[4], mx = 0u;
+// Split the 8 staged values of one (row, 8-wide k sub-chunk) item into the
+// swizzled BF16 block (hi at hi_dst, lo at lo_dst); returns max(m, max |x|).
+// Non-finite x gets lo = 0 (an infinity would otherwise give lo = NaN).
+template <bool KCONTIG>
+__device__ __forceinline__ float convert_item(const uint8_t* part, int ri, uint8_t* hi_dst, uint8_t* lo_dst, float m) {
+  float x[8];
+  if (KCONTIG) {
+    const float* row = reinterpret_cast<const float*>(part) + ri * 8;
+    const int sw = (ri >> 2) & 1;
+    const float4 u = *reinterpret_cast<const float4*>(row + 4 * sw);         // k 0-3
+    const float4 v = *reinterpret_cast<const float4*>(row + 4 * (sw ^ 1));   // k 4-7
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+    x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
+  } else {
+    const float* col = reinterpret_cast<const float*>(part) + ri;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = col[q * 64];
+  }
+  float mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) mx = fmaxf(mx, fabsf(x[q]));
+  uint32_t hw[4], lw[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const float x0 = srow[cc * 8 + 2 * q], x1 = srow[cc * 8 + 2 * q + 1];
-    mx = max(mx, max(__float_as_uint(x0) & 0x7FFFFFFFu, __float_as_uint(x1) & 0x7FFFFFFFu));
-    const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-    const float2 hf = __bfloat1622float2(h2);
-    __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-    uint32_t lb = *reinterpret_cast<uint32_t*>(&l2);
-    if (!isfinite(x0)) lb &= 0xFFFF0000u;  // non-finite x: lo = 0
-    if (!isfinite(x1)) lb &= 0x0000FFFFu;
-    hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
-    lw[q] = lb;
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+    const uint32_t hb = *reinterpret_cast<const uint32_t*>(&h2);
+    const float h0 = __uint_as_float(hb << 16), h1 = __uint_as_float(hb & 0xFFFF0000u);
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * q] - h0, x[2 * q + 1] - h1);
+    hw[q] = hb;
+    lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
   }
-  const int sw = rr & 7;
-  *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-  *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  return mx;
+  if (!(mx < __int_as_float(0x7F800000))) {  // rare: an infinity among the 8
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!isfinite(x[2 * q])) lw[q] &= 0xFFFF0000u;
+      if (!isfinite(x[2 * q + 1])) lw[q] &= 0x0000FFFFu;
+    }
+  }
+  *reinterpret_cast<uint4*>(hi_dst) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(lo_dst) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  return fmaxf(m, mx);
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
@@ -126,37 +197,33 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;
   uint8_t* const base_ptr = smem_raw + (base - raw_addr);
-  const uint32_t sB16 = base;                                             // kFusedStagesB x (A block | B block)
-  const uint32_t sF32 = base + kFusedStagesB * kFusedStageB;              // kFusedStagesF x (A rows | B rows)
-  const uint32_t misc = sF32 + kFusedStagesF * kFusedStageF;              // maxima, flags, barriers
-  uint32_t* rowmax = reinterpret_cast<uint32_t*>(base_ptr + (misc - base));   // 256 words
-  int* flags = reinterpret_cast<int*>(rowmax + 256);                           // 4-entry ring
-  int* tile_bad = flags + 4;
-  volatile int* conv_go = flags + 5;  // thread 0's go/stop decision for the converters, read after a barrier
-  const uint32_t bar0 = (misc + 256 * 4 + 64 + 7) & ~7u;
+  const uint32_t sB16 = base;                       // kFusedStagesB x (A block | B block)
+  const uint32_t sF32 = base + kOffF32;             // per converter warp: kFusedStagesF x (A part | B part)
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(base_ptr + kOffSlots);  // kMaxSlots x 256
+  const uint32_t bar0 = base + kOffBars;
   auto bfull = [&](int s) { return bar0 + 8u * s; };
   auto bempty = [&](int s) { return bar0 + 8u * (kFusedStagesB + s); };
   auto accf = [&](int b) { return bar0 + 8u * (2 * kFusedStagesB + b); };
   auto acce = [&](int b) { return bar0 + 8u * (2 * kFusedStagesB + 2 + b); };
-  auto flagbar = [&](int i) { return bar0 + 8u * (2 * kFusedStagesB + 4 + i); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * kFusedStagesB + 8);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(base_ptr + (bar0 - base) + 8 * (2 * kFusedStagesB + 9));
+  auto mxfull = [&](int i) { return bar0 + 8u * (2 * kFusedStagesB + 4 + i); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kFusedStagesB + 4 + kMaxSlots);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(base_ptr + kOffBars + 8 * (2 * kFusedStagesB + 5 + kMaxSlots));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_items = S.n_items;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kFusedStagesB; ++s) { mbar_init(bfull(s), 1); mbar_init(bempty(s), 1); }
+    for (int s = 0; s < kFusedStagesB; ++s) { mbar_init(bfull(s), kFusedConvWarps); mbar_init(bempty(s), 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(accf(b), 1); mbar_init(acce(b), kFusedEpiWarps); }
-    for (int i = 0; i < 4; ++i) mbar_init(flagbar(i), 1);
+    for (int i = 0; i < kMaxSlots; ++i) mbar_init(mxfull(i), 32 * kFusedConvWarps);
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (threadIdx.x < 256) rowmax[threadIdx.x] = 0u;
-  if (warp == 4) {
+  for (int i = threadIdx.x; i < kMaxSlots * 256; i += blockDim.x) slots[i] = 0ull;
+  if (warp == kFusedMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  ::"r"(smem_u32(tmem_holder)), "r"(kFusedTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -166,93 +233,112 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
-  auto group_of = [&](int t, int4& it) -> const FusedGroup& {
+  // the item's problem, copied into registers (the cp.async asm statements
+  // clobber memory, so a reference would be reloaded after each of them)
+  auto group_of = [&](int t, int4& it) -> FusedGroup {
     it = S.items[t];
     return S.groups[it.x];
   };
 
-  if (warp < 4) {
+  if (warp < kFusedConvWarps) {
     // ---------------- converters ----------------
-    const int t = threadIdx.x;
+    const int cc = warp & 3;         // k sub-chunk: k 8 cc .. 8 cc + 7 of every chunk
+    const int b0 = warp >> 2;        // 32-row blocks b0 and b0 + 2 of op(A) and of op(B)
+    const uint32_t my_f32 = sF32 + (uint32_t)warp * kFusedStagesF * kWarpStage;
     // issue cursor (item, k chunk) runs kFusedAhead chunks ahead of the convert cursor
     int it_i = blockIdx.x, kc_i = 0;
     int issued = 0;
+    int4 iti = make_int4(0, 0, 0, 0);
+    FusedGroup Gi{};
+    if (it_i < num_items) Gi = group_of(it_i, iti);
     auto issue_next = [&]() {
       if (it_i < num_items) {
-        int4 it;
-        const FusedGroup& G = group_of(it_i, it);
-        const uint32_t st = sF32 + (uint32_t)(issued % kFusedStagesF) * kFusedStageF;
-        const int64_t p0 = (int64_t)kc_i * 32;
-        stage_rows(st, G.A, G.lda, G.a_kcontig != 0, G.m, G.k, (int64_t)it.y * 128, p0, 128, t);
-        stage_rows(st + 128u * kStagePitch * 4u, G.B, G.ldb, G.b_kcontig != 0, G.n, G.k, (int64_t)it.z * G.bn, p0,
-                   G.bn, t);
-        if (++kc_i == G.nkc) { kc_i = 0; it_i += gridDim.x; }
+        const uint32_t st = my_f32 + (uint32_t)(issued % kFusedStagesF) * kWarpStage;
+        const int64_t pb = (int64_t)kc_i * 32 + cc * 8;
+        stage_part(st, Gi.A, Gi.lda, Gi.a_kcontig != 0, Gi.m, Gi.k, (int64_t)iti.y * 128 + 32 * b0, pb, 2, lane);
+        stage_part(st + kWarpPart, Gi.B, Gi.ldb, Gi.b_kcontig != 0, Gi.n, Gi.k, (int64_t)iti.z * Gi.bn + 32 * b0, pb,
+                   Gi.bn == 128 ? 2 : 1, lane);
+        if (++kc_i == Gi.nkc) {
+          kc_i = 0;
+          it_i += gridDim.x;
+          if (it_i < num_items) Gi = group_of(it_i, iti);
+        }
       }
       cp_async_commit();  // an empty group keeps the group count in step
       ++issued;
     };
     for (int a = 0; a < kFusedAhead; ++a) issue_next();
-    uint32_t my_max[8];
+
+    // This lane's conversion items: row ri = 32 bi + lane of the warp's part
+    // (tile row 32 (b0 + 2 bi) + lane), bi = 0, 1 of op(A) and of op(B).
+    uint32_t hi_off[4], lo_off[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) my_max[i] = 0u;
+    for (int i = 0; i < 4; ++i) {
+      const int trow = 32 * (b0 + 2 * (i & 1)) + lane;  // row within the operand's tile
+      const uint32_t rowb = (uint32_t)(i >> 1) * (uint32_t)kBlockBytes + (uint32_t)trow * 128u;
+      hi_off[i] = rowb + ((uint32_t)(cc ^ (trow & 7)) << 4);
+      lo_off[i] = rowb + ((uint32_t)((cc + 4) ^ (trow & 7)) << 4);
+    }
+    float my_max[4] = {0.f, 0.f, 0.f, 0.f};
     int g = 0, ordinal = 0;
     bool ok = true;
     for (int tt = blockIdx.x; tt < num_items && ok; tt += gridDim.x, ++ordinal) {
       int4 it;
-      const FusedGroup& G = group_of(tt, it);
-      const int items = (128 + G.bn) * 4;  // (row, 8-wide chunk) items: A rows then B rows
+      const FusedGroup G = group_of(tt, it);
+      const bool a_k = G.a_kcontig != 0, b_k = G.b_kcontig != 0;
+      const bool b_two = G.bn == 128;  // op(B) has row blocks b0 and b0 + 2
       for (int kc = 0; kc < G.nkc; ++kc, ++g) {
         issue_next();
         cp_async_wait<kFusedAhead>();  // chunk g's copies by this thread have landed
+        __syncwarp();                  // ... and those of the other lanes
         const int sb = g % kFusedStagesB;
-        if (t == 0) {
-          const bool go = mbar_wait(bempty(sb), (uint32_t)(((g / kFusedStagesB) & 1) ^ 1), abort_flag, timeout_ns);
+        int go = 1;
+        if (lane == 0) {
+          go = mbar_wait_hint(bempty(sb), (uint32_t)(((g / kFusedStagesB) & 1) ^ 1), abort_flag, timeout_ns, 1000u)
+                   ? 1 : 0;
           if (!go) raise_status(status, abort_flag);
-          *conv_go = (go && !*abort_flag) ? 1 : 0;
         }
-        conv_bar();  // every converter's copies of chunk g are visible; the BF16 stage is free
-        if (!*conv_go) { ok = false; break; }  // the same decision in all 128 threads
-        const float* stf = reinterpret_cast<const float*>(base_ptr + (sF32 - base) + (uint32_t)(g % kFusedStagesF) * kFusedStageF);
+        if (!__shfl_sync(0xFFFFFFFFu, go, 0)) { ok = false; break; }
+        const uint8_t* stf = base_ptr + (my_f32 - base) + (uint32_t)(g % kFusedStagesF) * kWarpStage;
         uint8_t* stb = base_ptr + (sB16 - base) + (uint32_t)sb * kFusedStageB;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int item = t + 128 * i;
-          if (item < items) {
-            const int row = item >> 2, cc = item & 3;  // rows 0-127: op(A); 128-: op(B)
-            const uint32_t mx = convert8(stf + row * kStagePitch, stb, row, cc);
-            my_max[i] = max(my_max[i], mx);
-          }
+        if (a_k) {
+          my_max[0] = convert_item<true>(stf, lane, stb + hi_off[0], stb + lo_off[0], my_max[0]);
+          my_max[1] = convert_item<true>(stf, 32 + lane, stb + hi_off[1], stb + lo_off[1], my_max[1]);
+        } else {
+          my_max[0] = convert_item<false>(stf, lane, stb + hi_off[0], stb + lo_off[0], my_max[0]);
+          my_max[1] = convert_item<false>(stf, 32 + lane, stb + hi_off[1], stb + lo_off[1], my_max[1]);
+        }
+        if (b_k) {
+          my_max[2] = convert_item<true>(stf + kWarpPart, lane, stb + hi_off[2], stb + lo_off[2], my_max[2]);
+          if (b_two)
+            my_max[3] = convert_item<true>(stf + kWarpPart, 32 + lane, stb + hi_off[3], stb + lo_off[3], my_max[3]);
+        } else {
+          my_max[2] = convert_item<false>(stf + kWarpPart, lane, stb + hi_off[2], stb + lo_off[2], my_max[2]);
+          if (b_two)
+            my_max[3] = convert_item<false>(stf + kWarpPart, 32 + lane, stb + hi_off[3], stb + lo_off[3], my_max[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // BF16 writes -> tensor core reads
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bfull(sb));
         if (kc == G.nkc - 1) {
-          // tile complete: exact max |x| of its vectors; flag the tile if any is badly scaled
+          // tile complete: contribute this lane's row maxima to the tile's slot
+          // (rows 0-127 op(A), 128-255 op(B)) and report to the epilogue
+          const unsigned long long epoch = (unsigned long long)(ordinal + 1) << 32;
+          unsigned long long* slot = slots + (ordinal % kMaxSlots) * 256;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int item = t + 128 * i;
-            if (item < items && my_max[i] != 0u) atomicMax(&rowmax[item >> 2], my_max[i]);
-            my_max[i] = 0u;
+          for (int i = 0; i < 4; ++i) {
+            if (i < 3 || b_two) {
+              const int srow = (i >> 1) * 128 + 32 * (b0 + 2 * (i & 1)) + lane;
+              atomicMax(slot + srow, epoch | __float_as_uint(my_max[i]));
+            }
+            my_max[i] = 0.f;
           }
-          if (t == 0) *tile_bad = 0;
-          conv_bar();
-          const int64_t rA = (int64_t)it.y * 128 + t, rB = (int64_t)it.z * G.bn + t;
-          int bad = 0;
-          if (rA < G.m && scale_exp_from_bits(rowmax[t]) != 0) bad = 1;
-          if (t < G.bn && rB < G.n && scale_exp_from_bits(rowmax[128 + t]) != 0) bad = 1;
-          if (bad) atomicOr(tile_bad, 1);
-          conv_bar();
-          rowmax[t] = 0u;
-          rowmax[128 + t] = 0u;
-          if (t == 0) {
-            flags[ordinal & 3] = *tile_bad;
-            mbar_arrive(flagbar(ordinal & 3));
-          }
+          mbar_arrive(mxfull(ordinal % kMaxSlots));
         }
-        conv_bar();  // all conversions of chunk g done: its FP32 stage may be refilled
-        if (t == 0) mbar_arrive(bfull(sb));
       }
     }
     cp_async_wait<0>();
-  } else if (warp == 4) {
+  } else if (warp == kFusedMmaWarp) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int g = 0, abuf = 0;
@@ -260,9 +346,9 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
       bool ok = true;
       for (int tt = blockIdx.x; tt < num_items && ok; tt += gridDim.x) {
         int4 it;
-        const FusedGroup& G = group_of(tt, it);
+        const FusedGroup G = group_of(tt, it);
         const uint32_t idesc = make_idesc_bf16(128, G.bn);
-        if (!mbar_wait(acce(abuf), aphase ^ 1u, abort_flag, timeout_ns)) {
+        if (!mbar_wait_hint(acce(abuf), aphase ^ 1u, abort_flag, timeout_ns, 20000u)) {
           raise_status(status, abort_flag);
           break;
         }
@@ -270,7 +356,7 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
         const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * kFusedMaxBN);
         for (int kc = 0; kc < G.nkc; ++kc, ++g) {
           const int sb = g % kFusedStagesB;
-          if (!mbar_wait(bfull(sb), (uint32_t)((g / kFusedStagesB) & 1), abort_flag, timeout_ns)) {
+          if (!mbar_wait_hint(bfull(sb), (uint32_t)((g / kFusedStagesB) & 1), abort_flag, timeout_ns, 1000u)) {
             raise_status(status, abort_flag);
             ok = false;
             break;
@@ -302,29 +388,45 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
   } else {
     // ---------------- epilogue ----------------
     const int q = warp & 3;
-    const int half = (warp - 5) >> 2;
     int abuf = 0, ordinal = 0;
     uint32_t aphase = 0;
     for (int tt = blockIdx.x; tt < num_items; tt += gridDim.x, ++ordinal) {
       int4 it;
-      const FusedGroup& G = group_of(tt, it);
+      const FusedGroup G = group_of(tt, it);
+      const int sl = ordinal % kMaxSlots;
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(accf(abuf), aphase, abort_flag, timeout_ns) ? 1 : 0;
-      if (lane == 0 && ok) ok = mbar_wait(flagbar(ordinal & 3), (uint32_t)((ordinal >> 2) & 1), abort_flag, timeout_ns);
+      if (lane == 0) ok = mbar_wait_hint(accf(abuf), aphase, abort_flag, timeout_ns, 20000u) ? 1 : 0;
+      if (lane == 0 && ok)
+        ok = mbar_wait_hint(mxfull(sl), (uint32_t)((ordinal / kMaxSlots) & 1), abort_flag, timeout_ns, 20000u);
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
         if (lane == 0) raise_status(status, abort_flag);
         break;
       }
       tc_fence_after();
-      const int bad = flags[ordinal & 3];
       const int64_t m0 = (int64_t)it.y * 128, n0 = (int64_t)it.z * G.bn;
+      // every epilogue warp reads the whole slot and reaches the same verdict
+      const unsigned long long* slot = slots + sl * 256;
+      const uint32_t epoch = (uint32_t)(ordinal + 1);
+      int bad_l = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int srow = 32 * i + lane;
+        const bool is_a = srow < 128;
+        const int64_t r = is_a ? m0 + srow : n0 + (srow - 128);
+        const bool used = is_a ? (r < G.m) : (srow - 128 < G.bn && r < G.n);
+        if (used) {
+          const unsigned long long v = slot[srow];
+          if ((uint32_t)(v >> 32) != epoch || scale_exp_from_bits((uint32_t)v) != 0) bad_l = 1;
+        }
+      }
+      const bool bad = __any_sync(0xFFFFFFFFu, bad_l) != 0;
       if (bad) {
         // leave C to the SIMT fallback: one 128 x 64 SIMT tile per 64 columns
-        if (warp == 5 && lane == 0) {
+        if (warp == kFusedMmaWarp + 1 && lane == 0) {
           for (int c = 0; c < G.bn && n0 + c < G.n; c += 64) {
-            const int slot = atomicAdd(S.fb_count, 1);
-            S.fb_items[slot] = make_int4(G.simt_index, it.y, (int)((n0 + c) / 64), 0);
+            const int slot_i = atomicAdd(S.fb_count, 1);
+            S.fb_items[slot_i] = make_int4(G.simt_index, it.y, (int)((n0 + c) / 64), 0);
           }
         }
       } else {
@@ -332,8 +434,7 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
         const bool row_ok = i < G.m;
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kFusedMaxBN);
         float* const crow = G.C + i;
-        const int c_begin = half * (G.bn >> 1), c_end = c_begin + (G.bn >> 1);
-        for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+        for (int c0 = 0; c0 < G.bn; c0 += 32) {
           if (n0 + c0 >= G.n) break;  // warp-uniform
           const int jmax = (G.n - (n0 + c0) < 32) ? (int)(G.n - (n0 + c0)) : 32;
           float* cp = crow + (n0 + c0) * G.ldc;
@@ -362,7 +463,7 @@ fused_gemm_kernel(const FusedSched S, int* status, uint64_t timeout_ns) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 4) {
+  if (warp == kFusedMmaWarp) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kFusedTmemCols) : "memory");
   }
 }

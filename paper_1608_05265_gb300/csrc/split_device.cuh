@@ -172,6 +172,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0u;
 }
 
+// As mbar_try, but a thread whose phase is not complete may be suspended for
+// up to `hint_ns` (it resumes as soon as the phase completes): long waits
+// then take no issue slots from the warps doing work.
+__device__ __forceinline__ bool mbar_try_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0u;
+}
+
 // Wait for the phase of parity `parity` to complete.  Gives up (returns
 // false) once `timeout_ns` has passed or another role raised the abort flag.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t timeout_ns) {
@@ -180,6 +195,20 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 31u) == 0u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > timeout_ns) return false;
+    }
+  }
+}
+
+// mbar_wait with suspending polls (see mbar_try_hint); same limits.
+__device__ __noinline__ bool mbar_wait_hint(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                            uint64_t timeout_ns, uint32_t hint_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_hint(bar, parity, hint_ns)) return true;
+    if ((it & 7u) == 0u) {
       if (*abort_flag) return false;
       if (globaltimer() - t0 > timeout_ns) return false;
     }

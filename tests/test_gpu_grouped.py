@@ -175,14 +175,22 @@ def test_grouped_uneven_batch_4096(h):
     plan.close()
 
 
-def test_grouped_badly_scaled_rows_take_the_fallback(h):
+SCALED_SHORT_K = [("N", "N", 300, 200, 256, 1.0, 0.5), ("T", "N", 200, 300, 384, 1.0, 0.0),
+                  ("N", "T", 130, 129, 200, -1.0, 1.0), ("T", "T", 64, 64, 128, 2.0, 0.0)]
+# k >= 512: the split-on-load kernel, whose tiles fall back to SIMT
+SCALED_LONG_K = [("N", "N", 300, 200, 600, 1.0, 0.5), ("T", "N", 200, 300, 777, 1.0, 0.0),
+                 ("N", "T", 130, 129, 512, -1.0, 1.0), ("T", "T", 64, 64, 1000, 2.0, 0.0),
+                 ("N", "N", 257, 40, 530, 1.0, 0.0)]
+
+
+@pytest.mark.parametrize("specs", [SCALED_SHORT_K, SCALED_LONG_K], ids=["short_k", "long_k"])
+def test_grouped_badly_scaled_rows_take_the_fallback(h, specs):
     """Problems whose rows of op(A) or columns of op(B) are badly scaled (max
-    |x| outside [2^-48, 2^48)): the split-on-load tiles touching them are
-    finished by the SIMT fallback; every result stays within the bound."""
+    |x| outside [2^-48, 2^48)): the split kernels scale them (panels) or
+    leave the tiles touching them to the SIMT fallback (split on load);
+    every result stays within the bound."""
     import torch
     from paper_1608_05265_gb300 import gbgemm
-    specs = [("N", "N", 300, 200, 256, 1.0, 0.5), ("T", "N", 200, 300, 384, 1.0, 0.0),
-             ("N", "T", 130, 129, 200, -1.0, 1.0), ("T", "T", 64, 64, 128, 2.0, 0.0)]
     b = Batch(specs, 81)
     # scale some stored rows of A by 2^60 and some of B by 2^-70
     for g, (ta, tb, m, n, k, alpha, beta) in enumerate(specs):
@@ -205,3 +213,37 @@ def test_grouped_badly_scaled_rows_take_the_fallback(h):
         assert h.get_device_status() == 0
         b.check()
         plan.close()
+
+
+def test_grouped_long_k_infinities(h):
+    """An infinity in op(A) on the split-on-load path.  Its lo part is zero,
+    but inf * hi(b) + inf * lo(b) is NaN wherever lo(b) has the other sign,
+    so the split can only promise that the row it touches is non-finite (as
+    the FP64 result is); every other entry stays within the bound."""
+    import torch
+    from paper_1608_05265_gb300 import gbgemm
+    specs = [("N", "N", 150, 140, 640, 1.0, 0.0), ("T", "N", 90, 200, 520, 1.0, 0.0)]
+    b = Batch(specs, 82)
+    hits = []
+    for g, (ta, tb, m, n, k, alpha, beta) in enumerate(specs):
+        A, lda, B, ldb, C, ldc = b.host[g]
+        A = A.copy()
+        i, p = 7 + 11 * g, 300 + g
+        A[(i + p * lda) if ta == "N" else (p + i * lda)] = np.float32(np.inf)
+        b.host[g] = (A, lda, B, ldb, C, ldc)
+        b.dev[g][0].copy_(torch.from_numpy(A))
+        hits.append(i)
+    plan = gbgemm.GroupedPlan(h, b.probs, configs=[gbgemm.CFG_SPLIT_BN128] * len(specs))
+    plan.run(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert h.get_device_status() == 0
+    for g, ((ta, tb, m, n, k, alpha, beta), (A, lda, B, ldb, C, ldc), out) in enumerate(
+            zip(specs, b.host, b.results())):
+        c64, bnd = O.gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc)
+        got = synth.logical(out, m, n, ldc)
+        row = hits[g]
+        assert not np.any(np.isfinite(c64[row])) and not np.any(np.isfinite(got[row]))
+        others = np.ones(m, bool)
+        others[row] = False
+        assert O.error_ratio(got[others], c64[others], bnd[others]) <= 1.0
+    plan.close()
