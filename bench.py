@@ -38,6 +38,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sgemm TFLOP/s at 8192^3: 3xBF16 tensor vs FP32 SIMT, same GPU, same error bound"
+# DRAM bytes (read + write) of one split_gemm_kernel launch at 8192^3 NN, ld 8200,
+# from one ncu capture of the current kernel (profiles/split_gemm_8192_nn_traffic.md).
+GEMM_TRAFFIC_8192 = 2544064768 + 259988480
 UNIT = "TFLOP/s"
 N = 8192
 LD = N + 8
@@ -282,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flop / (gemm_avg_ms * 1e-3) / 1e12
     peak = bf16_peak / 3.0
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "split_gemm_kernel<256>",
+                "traffic": GEMM_TRAFFIC_8192, "kernel": "split_gemm_kernel<256>",
                 "note": (f"sgemm-equivalent 2mnk per launch / launch time; peak = {peak_src} bf16 dense "
                          f"{bf16_peak:.1f} TFLOP/s / 3 products (sustained {bf16_sust:.1f}/3 = "
                          f"{bf16_sust / 3:.1f}: frac {achieved / (bf16_sust / 3) if bf16_sust else float('nan'):.3f})"),
@@ -404,6 +407,12 @@ def run_extras(h, stream, flop8192):
         bufs.append((Ag, Bg, Cg))
         probs.append(gbgemm.problem(ta, tb, mm, nn, kk, 1.0, Ag, ar, Bg, br, 0.0, Cg, mm))
         fl_total += metrics.gemm_flops(mm, nn, kk)
+    # The equivalent single-large-GEMM rate: the batch's FLOPs at the 4096^3 rate
+    # of the path each problem is eligible for (split from k = 128, SIMT below),
+    # as one harmonic mean; it does not depend on the configurations a plan picks.
+    fl_split = sum(metrics.gemm_flops(mm, nn, kk) for (_, _, mm, nn, kk) in shapes if kk >= 128)
+    fs = fl_split / fl_total
+    equiv = 1.0 / (fs / rates["split"] + (1 - fs) / rates["simt"])
     grouped = {}
     sources = [("default", gbgemm.CONFIG_DEFAULT)]
     weights = os.path.join(ROOT, "paper_1608_05265_gb300", "data", "predictor_gb300.bin")
@@ -417,15 +426,15 @@ def run_extras(h, stream, flop8192):
         t_plan = time.time() - t0
         ms = _time(lambda: plan.run(stream), stream, 20)
         st = plan.stats()
-        fs = st["flops_split"] / max(st["flops_split"] + st["flops_simt"], 1.0)
-        equiv = 1.0 / (fs / rates["split"] + (1 - fs) / rates["simt"])
         tf = fl_total / (ms * 1e-3) / 1e12
-        grouped[name] = {"ms": ms, "tflops": tf, "plan_seconds": t_plan, "split_flop_share": fs,
-                         "equivalent_single_gemm_tflops": equiv, "fraction_of_equivalent": tf / equiv,
-                         "kernels_per_run": st["kernels_per_run"]}
+        grouped[name] = {"ms": ms, "tflops": tf, "plan_seconds": t_plan,
+                         "plan_split_flop_share": st["flops_split"] / max(st["flops_split"] + st["flops_simt"], 1.0),
+                         "fraction_of_equivalent": tf / equiv, "kernels_per_run": st["kernels_per_run"]}
         plan.close()
-    out["grouped_4096"] = dict(grouped, problems=4096, flops=fl_total,
-                               note="equivalent rate = flop-weighted harmonic mean of the 4096^3 split and SIMT rates")
+    out["grouped_4096"] = dict(grouped, problems=4096, flops=fl_total, split_eligible_flop_share=fs,
+                               equivalent_single_gemm_tflops=equiv,
+                               note=("equivalent rate = harmonic mean of the 4096^3 split and SIMT rates, weighted by "
+                                     "the FLOPs of problems with k >= 128 (split-eligible) and k < 128"))
     assert h.get_device_status() == 0
     return out
 
