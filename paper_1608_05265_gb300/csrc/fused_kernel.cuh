@@ -105,6 +105,7 @@ __device__ __forceinline__ uint32_t kpart_word(int ri, int kk) {
 //     consecutive bytes.
 __device__ __forceinline__ void stage_part(uint32_t dst, const float* X, int64_t ld, bool kcontig, int64_t rows,
                                            int64_t k, int64_t R, int64_t pb, int nb, int lane) {
+  const bool full_k = pb + 8 <= k;
   if (!kcontig) {
     int64_t rc[2];
     uint32_t sz[2];
@@ -115,33 +116,65 @@ __device__ __forceinline__ void stage_part(uint32_t dst, const float* X, int64_t
       rc[bi] = rv ? r : rows - 1;
       sz[bi] = rv ? 4u : 0u;
     }
+    const uint32_t d = dst + (uint32_t)lane * 4u;
+    if (full_k) {
+      // common case: one pointer walks the 8 columns
+      const float* q = X + pb * ld + rc[0];
+      const int64_t d1 = rc[1] - rc[0];
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const int64_t p = pb + kk;
-      const uint32_t d = dst + (uint32_t)(kk * 64 + lane) * 4u;
-      if (p < k) {  // warp-uniform
-        const float* col = X + p * ld;
-        cp_async4(d, col + rc[0], sz[0]);
-        if (nb == 2) cp_async4(d + 128u, col + rc[1], sz[1]);
-      } else {
-        st_shared_zero(d);
-        if (nb == 2) st_shared_zero(d + 128u);
+      for (int kk = 0; kk < 8; ++kk) {
+        cp_async4(d + kk * 256u, q, sz[0]);
+        if (nb == 2) cp_async4(d + kk * 256u + 128u, q + d1, sz[1]);
+        q += ld;
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int64_t p = pb + kk;
+        if (p < k) {  // warp-uniform
+          const float* col = X + p * ld;
+          cp_async4(d + kk * 256u, col + rc[0], sz[0]);
+          if (nb == 2) cp_async4(d + kk * 256u + 128u, col + rc[1], sz[1]);
+        } else {
+          st_shared_zero(d + kk * 256u);
+          if (nb == 2) st_shared_zero(d + kk * 256u + 128u);
+        }
       }
     }
   } else {
     const int rs = lane >> 3, kk = lane & 7;
-    const int64_t p = pb + kk;
-    const bool pv = p < k;
-    const float* src = X + (pv ? p : k - 1);
+    if (full_k && R + 64 * (nb - 1) + 32 <= rows) {
+      // common case: every row of the part inside the matrix; one pointer
+      // per 32-row block walks its rows 4 at a time
+      const uint32_t w_even = kpart_word(rs, kk), w_odd = kpart_word(4 + rs, kk) - 32;
+      const float* q = X + (R + rs) * ld + pb + kk;
+      const int64_t s4 = 4 * ld;
 #pragma unroll
-    for (int bi = 0; bi < 2; ++bi) {
-      if (bi < nb) {
+      for (int bi = 0; bi < 2; ++bi) {
+        if (bi < nb) {
+          const float* qb = q + 64 * bi * ld;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int ri = bi * 32 + 4 * j + rs;
-          const int64_t r = R + 64 * bi + 4 * j + rs;
-          const bool rv = r < rows;
-          cp_async4(dst + kpart_word(ri, kk) * 4u, src + (rv ? r : rows - 1) * ld, (rv && pv) ? 4u : 0u);
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t w = ((j & 1) ? w_odd : w_even) + (uint32_t)(bi * 32 + 4 * j) * 8u;
+            cp_async4(dst + w * 4u, qb, 4u);
+            qb += s4;
+          }
+        }
+      }
+    } else {
+      const int64_t p = pb + kk;
+      const bool pv = p < k;
+      const float* src = X + (pv ? p : k - 1);
+#pragma unroll
+      for (int bi = 0; bi < 2; ++bi) {
+        if (bi < nb) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int ri = bi * 32 + 4 * j + rs;
+            const int64_t r = R + 64 * bi + 4 * j + rs;
+            const bool rv = r < rows;
+            cp_async4(dst + kpart_word(ri, kk) * 4u, src + (rv ? r : rows - 1) * ld, (rv && pv) ? 4u : 0u);
+          }
         }
       }
     }

@@ -6,7 +6,7 @@
 // value: the MMA instruction descriptor, the B copy size and the epilogue
 // width all follow it, and shared memory and TMEM are sized for 256.
 //
-// Roles (one CTA per SM, 320 threads):
+// Roles (one CTA per SM, 576 threads):
 //   warp 0, lane 0  producer: per 32-deep k chunk one bulk async copy of the
 //                   128-row A block and one of the BN-row B rows into a
 //                   4-stage ring, signalled on the stage's "full" mbarrier;
@@ -17,8 +17,10 @@
 //                   "accumulator full" barrier -- the paper's Accumulator
 //                   (Section III-C): clear on the first k block, accumulate,
 //                   send the result after the last;
-//   warps 2-9       epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (the
-//                   tile rows it owns) for half of the tile's columns,
+//   warps 2-17      epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (the
+//                   tile rows it owns) for a quarter of the tile's columns
+//                   (at least 32; sixteen warps keep enough C loads in
+//                   flight for the HBM-bound shapes with beta != 0),
 //                   applies 2^(e_i + f_j), alpha and beta once and stores
 //                   column-major C with one 128-byte store per warp and
 //                   column (Section III-D: each core owns whole column
@@ -35,7 +37,7 @@ namespace {
 
 constexpr int kStages = 4;
 constexpr int kMaxBN = 256;
-constexpr int kEpiWarps = 8;                       // two per TMEM lane quadrant, each half of the columns
+constexpr int kEpiWarps = 16;                      // four per TMEM lane quadrant, each a quarter of the columns
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kTmemCols = 2 * kMaxBN;         // two accumulator buffers
@@ -289,13 +291,13 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   } else {
     // ---------------- epilogue ----------------
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int part = (warp - 2) >> 2;  // column part: 0 .. kEpiWarps / 4 - 1
     int abuf = 0;
     uint32_t aphase = 0;
     for (int t = blockIdx.x; t < num_items; t += gridDim.x) {
       const TileJob J = S.job(t);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(accf_bar(abuf), aphase, abort_flag, timeout_ns) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait_hint(accf_bar(abuf), aphase, abort_flag, timeout_ns, 2000u) ? 1 : 0;
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
         if (lane == 0) raise_status(status, abort_flag);
@@ -307,7 +309,8 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       const int ea = row_ok ? scale_exp_from_bits(J.amaxA[i]) : 0;
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kMaxBN);
       float* const crow = J.C + i;
-      const int c_begin = half * (J.bn >> 1), c_end = c_begin + (J.bn >> 1);
+      const int cols = (J.bn / (kEpiWarps / 4)) > 32 ? J.bn / (kEpiWarps / 4) : 32;
+      const int c_begin = part * cols, c_end = (c_begin + cols < J.bn) ? c_begin + cols : J.bn;
       for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         if (J.n0 + c0 >= J.n) break;  // warp-uniform
         const int jmax = (J.n - (J.n0 + c0) < 32) ? (int)(J.n - (J.n0 + c0)) : 32;

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) grouped_rescale_kernel(const PackTask* __
 // One launch per tile shape and (transpose, vector-load) variant, so each
 // launch is a fully specialised tile loop.
 template <int BM, int BN, bool TA, bool TB, bool VEC>
-__global__ void __launch_bounds__((BM / 8) * (BN / 8), (BM / 8) * (BN / 8) >= 256 ? 2 : 1)
+__global__ void __launch_bounds__((BM / 8) * (BN / 8), 512 / ((BM / 8) * (BN / 8)))
 grouped_simt_kernel(const int4* __restrict__ items, int n_items, const Problem* __restrict__ probs) {
   __shared__ __align__(16) SimtSmem<BM, BN> sm;
   // The item's problem descriptor is staged in shared memory so that its
@@ -96,7 +96,7 @@ void launch_grouped_simt(int variant, int grid, cudaStream_t s, const int4* item
 // SIMT fallback of the fused path: tiles listed on the device (count read at
 // run time), any transpose/alignment variant.
 template <int BM, int BN>
-__global__ void __launch_bounds__((BM / 8) * (BN / 8))
+__global__ void __launch_bounds__((BM / 8) * (BN / 8), 512 / ((BM / 8) * (BN / 8)))
 fallback_simt_kernel(const int4* __restrict__ items, const int* __restrict__ count, const Problem* __restrict__ probs) {
   __shared__ __align__(16) SimtSmem<BM, BN> sm;
   __shared__ Problem sp;
@@ -183,7 +183,11 @@ bool config_legal(const gbgemm_problem& q, int cfg) {
 
 int default_config(const gbgemm_problem& q) {
   if (q.k >= kSplitMinK && q.alpha != 0.0f) return q.n <= 64 ? GBGEMM_CFG_SPLIT_BN64 : GBGEMM_CFG_SPLIT_BN128;
-  return GBGEMM_CFG_SIMT_128x128;
+  // SIMT: the tile shape with the least padded area (ties to the larger tile)
+  auto area = [&](int64_t bm, int64_t bn) { return ((q.m + bm - 1) / bm) * bm * (((q.n + bn - 1) / bn) * bn); };
+  const int64_t a_big = area(128, 128), a_wide = area(128, 64), a_small = area(64, 64);
+  if (a_big <= a_wide && a_big <= a_small) return GBGEMM_CFG_SIMT_128x128;
+  return a_wide <= a_small ? GBGEMM_CFG_SIMT_128x64 : GBGEMM_CFG_SIMT_64x64;
 }
 
 int config_bn(int cfg) { return cfg == GBGEMM_CFG_SPLIT_BN64 ? 64 : cfg == GBGEMM_CFG_SPLIT_BN128 ? 128 : 256; }
@@ -450,7 +454,7 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
       F.fb_items = dfb;
       const int grid = (int)std::min<int64_t>((int64_t)fused_items.size(), P->num_sms);
       fused_gemm_kernel<<<grid, kFusedThreads, kFusedSmemBytes, capture_stream>>>(F, P->status, kTimeoutNs);
-      fallback_simt_kernel<128, 64><<<P->num_sms * 2, 128, 0, capture_stream>>>(dfb, dcount, dprobs);
+      fallback_simt_kernel<128, 64><<<P->num_sms * 4, 128, 0, capture_stream>>>(dfb, dcount, dprobs);
       P->kernels_per_run += 2;
     }
   }
@@ -459,7 +463,8 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     if (n == 0) continue;
     const int c = cv / 8, variant = cv % 8;
     const int4* di = reinterpret_cast<const int4*>(base + simt_items_r[cv].off);
-    const int per_sm = (c == GBGEMM_CFG_SIMT_128x128) ? 2 : 4;
+    // resident CTAs per SM at the kernels' 512-thread bound: 2, 4 or 8
+    const int per_sm = (c == GBGEMM_CFG_SIMT_128x128) ? 2 : (c == GBGEMM_CFG_SIMT_128x64) ? 4 : 8;
     const int grid = (int)std::min<int64_t>(n, (int64_t)P->num_sms * per_sm);
     cudaStream_t st = side[P->kernels_per_run % kSide];
     if (c == GBGEMM_CFG_SIMT_128x128) launch_grouped_simt<128, 128>(variant, grid, st, di, n, dprobs);

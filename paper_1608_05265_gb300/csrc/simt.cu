@@ -8,7 +8,7 @@ namespace {
 
 // 256-thread tiles keep two blocks per SM (at most 128 registers a thread).
 template <int BM, int BN, bool TA, bool TB, bool VEC>
-__global__ void __launch_bounds__((BM / 8) * (BN / 8), (BM / 8) * (BN / 8) >= 256 ? 2 : 1)
+__global__ void __launch_bounds__((BM / 8) * (BN / 8), 512 / ((BM / 8) * (BN / 8)))
 sgemm_simt_kernel(Problem P) {
   __shared__ __align__(16) SimtSmem<BM, BN> sm;
   simt_tile<BM, BN, TA, TB, VEC>(P, (int64_t)blockIdx.x * BM, (int64_t)blockIdx.y * BN, sm.As, sm.Bs);
