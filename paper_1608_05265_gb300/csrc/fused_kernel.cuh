@@ -17,7 +17,7 @@
 //   warps 0-7   converters.  Warp w owns k sub-chunk cc = w % 4 (8 values)
 //               of the 32-row blocks w / 4 and w / 4 + 2 of op(A) and of
 //               op(B): it copies exactly the values it converts, through a
-//               private 4-stage cp.async ring, so the converter warps never
+//               private 3-stage cp.async ring, so the converter warps never
 //               wait for one another; each signals the MMA warp per chunk;
 //   warp 8      TMEM owner (256 columns: two 128 x 128 accumulators); lane 0
 //               issues the MMAs and commits;
@@ -38,9 +38,9 @@ constexpr int kFusedMmaWarp = kFusedConvWarps;
 constexpr int kFusedEpiWarps = 4;
 constexpr int kFusedThreads = 32 * kFusedConvWarps + 32 + 32 * kFusedEpiWarps;
 constexpr int kFusedMaxBN = 128;
-constexpr int kFusedStagesF = 4;                     // FP32 stages per converter warp
+constexpr int kFusedStagesF = 3;                     // FP32 stages per converter warp
 constexpr int kFusedAhead = kFusedStagesF - 1;       // chunks of copies in flight ahead of conversion
-constexpr int kFusedStagesB = 2;                     // BF16 stages consumed by the MMA
+constexpr int kFusedStagesB = 3;                     // BF16 stages consumed by the MMA
 constexpr int kMaxSlots = 4;                         // tile slots of row maxima
 // One converter warp's FP32 stage: its 64 rows x 8 k of op(A) (2 KiB), then
 // of op(B).  A k-contiguous operand is staged [row][8 k], the two 16-byte
