@@ -373,53 +373,123 @@ def _time(fn, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def run_extras(h, stream, flop8192):
-    """Linpack-shaped update, grouped uneven batch and the 4096^3 rates they are
-    compared with.  Inputs generated on the device (seeded torch generators)."""
+def _time_stats(fn, stream, reps, flush=None):
+    """Median and minimum of `reps` individually timed calls (CUDA events on the
+    launching stream); `flush`, a buffer larger than L2, is rewritten before
+    every call, outside the timed pair."""
     import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    pairs = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        pairs.append((e0, e1))
+    torch.cuda.synchronize()
+    t = sorted(x.elapsed_time(y) for x, y in pairs)
+    return t[len(t) // 2], t[0]
 
+
+def run_extras(h, stream, flop8192):
+    """The square sweep, the Linpack-shaped updates, the 256^3 SIMT case and the
+    grouped uneven batch.  Inputs generated on the device (seeded torch
+    generators); L2 (129 MB) flushed before every timed call of a sweep point."""
+    import torch
     from paper_1608_05265_gb300 import gbgemm, metrics, synth
-
     out = {}
-    _, _, hbm, peak_src = load_peaks()
     g = torch.Generator(device="cuda")
-    # -- 4096^3 NN, ld 4104: the equivalent single-GEMM rates of both paths --
-    n4, ld4 = 4096, 4104
-    g.manual_seed(11)
-    A4 = torch.rand(n4 * ld4, device="cuda", generator=g) * 2 - 1
-    B4 = torch.rand(n4 * ld4, device="cuda", generator=g) * 2 - 1
-    C4 = torch.rand(n4 * ld4, device="cuda", generator=g) * 2 - 1
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")  # 256 MB
+    _, _, hbm, peak_src = load_peaks()
+
+    # -- 256^3 NN, ld 256, alpha 1, beta 0.5, uniform (seed 0): SIMT only --
+    A0_, B0_, C0_ = (torch.from_numpy(x).cuda() for x in synth.gemm_problem("uniform", 0, "N", "N", 256, 256, 256)[0::2])
+    Cw = C0_.clone()
+    h.set_path(gbgemm.PATH_SIMT)
+    med, mn = _time_stats(lambda: h.sgemm("N", "N", 256, 256, 256, 1.0, A0_, 256, B0_, 256, 0.5, Cw, 256), stream, 20,
+                          flush)
+    Cw.copy_(C0_)
+    h.sgemm("N", "N", 256, 256, 256, 1.0, A0_, 256, B0_, 256, 0.5, Cw, 256)
+    torch.cuda.synchronize()
+    out["simt_256"] = {"us_median": med * 1e3, "us_min": mn * 1e3,
+                       "tflops": metrics.gemm_flops(256, 256, 256) / (med * 1e-3) / 1e12,
+                       "max_error_ratio": h.check_error("N", "N", 256, 256, 256, 1.0, A0_, 256, B0_, 256, 0.5, C0_, Cw,
+                                                        256)}
+    del A0_, B0_, C0_, Cw
+
+    # -- square sweep: n in {1024, 2048, 4096, 8192}, four transposes, ld = n + 8,
+    #    alpha 1.5, beta -0.25, uniform (device generator, seed 1), both paths --
+    sweep = {}
     rates = {}
-    for path, name in ((gbgemm.PATH_SPLIT_BF16, "split"), (gbgemm.PATH_SIMT, "simt")):
-        h.set_path(path)
-        ms = _time(lambda: h.sgemm("N", "N", n4, n4, n4, 1.5, A4, ld4, B4, ld4, -0.25, C4, ld4), stream,
-                   20 if name == "split" else 5)
-        rates[name] = metrics.gemm_flops(n4, n4, n4) / (ms * 1e-3) / 1e12
-    del A4, B4, C4
-    out["square_4096"] = {"split": rates["split"], "simt": rates["simt"], "unit": "TFLOP/s"}
-    # -- Linpack-shaped trailing update: C(16384^2) -= A(16384 x nb) B(nb x 16384) --
+    for n in (1024, 2048, 4096, 8192):
+        ld = n + 8
+        g.manual_seed(1)
+        A = torch.rand(n * ld, device="cuda", generator=g) * 2 - 1
+        B = torch.rand(n * ld, device="cuda", generator=g) * 2 - 1
+        C0 = torch.rand(n * ld, device="cuda", generator=g) * 2 - 1
+        C = C0.clone()
+        blocks = [((0, n), (0, n))] if n <= 2048 else [((0, 256), (0, 256)), ((n - 256, n), (n // 2, n // 2 + 256))]
+        for ta, tb in (("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")):
+            pt = {}
+            for path, name in ((gbgemm.PATH_SPLIT_BF16, "split"), (gbgemm.PATH_SIMT, "simt")):
+                h.set_path(path)
+                reps = 10 if (name == "split" or n <= 4096) else 3
+                med, mn = _time_stats(lambda: h.sgemm(ta, tb, n, n, n, 1.5, A, ld, B, ld, -0.25, C, ld), stream, reps,
+                                      flush)
+                C.copy_(C0)
+                h.sgemm(ta, tb, n, n, n, 1.5, A, ld, B, ld, -0.25, C, ld)
+                torch.cuda.synchronize()
+                err = max(h.check_error(ta, tb, n, n, n, 1.5, A, ld, B, ld, -0.25, C0, C, ld, rows=r, cols=c)
+                          for r, c in blocks)
+                fl = metrics.gemm_flops(n, n, n)
+                pt[name] = {"tflops": fl / (med * 1e-3) / 1e12, "tflops_best": fl / (mn * 1e-3) / 1e12,
+                            "ms_median": med, "max_error_ratio": err}
+            pt["split_over_simt"] = pt["split"]["tflops"] / pt["simt"]["tflops"]
+            sweep[f"{n}_{ta}{tb}"] = pt
+            if n == 4096 and ta == "N" and tb == "N":
+                rates = {"split": pt["split"]["tflops"], "simt": pt["simt"]["tflops"]}
+        del A, B, C, C0
+    out["square_sweep"] = dict(sweep, note=("ld = n + 8, alpha 1.5, beta -0.25; median of 10 calls (3 for SIMT at "
+                                            "8192), L2 flushed before each; error ratio on the full result for "
+                                            "n <= 2048, on two 256x256 blocks above"))
+
+    # -- Linpack-shaped trailing updates: C(m x m) -= A(m x nb) B(nb x m), m in
+    #    {4096, 8192, 16384}, nb in {128, 256}, entries normal(0,1) 2^e per row --
     lp = {}
-    m = 16384
-    for nb in (128, 256):
-        g.manual_seed(20 + nb)
-        def rowscaled(rows, cols):
-            x = torch.randn(cols, rows, device="cuda", generator=g)
-            e = torch.randint(-20, 21, (rows,), device="cuda", generator=g).float()
-            return (x * torch.exp2(e)[None, :]).reshape(-1).contiguous()
-        A = rowscaled(m, nb)
-        B = rowscaled(nb, m)
-        C = rowscaled(m, m)
-        h.set_path(gbgemm.PATH_AUTO)
-        ms = _time(lambda: h.sgemm("N", "N", m, m, nb, -1.0, A, m, B, nb, 1.0, C, m), stream, 20)
-        fl = metrics.gemm_flops(m, m, nb)
-        by = 8.0 * m * m + 4.0 * (2 * m) * nb
-        tf = fl / (ms * 1e-3) / 1e12
-        gbs = by / (ms * 1e-3) / 1e9
-        lp[f"nb{nb}"] = {"ms": ms, "tflops": tf, "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
-                         "roofline_tflops": min(642.6, fl / by * hbm / 1e3),
-                         "path": "split" if h.last_path() == 2 else "simt"}
-        del A, B, C
-    out["linpack_update_16384"] = dict(lp, note=f"bytes = 8 m n + 4 (m + n) nb; HBM peak {hbm:.0f} GB/s ({peak_src})")
+    for m in (4096, 8192, 16384):
+        for nb in (128, 256):
+            g.manual_seed(20 + nb)
+            def rowscaled(rows, cols):
+                x = torch.randn(cols, rows, device="cuda", generator=g)
+                e = torch.randint(-20, 21, (rows,), device="cuda", generator=g).float()
+                return (x * torch.exp2(e)[None, :]).reshape(-1).contiguous()
+            A = rowscaled(m, nb)
+            B = rowscaled(nb, m)
+            C0 = rowscaled(m, m)
+            C = C0.clone()
+            h.set_path(gbgemm.PATH_AUTO)
+            med, mn = _time_stats(lambda: h.sgemm("N", "N", m, m, nb, -1.0, A, m, B, nb, 1.0, C, m), stream, 10,
+                                  flush if m < 8192 else None)
+            C.copy_(C0)
+            h.sgemm("N", "N", m, m, nb, -1.0, A, m, B, nb, 1.0, C, m)
+            torch.cuda.synchronize()
+            blk = [((0, m), (0, m))] if m <= 4096 else [((0, 1024), (0, 1024)), ((m - 1024, m), (m // 2, m // 2 + 1024))]
+            err = max(h.check_error("N", "N", m, m, nb, -1.0, A, m, B, nb, 1.0, C0, C, m, rows=r, cols=c) for r, c in blk)
+            fl = metrics.gemm_flops(m, m, nb)
+            by = 8.0 * m * m + 4.0 * (2 * m) * nb
+            gbs = by / (med * 1e-3) / 1e9
+            lp[f"m{m}_nb{nb}"] = {"ms_median": med, "tflops": fl / (med * 1e-3) / 1e12, "hbm_gbs": gbs,
+                                  "hbm_frac": gbs / hbm, "roofline_tflops": min(642.6, fl / by * hbm / 1e3),
+                                  "max_error_ratio": err, "path": "split" if h.last_path() == 2 else "simt"}
+            del A, B, C, C0
+    out["linpack_updates"] = dict(lp, note=(f"bytes = 8 m n + 4 (m + n) nb; HBM peak {hbm:.0f} GB/s ({peak_src}); "
+                                            "median of 10 calls; L2 flushed before each call for m = 4096"))
+    del flush
     # -- grouped uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024] (seed 3) --
     shapes = synth.grouped_shapes(3, 4096)
     bufs, probs = [], []
@@ -440,6 +510,15 @@ def run_extras(h, stream, flop8192):
     fl_split = sum(metrics.gemm_flops(mm, nn, kk) for (_, _, mm, nn, kk) in shapes if kk >= 128)
     fs = fl_split / fl_total
     equiv = 1.0 / (fs / rates["split"] + (1 - fs) / rates["simt"])
+    # Sum of per-problem rooflines: each problem at the larger of its FLOPs at its
+    # path's peak (BF16 dense / 3 from k = 128, FP32 SIMT below) and its
+    # 4 (mk + kn + mn) bytes at the HBM rate.
+    bf16_peak, _, hbm_gbs, _ = load_peaks()
+    simt_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    roof_s = 0.0
+    for (_, _, mm, nn, kk) in shapes:
+        pk = bf16_peak / 3.0 if kk >= 128 else simt_peak
+        roof_s += max(metrics.gemm_flops(mm, nn, kk) / (pk * 1e12), 4.0 * (mm * kk + kk * nn + mm * nn) / (hbm_gbs * 1e9))
     grouped = {}
     sources = [("default", gbgemm.CONFIG_DEFAULT)]
     weights = os.path.join(ROOT, "paper_1608_05265_gb300", "data", "predictor_gb300.bin")
@@ -454,12 +533,12 @@ def run_extras(h, stream, flop8192):
         ms = _time(lambda: plan.run(stream), stream, 20)
         st = plan.stats()
         tf = fl_total / (ms * 1e-3) / 1e12
-        grouped[name] = {"ms": ms, "tflops": tf, "plan_seconds": t_plan,
+        grouped[name] = {"ms": ms, "tflops": tf, "plan_seconds": t_plan, "fraction_of_roofline_sum": roof_s * 1e3 / ms,
                          "plan_split_flop_share": st["flops_split"] / max(st["flops_split"] + st["flops_simt"], 1.0),
                          "fraction_of_equivalent": tf / equiv, "kernels_per_run": st["kernels_per_run"]}
         plan.close()
     out["grouped_4096"] = dict(grouped, problems=4096, flops=fl_total, split_eligible_flop_share=fs,
-                               equivalent_single_gemm_tflops=equiv,
+                               equivalent_single_gemm_tflops=equiv, roofline_sum_ms=roof_s * 1e3,
                                note=("equivalent rate = harmonic mean of the 4096^3 split and SIMT rates, weighted by "
                                      "the FLOPs of problems with k >= 128 (split-eligible) and k < 128"))
     assert h.get_device_status() == 0
