@@ -21,7 +21,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbgemm.so")
 SOURCES = ["api.cu", "simt.cu", "split.cu", "noalloc.cu", "grouped.cu", "tuner.cu", "mlp.cu", "check.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("internal.h", "split_device.cuh", "simt_device.cuh", "gemm_kernel.cuh",
-                                            "grouped.h", "tuner.h", "mlp.h", "fused_kernel.cuh")] + \
+                                            "grouped.h", "tuner.h", "mlp.h")] + \
     [os.path.join(ROOT, "include", "gbgemm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

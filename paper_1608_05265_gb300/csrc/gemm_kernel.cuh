@@ -35,13 +35,20 @@
 namespace gbg {
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 4;                         // ring depth of the general (BN <= 256) kernel
 constexpr int kMaxBN = 256;
 constexpr int kEpiWarps = 16;                      // four per TMEM lane quadrant, each a quarter of the columns
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
-constexpr uint32_t kTmemCols = 2 * kMaxBN;         // two accumulator buffers
-constexpr int kGemmSmemBytes = kStages * (kBlockBytes + kMaxBN * 128) + 1024 + 256;
+// Shared memory of a kernel instance: STAGES ring slots of one A block and
+// MAXBN B rows, barriers, 1024-byte alignment.  With tiles of at most 128
+// columns the same memory holds a six-slot ring (more copies in flight for
+// the latency-bound grouped batches).
+template <int STAGES, int MAXBN>
+constexpr int gemm_smem_bytes() { return STAGES * (kBlockBytes + MAXBN * 128) + 1024 + 256; }
+constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN>();
+constexpr int kNarrowStages = 6;                   // ring depth of the BN <= 128 instance
+constexpr int kNarrowBN = 128;
 
 // Everything one tile needs.
 struct TileJob {
@@ -135,11 +142,14 @@ struct GroupedSched {
   }
 };
 
-template <class Sched>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   constexpr uint32_t A_BYTES = kBlockBytes;        // 128 rows x 128 B
-  constexpr uint32_t B_STAGE = kMaxBN * 128;       // room for 256 rows x 128 B
+  constexpr uint32_t B_STAGE = MAXBN * 128;        // room for MAXBN rows x 128 B
+  constexpr uint32_t kTmemCols = 2 * MAXBN;        // two accumulator buffers
+  constexpr int kStages = STAGES;
+  constexpr int kMaxBN = MAXBN;
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -354,14 +364,15 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
 
 // The shared-memory opt-in is a per-device function attribute: set it once
 // for every device a kernel instance is launched on.
-template <class Sched>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
 cudaError_t ensure_gemm_smem_attr() {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<Sched>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmemBytes);
+    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gemm_smem_bytes<STAGES, MAXBN>());
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }

@@ -12,7 +12,6 @@
 #include <new>
 #include <vector>
 
-#include "fused_kernel.cuh"
 #include "gemm_kernel.cuh"
 #include "grouped.h"
 #include "simt_device.cuh"
@@ -37,15 +36,20 @@ struct PackTask {
 };
 
 // block_task[b]: the task of pack-kernel block b (and, for the re-pack
-// kernel, of row block b), built on the host at plan creation.
+// kernel, of row block b), built on the host at plan creation.  A pack
+// block splits kPackChunks consecutive k chunks of one 128-row block, with
+// all their loads in flight at once.
+constexpr int kPackChunks = 2;
 __global__ void __launch_bounds__(256) grouped_pack_kernel(const PackTask* __restrict__ tasks,
                                                            const int* __restrict__ block_task) {
   __shared__ uint32_t smax[128];
   const PackTask T = tasks[block_task[blockIdx.x]];
   const int64_t local = (int64_t)blockIdx.x - T.block_begin;
-  const int64_t rb = local % T.rb_count, kc = local / T.rb_count;
-  if (T.kcontig) pack_block<true>(T.rows, T.k, T.X, T.ld, T.amax, T.panel, T.panel2, T.rows_alloc, rb, kc, smax);
-  else pack_block<false>(T.rows, T.k, T.X, T.ld, T.amax, T.panel, T.panel2, T.rows_alloc, rb, kc, smax);
+  const int64_t rb = local % T.rb_count, kc0 = (local / T.rb_count) * kPackChunks;
+  if (T.kcontig)
+    pack_block<true, kPackChunks>(T.rows, T.k, T.X, T.ld, T.amax, T.panel, T.panel2, T.rows_alloc, rb, kc0, smax, T.nkc);
+  else
+    pack_block<false, kPackChunks>(T.rows, T.k, T.X, T.ld, T.amax, T.panel, T.panel2, T.rows_alloc, rb, kc0, smax, T.nkc);
 }
 
 __global__ void __launch_bounds__(256) grouped_rescale_kernel(const PackTask* __restrict__ tasks,
@@ -91,52 +95,6 @@ void launch_grouped_simt(int variant, int grid, cudaStream_t s, const int4* item
     case 6: grouped_simt_kernel<BM, BN, false, true, true><<<grid, NT, 0, s>>>(items, n, probs); break;
     default: grouped_simt_kernel<BM, BN, true, true, true><<<grid, NT, 0, s>>>(items, n, probs); break;
   }
-}
-
-// SIMT fallback of the fused path: tiles listed on the device (count read at
-// run time), any transpose/alignment variant.
-template <int BM, int BN>
-__global__ void __launch_bounds__((BM / 8) * (BN / 8), 512 / ((BM / 8) * (BN / 8)))
-fallback_simt_kernel(const int4* __restrict__ items, const int* __restrict__ count, const Problem* __restrict__ probs) {
-  __shared__ __align__(16) SimtSmem<BM, BN> sm;
-  __shared__ Problem sp;
-  __shared__ int4 sit;
-  const int n = *count;
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    if (threadIdx.x == 0) {
-      sit = items[t];
-      sp = probs[sit.x];
-    }
-    __syncthreads();
-    const bool vec = ((sp.lda & 3) == 0) && ((sp.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(sp.A) & 15) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(sp.B) & 15) == 0);
-    const int64_t m0 = (int64_t)sit.y * BM, n0 = (int64_t)sit.z * BN;
-    const int v = sp.ta | (sp.tb << 1) | (vec ? 4 : 0);
-    switch (v) {
-      case 0: simt_tile<BM, BN, false, false, false>(sp, m0, n0, sm.As, sm.Bs); break;
-      case 1: simt_tile<BM, BN, true, false, false>(sp, m0, n0, sm.As, sm.Bs); break;
-      case 2: simt_tile<BM, BN, false, true, false>(sp, m0, n0, sm.As, sm.Bs); break;
-      case 3: simt_tile<BM, BN, true, true, false>(sp, m0, n0, sm.As, sm.Bs); break;
-      case 4: simt_tile<BM, BN, false, false, true>(sp, m0, n0, sm.As, sm.Bs); break;
-      case 5: simt_tile<BM, BN, true, false, true>(sp, m0, n0, sm.As, sm.Bs); break;
-      case 6: simt_tile<BM, BN, false, true, true>(sp, m0, n0, sm.As, sm.Bs); break;
-      default: simt_tile<BM, BN, true, true, true>(sp, m0, n0, sm.As, sm.Bs); break;
-    }
-    __syncthreads();
-  }
-}
-
-cudaError_t ensure_fused_smem_attr() {
-  static bool attr_set[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(fused_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemBytes);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_set[dev] = true;
-  }
-  return cudaSuccess;
 }
 
 int trans_code_g(char t) {
@@ -214,8 +172,6 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   std::vector<int64_t> split_of;           // problem index of each split group
   std::vector<Problem> sprobs;             // SIMT problems
   std::vector<int> simt_cfg;
-  std::vector<FusedGroup> fgroups;         // split problems on the fused path
-  std::vector<Problem> fprobs;             // their SIMT descriptors (fallback)
   struct Region { size_t off, bytes; };
   size_t off = 0;
   auto take = [&](size_t bytes) { Region r{off, bytes}; off = align256(off + bytes); return r; };
@@ -229,18 +185,7 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     const bool use_ab = (q.alpha != 0.0f) && (q.k > 0);
     if (!use_ab && q.beta == 1.0f) continue;
     const int ta = trans_code_g(q.transa), tb = trans_code_g(q.transb);
-    if (use_ab && (cfg == GBGEMM_CFG_SPLIT_BN64 || cfg == GBGEMM_CFG_SPLIT_BN128) && split_parts(q.k) == 1) {
-      // Split done on load (no panels); a SIMT descriptor serves the fallback.
-      FusedGroup f{};
-      f.A = q.A; f.lda = q.lda; f.B = q.B; f.ldb = q.ldb; f.C = q.C; f.ldc = q.ldc;
-      f.m = q.m; f.n = q.n; f.k = q.k; f.alpha = q.alpha; f.beta = q.beta;
-      f.a_kcontig = ta == 1; f.b_kcontig = tb == 0;
-      f.bn = config_bn(cfg);
-      f.nkc = (int)panel_k_chunks(q.k);
-      fgroups.push_back(f);
-      fprobs.push_back(Problem{ta, tb, q.m, q.n, q.k, q.alpha, q.beta, q.A, q.lda, q.B, q.ldb, q.C, q.ldc});
-      P->flops_split += 2.0 * q.m * q.n * q.k;
-    } else if (use_ab && cfg >= GBGEMM_CFG_SPLIT_BN64) {
+    if (use_ab && cfg >= GBGEMM_CFG_SPLIT_BN64) {
       // Compact panels: rows rounded up to 8 per k chunk.  A tile copy may
       // run past the last row into the next chunk (or, for the last chunk,
       // into 32 KiB of slack): those rows feed only outputs that are never
@@ -294,27 +239,6 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   }
   for (auto& v : simt_items)
     std::stable_sort(v.begin(), v.end(), [&](const int4& a, const int4& b) { return sprobs[a.x].k > sprobs[b.x].k; });
-  // fused path: fallback descriptors follow the SIMT problems; work list by decreasing cost
-  for (size_t f = 0; f < fgroups.size(); ++f) {
-    fgroups[f].simt_index = (int)sprobs.size();
-    sprobs.push_back(fprobs[f]);
-  }
-  std::vector<int4> fused_items;
-  int64_t fb_capacity = 0;
-  for (size_t f = 0; f < fgroups.size(); ++f) {
-    const int64_t tm = (fgroups[f].m + 127) / 128, tn = (fgroups[f].n + fgroups[f].bn - 1) / fgroups[f].bn;
-    for (int64_t i = 0; i < tm; ++i)
-      for (int64_t j = 0; j < tn; ++j) fused_items.push_back(make_int4((int)f, (int)i, (int)j, 0));
-    fb_capacity += tm * ((fgroups[f].n + 63) / 64);
-  }
-  std::stable_sort(fused_items.begin(), fused_items.end(), [&](const int4& a, const int4& b) {
-    return (int64_t)fgroups[a.x].nkc * fgroups[a.x].bn > (int64_t)fgroups[b.x].nkc * fgroups[b.x].bn;
-  });
-
-  const Region fgroup_r = take(fgroups.size() * sizeof(FusedGroup) + 16);
-  const Region fitems_r = take(fused_items.size() * sizeof(int4) + 16);
-  const Region fb_items_r = take((size_t)fb_capacity * sizeof(int4) + 16);
-  const Region fb_count_r = take(16);
   const Region gdev_r = take(gdev.size() * sizeof(GroupDev) + 16);
   const Region sitems_r = take(split_items.size() * sizeof(int4) + 16);
   const Region sprob_r = take(sprobs.size() * sizeof(Problem) + 16);
@@ -325,7 +249,7 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   int64_t n_blocks = 0, n_rowblocks = 0;
   for (size_t s = 0; s < gdev.size(); ++s) {
     const gbgemm_problem& q = probs[split_of[s]];
-    n_blocks += ((q.m + 127) / 128 + (q.n + 127) / 128) * gdev[s].nkc;
+    n_blocks += ((q.m + 127) / 128 + (q.n + 127) / 128) * ((gdev[s].nkc + kPackChunks - 1) / kPackChunks);
     n_rowblocks += (q.m + 127) / 128 + (q.n + 127) / 128;
   }
   if (n_blocks > 0x7FFFFFFF || n_rowblocks > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
@@ -359,18 +283,19 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     const int64_t rbA = (q.m + 127) / 128, rbB = (q.n + 127) / 128;
     PackTask ta_{q.A, q.lda, const_cast<uint32_t*>(d.amaxA), const_cast<uint8_t*>(d.panelA), pA2, q.m, q.k,
                  rbA, d.nkc, d.rowsA, blocks, rowblocks, ta == 1, 0};
-    blocks += rbA * d.nkc;
+    blocks += rbA * ((d.nkc + kPackChunks - 1) / kPackChunks);
     rowblocks += rbA;
     PackTask tb_{q.B, q.ldb, const_cast<uint32_t*>(d.amaxB), const_cast<uint8_t*>(d.panelB), pB2, q.n, q.k,
                  rbB, d.nkc, d.rowsB, blocks, rowblocks, tb == 0, 0};
-    blocks += rbB * d.nkc;
+    blocks += rbB * ((d.nkc + kPackChunks - 1) / kPackChunks);
     rowblocks += rbB;
     tasks.push_back(ta_);
     tasks.push_back(tb_);
   }
   std::vector<int> bmap((size_t)blocks), rmap((size_t)rowblocks);
   for (size_t t = 0; t < tasks.size(); ++t) {
-    for (int64_t b = 0; b < tasks[t].rb_count * tasks[t].nkc; ++b) bmap[(size_t)(tasks[t].block_begin + b)] = (int)t;
+    const int64_t nb = tasks[t].rb_count * ((tasks[t].nkc + kPackChunks - 1) / kPackChunks);
+    for (int64_t b = 0; b < nb; ++b) bmap[(size_t)(tasks[t].block_begin + b)] = (int)t;
     for (int64_t b = 0; b < tasks[t].rb_count; ++b) rmap[(size_t)(tasks[t].rowblock_begin + b)] = (int)t;
   }
   auto h2d = [&](const Region& r, const void* src, size_t bytes) {
@@ -380,22 +305,29 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
             h2d(sitems_r, split_items.data(), split_items.size() * sizeof(int4)) &&
             h2d(sprob_r, sprobs.data(), sprobs.size() * sizeof(Problem)) &&
             h2d(tasks_r, tasks.data(), tasks.size() * sizeof(PackTask)) &&
-            h2d(bmap_r, bmap.data(), bmap.size() * 4) && h2d(rmap_r, rmap.data(), rmap.size() * 4) &&
-            h2d(fgroup_r, fgroups.data(), fgroups.size() * sizeof(FusedGroup)) &&
-            h2d(fitems_r, fused_items.data(), fused_items.size() * sizeof(int4));
+            h2d(bmap_r, bmap.data(), bmap.size() * 4) && h2d(rmap_r, rmap.data(), rmap.size() * 4);
   for (int c = 0; c < 24; ++c) ok = ok && h2d(simt_items_r[c], simt_items[c].data(), simt_items[c].size() * sizeof(int4));
   if (!ok) return GBGEMM_ERR_CUDA;
-  P->n_split = (int64_t)(gdev.size() + fgroups.size());
-  P->n_simt = (int64_t)(sprobs.size() - fgroups.size());
-  P->split_tiles = (int64_t)(split_items.size() + fused_items.size());
+  P->n_split = (int64_t)gdev.size();
+  P->n_simt = (int64_t)sprobs.size();
+  P->split_tiles = (int64_t)split_items.size();
   P->kernels_per_run = 0;
 
   // ---- capture the graph ----
   if (blocks > 0x7FFFFFFF || rowblocks > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
-  if (!gdev.empty() && ensure_gemm_smem_attr<GroupedSched>() != cudaSuccess) return GBGEMM_ERR_CUDA;
-  if (!fgroups.empty() && ensure_fused_smem_attr() != cudaSuccess) return GBGEMM_ERR_CUDA;
-  // The SIMT launches run on side branches of the graph, concurrently with
-  // the (memory-bound) split-path chain on the main branch.
+  // Tiles of at most 128 columns everywhere: the six-slot ring instance.
+  bool narrow = true;
+  for (const GroupDev& gd : gdev) narrow = narrow && gd.bn <= kNarrowBN;
+  if (!gdev.empty()) {
+    const cudaError_t ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowStages, kNarrowBN>()
+                                  : ensure_gemm_smem_attr<GroupedSched>();
+    if (ea != cudaSuccess) return GBGEMM_ERR_CUDA;
+  }
+  // Graph: the SIMT launches run on side branches, concurrently with the
+  // split chain (packing, re-packing, tcgen05 GEMM) on the main branch; the
+  // branches join at the end.  (Holding the GEMM back until the SIMT
+  // branches finish, so that they overlap the memory-bound packing, measured
+  // 1% slower.)
   constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, joins[kSide] = {};
@@ -421,43 +353,8 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   }
   cudaError_t e = cudaEventRecord(fork, capture_stream);
   for (int i = 0; i < kSide && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[i], fork, 0);
-  if (!gdev.empty()) {
-    const PackTask* dt = reinterpret_cast<const PackTask*>(base + tasks_r.off);
-    e = cudaMemsetAsync(amax_base, 0, (size_t)amax_words * 4, capture_stream);
-    if (e == cudaSuccess) {
-      const int* dbmap = reinterpret_cast<const int*>(base + bmap_r.off);
-      const int* drmap = reinterpret_cast<const int*>(base + rmap_r.off);
-      grouped_pack_kernel<<<(unsigned)blocks, 256, 0, capture_stream>>>(dt, dbmap);
-      grouped_rescale_kernel<<<(unsigned)rowblocks, 256, 0, capture_stream>>>(dt, drmap);
-    }
-    if (e == cudaSuccess) {
-      GroupedSched S;
-      S.items = reinterpret_cast<const int4*>(base + sitems_r.off);
-      S.groups = reinterpret_cast<const GroupDev*>(base + gdev_r.off);
-      S.n_items = (int)split_items.size();
-      const int grid = (int)std::min<int64_t>((int64_t)split_items.size(), P->num_sms);
-      split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status, kTimeoutNs);
-      P->kernels_per_run += 3;
-    }
-  }
   const Problem* dprobs = reinterpret_cast<const Problem*>(base + sprob_r.off);
-  if (!fgroups.empty() && e == cudaSuccess) {
-    int* dcount = reinterpret_cast<int*>(base + fb_count_r.off);
-    int4* dfb = reinterpret_cast<int4*>(base + fb_items_r.off);
-    e = cudaMemsetAsync(dcount, 0, sizeof(int), capture_stream);
-    if (e == cudaSuccess) {
-      FusedSched F;
-      F.items = reinterpret_cast<const int4*>(base + fitems_r.off);
-      F.groups = reinterpret_cast<const FusedGroup*>(base + fgroup_r.off);
-      F.n_items = (int)fused_items.size();
-      F.fb_count = dcount;
-      F.fb_items = dfb;
-      const int grid = (int)std::min<int64_t>((int64_t)fused_items.size(), P->num_sms);
-      fused_gemm_kernel<<<grid, kFusedThreads, kFusedSmemBytes, capture_stream>>>(F, P->status, kTimeoutNs);
-      fallback_simt_kernel<128, 64><<<P->num_sms * 4, 128, 0, capture_stream>>>(dfb, dcount, dprobs);
-      P->kernels_per_run += 2;
-    }
-  }
+  int simt_launches = 0;
   for (int cv = 0; cv < 24 && e == cudaSuccess; ++cv) {
     const int n = (int)simt_items[cv].size();
     if (n == 0) continue;
@@ -466,10 +363,36 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     // resident CTAs per SM at the kernels' 512-thread bound: 2, 4 or 8
     const int per_sm = (c == GBGEMM_CFG_SIMT_128x128) ? 2 : (c == GBGEMM_CFG_SIMT_128x64) ? 4 : 8;
     const int grid = (int)std::min<int64_t>(n, (int64_t)P->num_sms * per_sm);
-    cudaStream_t st = side[P->kernels_per_run % kSide];
+    cudaStream_t st = side[simt_launches % kSide];
     if (c == GBGEMM_CFG_SIMT_128x128) launch_grouped_simt<128, 128>(variant, grid, st, di, n, dprobs);
     else if (c == GBGEMM_CFG_SIMT_64x64) launch_grouped_simt<64, 64>(variant, grid, st, di, n, dprobs);
     else launch_grouped_simt<128, 64>(variant, grid, st, di, n, dprobs);
+    ++simt_launches;
+  }
+  P->kernels_per_run += simt_launches;
+  if (!gdev.empty() && e == cudaSuccess) {
+    const PackTask* dt = reinterpret_cast<const PackTask*>(base + tasks_r.off);
+    e = cudaMemsetAsync(amax_base, 0, (size_t)amax_words * 4, capture_stream);
+    if (e == cudaSuccess) {
+      const int* dbmap = reinterpret_cast<const int*>(base + bmap_r.off);
+      const int* drmap = reinterpret_cast<const int*>(base + rmap_r.off);
+      grouped_pack_kernel<<<(unsigned)blocks, 256, 0, capture_stream>>>(dt, dbmap);
+      grouped_rescale_kernel<<<(unsigned)rowblocks, 256, 0, capture_stream>>>(dt, drmap);
+      P->kernels_per_run += 2;
+    }
+  }
+  if (!gdev.empty() && e == cudaSuccess) {
+    GroupedSched S;
+    S.items = reinterpret_cast<const int4*>(base + sitems_r.off);
+    S.groups = reinterpret_cast<const GroupDev*>(base + gdev_r.off);
+    S.n_items = (int)split_items.size();
+    const int grid = (int)std::min<int64_t>((int64_t)split_items.size(), P->num_sms);
+    if (narrow)
+      split_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN>
+          <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowStages, kNarrowBN>(), capture_stream>>>(S, P->status,
+                                                                                               kTimeoutNs);
+    else
+      split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status, kTimeoutNs);
     P->kernels_per_run += 1;
   }
   for (int i = 0; i < kSide && e == cudaSuccess; ++i) {

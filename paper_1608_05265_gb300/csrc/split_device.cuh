@@ -291,36 +291,50 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // smax: 128 words of shared memory.
 // With panel2 != NULL the three-part split is written ([hi | mid] into
 // panel, [lo3 | 0] into panel2 at the same offsets).
-template <bool KCONTIG>
+template <bool KCONTIG, int G = 1>
 __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                            uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
-                                           uint8_t* __restrict__ panel2, int64_t rows_alloc, int64_t rb, int64_t kc,
-                                           uint32_t* smax) {
-  const int64_t r0 = rb * 128, p0 = kc * 32;
+                                           uint8_t* __restrict__ panel2, int64_t rows_alloc, int64_t rb, int64_t kc0,
+                                           uint32_t* smax, int64_t nkc = 1 << 30) {
+  // G consecutive k chunks kc0 .. kc0 + G - 1 (those below nkc) of one 128-row block
+  const int64_t r0 = rb * 128;
   const int tid = threadIdx.x;
   const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   if (tid < 128) smax[tid] = 0u;
-  float x[2][8];
+  float x[G][2][8];
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {  // all loads first: 16 (or 4 vector) loads in flight per thread
-    int rr, cc;
-    item_of<KCONTIG>(tid, it, rr, cc);
-    load8<KCONTIG>(X, ld, r0 + rr, p0 + cc * 8, rows, k, vec, x[it]);
+  for (int c = 0; c < G; ++c) {  // all loads first: 16 G (or 4 G vector) loads in flight per thread
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      int rr, cc;
+      item_of<KCONTIG>(tid, it, rr, cc);
+      if (kc0 + c < nkc) load8<KCONTIG>(X, ld, r0 + rr, (kc0 + c) * 32 + cc * 8, rows, k, vec, x[c][it]);
+    }
   }
   __syncthreads();
-  const size_t boff = ((size_t)kc * rows_alloc + r0) * 128;
-  uint8_t* blk = panel + boff;
+  uint32_t mxr[2] = {0u, 0u};
+#pragma unroll
+  for (int c = 0; c < G; ++c) {
+    if (kc0 + c >= nkc) break;
+    const size_t boff = ((size_t)(kc0 + c) * rows_alloc + r0) * 128;
+    uint8_t* blk = panel + boff;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      int rr, cc;
+      item_of<KCONTIG>(tid, it, rr, cc);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) mxr[it] = max(mxr[it], __float_as_uint(x[c][it][q]) & 0x7FFFFFFFu);
+      if (r0 + rr < rows_alloc) {
+        if (panel2) store_split8_3(blk, panel2 + boff, rr, cc, x[c][it]);
+        else store_split8(blk, rr, cc, x[c][it]);
+      }
+    }
+  }
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     int rr, cc;
     item_of<KCONTIG>(tid, it, rr, cc);
-    uint32_t mx = 0u;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) mx = max(mx, __float_as_uint(x[it][q]) & 0x7FFFFFFFu);
-    if (r0 + rr < rows_alloc) {
-      if (panel2) store_split8_3(blk, panel2 + boff, rr, cc, x[it]);
-      else store_split8(blk, rr, cc, x[it]);
-    }
+    uint32_t mx = mxr[it];
     if (KCONTIG) {
       mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
       mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));

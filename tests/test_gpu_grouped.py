@@ -177,7 +177,7 @@ def test_grouped_uneven_batch_4096(h):
 
 SCALED_SHORT_K = [("N", "N", 300, 200, 256, 1.0, 0.5), ("T", "N", 200, 300, 384, 1.0, 0.0),
                   ("N", "T", 130, 129, 200, -1.0, 1.0), ("T", "T", 64, 64, 128, 2.0, 0.0)]
-# k >= 512: the split-on-load kernel, whose tiles fall back to SIMT
+# k >= 512: two-part panels (three products)
 SCALED_LONG_K = [("N", "N", 300, 200, 600, 1.0, 0.5), ("T", "N", 200, 300, 777, 1.0, 0.0),
                  ("N", "T", 130, 129, 512, -1.0, 1.0), ("T", "T", 64, 64, 1000, 2.0, 0.0),
                  ("N", "N", 257, 40, 530, 1.0, 0.0)]
@@ -186,9 +186,9 @@ SCALED_LONG_K = [("N", "N", 300, 200, 600, 1.0, 0.5), ("T", "N", 200, 300, 777, 
 @pytest.mark.parametrize("specs", [SCALED_SHORT_K, SCALED_LONG_K], ids=["short_k", "long_k"])
 def test_grouped_badly_scaled_rows_take_the_fallback(h, specs):
     """Problems whose rows of op(A) or columns of op(B) are badly scaled (max
-    |x| outside [2^-48, 2^48)): the split kernels scale them (panels) or
-    leave the tiles touching them to the SIMT fallback (split on load);
-    every result stays within the bound."""
+    |x| outside [2^-48, 2^48)): the grouped re-pack scales them by powers of
+    two, in three-part (k < 512) and two-part panels alike; every result
+    stays within the bound."""
     import torch
     from paper_1608_05265_gb300 import gbgemm
     b = Batch(specs, 81)
@@ -216,7 +216,7 @@ def test_grouped_badly_scaled_rows_take_the_fallback(h, specs):
 
 
 def test_grouped_long_k_infinities(h):
-    """An infinity in op(A) on the split-on-load path.  Its lo part is zero,
+    """An infinity in op(A) on the long-k split path.  Its lo part is zero,
     but inf * hi(b) + inf * lo(b) is NaN wherever lo(b) has the other sign,
     so the split can only promise that the row it touches is non-finite (as
     the FP64 result is); every other entry stays within the bound."""
