@@ -268,27 +268,28 @@ def run_ours(args, rank, world, local_rank):
     h.set_path(gbgemm.PATH_SPLIT_BF16)
     sets = [(A, B, C), (torch.empty_like(A), torch.empty_like(B), torch.empty_like(C))]
     outs = [Cout_h, torch.empty_like(Cout_h).pin_memory()]
-    h2d, d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event() for _ in range(2)]
+    h2d = [torch.cuda.Stream(device=dev) for _ in range(3)]  # one per input: several copy engines
+    d2h = torch.cuda.Stream(device=dev)
+    ev_in = [[torch.cuda.Event() for _ in range(3)] for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
     barrier()
     x0 = torch.cuda.Event(enable_timing=True)
     x1 = torch.cuda.Event(enable_timing=True)
     x0.record(stream)
-    h2d.wait_event(x0)
+    for hs in h2d:
+        hs.wait_event(x0)
     used = [False, False]
     for it in range(e2e_steps):
         b = it % 2
+        for hs, dst, src, ev in zip(h2d, sets[b], (A_h, B_h, C_h), ev_in[b]):
+            if used[b]:
+                hs.wait_event(ev_out[b])  # the set's previous result has been read back
+            with torch.cuda.stream(hs):
+                dst.copy_(src, non_blocking=True)
+                ev.record(hs)
+            stream.wait_event(ev)
         Ab, Bb, Cb = sets[b]
-        if used[b]:
-            h2d.wait_event(ev_out[b])  # the set's previous result has been read back
-        with torch.cuda.stream(h2d):
-            Ab.copy_(A_h, non_blocking=True)
-            Bb.copy_(B_h, non_blocking=True)
-            Cb.copy_(C_h, non_blocking=True)
-            ev_in[b].record(h2d)
-        stream.wait_event(ev_in[b])
         h.sgemm("N", "N", N, N, N, ALPHA, Ab, LD, Bb, LD, BETA, Cb, LD)
         ev_done[b].record(stream)
         d2h.wait_event(ev_done[b])

@@ -354,9 +354,13 @@ int gbgemm_sgemm_split_noalloc(void* cuda_stream, char transa, char transb, int6
  *              transb, X = B, ldx = ldb).
  * Outputs (device, caller-owned):
  *   amax_bits[r] = bit pattern of max_p |x(r,p)| (NaN/Inf patterns kept), rows entries.
- *   panel2 (needed when k < 512, else ignored and may be NULL): a second
- *   panel of the same size and layout holding lo3 in chunks 0-3 and zeros in
- *   chunks 4-7; the first panel then holds hi and mid (= the two-part lo).
+ *   panel2 (needed when k < 512, else ignored and may be NULL; allocate
+ *   gbgemm_panel_bytes(rows, k) bytes): the compact lo3 panel.  Its block
+ *   (j, rb), at byte offset (j * RB + rb) * 16384, holds lo3 of k chunk 2j in
+ *   logical chunks 0-3 and of k chunk 2j+1 in logical chunks 4-7, rows and
+ *   swizzle as below; when the number of k chunks is odd the upper half of
+ *   the last block is not written, and blocks from ceil(KC/2) on are unused.
+ *   The first panel then holds hi and mid (= the two-part lo).
  *   panel: BF16 hi/lo panel of gbgemm_panel_bytes(rows, k) bytes.  It is a
  *   sequence of 16 KiB blocks, block (kc, rb) at byte offset
  *   (kc * RB + rb) * 16384 with RB = ceil(rows/256)*2 and kc = p / 32.  A

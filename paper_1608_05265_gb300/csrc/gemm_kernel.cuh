@@ -58,8 +58,8 @@ struct TileJob {
   size_t b_kstride;         // bytes between k chunks of the B panel
   int nkc;                  // k chunks
   int bn;                   // tile width: 64, 128 or 256
-  int parts;                // 1: [hi | lo] panels, 3 products; 2: also [lo3 | 0] panels, 6 products
-  int64_t a_part, b_part;   // byte offsets from the [hi | mid] panels to the [lo3 | 0] panels
+  int parts;                // 1: [hi | lo] panels, 3 products; 2: also compact lo3 panels, 6 products
+  int64_t a_part, b_part;   // byte offsets from the [hi | mid] panels to the compact lo3 panels
   int64_t m0, n0;           // tile origin in C
   int64_t m, n;             // problem extents
   const uint32_t* amaxA;
@@ -114,7 +114,7 @@ struct GroupDev {
   int64_t rowsA, rowsB;     // panel rows per k chunk
   float alpha, beta;
   int parts, pad_;
-  int64_t a_part, b_part;   // byte offsets to the [lo3 | 0] panels (parts == 2)
+  int64_t a_part, b_part;   // byte offsets to the compact lo3 panels (parts == 2)
 };
 
 // Many problems: item t = (group, tile row, tile column), items sorted by
@@ -199,16 +199,20 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x) {
         const TileJob J = S.job(t);
         const uint32_t b_bytes = (uint32_t)J.bn * 128u;
-        // one ring slot per panel part and k chunk
+        // one ring slot per k chunk, and with three parts one more per pair
+        // of chunks (the compact [lo3 | lo3] block, loaded with the even chunk)
         for (int kc = 0; kc < J.nkc && ok; ++kc) {
-          for (int part = 0; part < J.parts; ++part) {
+          const int nparts = (J.parts == 2 && (kc & 1) == 0) ? 2 : 1;
+          for (int part = 0; part < nparts; ++part) {
             if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, timeout_ns)) {
               raise_status(status, abort_flag);
               ok = false;
               break;
             }
-            const uint8_t* a = J.a_src + (part ? J.a_part : 0) + (size_t)kc * J.a_kstride;
-            const uint8_t* b = J.b_src + (part ? J.b_part : 0) + (size_t)kc * J.b_kstride;
+            const uint8_t* a = part ? J.a_src + J.a_part + (size_t)(kc >> 1) * J.a_kstride
+                                    : J.a_src + (size_t)kc * J.a_kstride;
+            const uint8_t* b = part ? J.b_src + J.b_part + (size_t)(kc >> 1) * J.b_kstride
+                                    : J.b_src + (size_t)kc * J.b_kstride;
             mbar_arrive_expect_tx(full_bar(stage), A_BYTES + b_bytes);
             bulk_copy_g2s(sA + stage * A_BYTES, a, A_BYTES, full_bar(stage));
             bulk_copy_g2s(sB + stage * B_STAGE, b, b_bytes, full_bar(stage));
@@ -241,9 +245,10 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * kMaxBN);
+        int s1 = 0;  // with three parts: the slot of the current [lo3 | lo3] block
         for (int kc = 0; kc < J.nkc; ++kc) {
-          // the chunk's slots: s0 holds [hi | lo] (or [hi | mid]); s1, with three
-          // parts, holds [lo3 | 0]
+          // the chunk's slot s0 holds [hi | lo] (or [hi | mid]); with three parts
+          // an even chunk also brings the pair's [lo3 | lo3] slot
           const int s0 = stage;
           const uint32_t ph0 = phase;
           if (!mbar_wait(full_bar(s0), ph0, abort_flag, timeout_ns)) {
@@ -251,8 +256,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
             ok = false;
             break;
           }
-          int s1 = s0;
-          if (J.parts == 2) {
+          if (J.parts == 2 && (kc & 1) == 0) {
             if (++stage == kStages) { stage = 0; phase ^= 1u; }
             s1 = stage;
             if (!mbar_wait(full_bar(s1), phase, abort_flag, timeout_ns)) {
@@ -264,8 +268,8 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           tc_fence_after();
           const uint32_t a_addr = sA + s0 * A_BYTES;
           const uint32_t b_addr = sB + s0 * B_STAGE;
-          const uint32_t a3_addr = sA + s1 * A_BYTES;
-          const uint32_t b3_addr = sB + s1 * B_STAGE;
+          const uint32_t a3_addr = sA + s1 * A_BYTES + 64u * (uint32_t)(kc & 1);
+          const uint32_t b3_addr = sB + s1 * B_STAGE + 64u * (uint32_t)(kc & 1);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             const uint64_t ah = make_desc_sw128(a_addr + 32u * kk);
@@ -284,8 +288,8 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
               mma_bf16(d_tmem, a3, bh, idesc, 1u);
             }
           }
-          mma_commit(empty_bar(s0));  // frees the slots once these MMAs have read them
-          if (J.parts == 2) mma_commit(empty_bar(s1));
+          mma_commit(empty_bar(s0));  // frees the slot once these MMAs have read it
+          if (J.parts == 2 && ((kc & 1) == 1 || kc == J.nkc - 1)) mma_commit(empty_bar(s1));
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;

@@ -25,7 +25,7 @@ struct PackTask {
   int64_t ld;
   uint32_t* amax;
   uint8_t* panel;
-  uint8_t* panel2;         // [lo3 | 0] panel of a three-part split, else NULL
+  uint8_t* panel2;         // compact lo3 panel of a three-part split, else NULL
   int64_t rows, k;
   int64_t rb_count, nkc;   // 128-row blocks per k chunk, k chunks
   int64_t rows_alloc;      // panel rows per k chunk (rows rounded up to 8)
@@ -196,8 +196,9 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
       const int parts = split_parts(q.k);
       panelA_r.push_back(take((size_t)rowsA * nkc * 128 + 32768));
       panelB_r.push_back(take((size_t)rowsB * nkc * 128 + 32768));
-      panelA2_r.push_back(parts == 2 ? take((size_t)rowsA * nkc * 128 + 32768) : Region{0, 0});
-      panelB2_r.push_back(parts == 2 ? take((size_t)rowsB * nkc * 128 + 32768) : Region{0, 0});
+      // three parts: compact [lo3 | lo3] panels, one block per pair of k chunks
+      panelA2_r.push_back(parts == 2 ? take((size_t)rowsA * ((nkc + 1) / 2) * 128 + 32768) : Region{0, 0});
+      panelB2_r.push_back(parts == 2 ? take((size_t)rowsB * ((nkc + 1) / 2) * 128 + 32768) : Region{0, 0});
       split_of.push_back(g);
       GroupDev d{};
       d.m = q.m; d.n = q.n; d.nkc = (int)nkc; d.bn = bn; d.rowsA = rowsA; d.rowsB = rowsB;

@@ -32,7 +32,7 @@ constexpr int kBlockBytes = kPanelRows * 128;  // 16 KiB
 constexpr int kSplitMinK = 128;     // AUTO uses the split path from this k upwards
 constexpr int kSplitTwoPartK = 512; // from this k two BF16 parts (3 products) meet the bound; below, three parts (6 products)
 
-// Number of panel parts of the split path for a given k: 1 ([hi | lo]) or 2 ([hi | mid] and [lo3 | 0]).
+// Number of panel parts of the split path for a given k: 1 ([hi | lo]) or 2 ([hi | mid] and compact lo3).
 inline int split_parts(int64_t k) { return k < kSplitTwoPartK ? 2 : 1; }
 
 inline int64_t panel_row_blocks(int64_t rows) { return (rows + 255) / 256 * 2; }
@@ -46,14 +46,16 @@ inline size_t panel_bytes(int64_t rows, int64_t k) {
 // (max outside [2^-48, 2^48)).  `kcontig` selects the view: element (r, p) =
 // X[r*ld + p] (kcontig) or X[r + p*ld] (!kcontig).  amax_bits must hold
 // `rows` words; it is zeroed here.
-// With three parts (k < kSplitTwoPartK) panel2 receives the [lo3 | 0] panel
-// (same layout and size as `panel`); otherwise panel2 is ignored (may be NULL).
+// With three parts (k < kSplitTwoPartK) panel2 (allocated with the size of
+// `panel`) receives the compact lo3 panel: block (kc / 2, rb) holds lo3 of k
+// chunk kc in logical chunks 4 (kc % 2) .. 4 (kc % 2) + 3; otherwise panel2 is
+// ignored (may be NULL).
 cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
                               uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s);
 
 struct SplitGemmArgs {
   const void* panelA; const void* panelB;     // [hi | lo] (or [hi | mid]) panels
-  const void* panelA2; const void* panelB2;   // [lo3 | 0] panels when split_parts(k) == 2
+  const void* panelA2; const void* panelB2;   // compact lo3 panels when split_parts(k) == 2
   const uint32_t* amaxA; const uint32_t* amaxB;
   int64_t m, n, k;
   float alpha, beta;

@@ -76,8 +76,9 @@ __device__ __forceinline__ void store_split8(uint8_t* blk, int rr, int cc, const
 }
 
 // Three-part split of 8 values: [hi | mid] into blk (as store_split8, mid =
-// the two-part lo) and [lo3 | 0] into blk2, lo3 = bf16((x - hi) - mid).
-__device__ __forceinline__ void store_split8_3(uint8_t* blk, uint8_t* blk2, int rr, int cc, const float (&x)[8]) {
+// the two-part lo) into blk and lo3 = bf16((x - hi) - mid) into half `half` of the compact block blk2.
+__device__ __forceinline__ void store_split8_3(uint8_t* blk, uint8_t* blk2, int half, int rr, int cc,
+                                               const float (&x)[8]) {
   uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -100,8 +101,9 @@ __device__ __forceinline__ void store_split8_3(uint8_t* blk, uint8_t* blk2, int 
   const int sw = rr & 7;
   *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
   *reinterpret_cast<uint4*>(blk + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-  *reinterpret_cast<uint4*>(blk2 + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  *reinterpret_cast<uint4*>(blk2 + rr * 128 + (((cc + 4) ^ sw) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+  // lo3 of an even k chunk in logical chunks 0-3 of the compact block, of an
+  // odd one in 4-7
+  *reinterpret_cast<uint4*>(blk2 + rr * 128 + (((cc + 4 * half) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
 // Item mapping inside a 256-thread CTA, two items per thread.
@@ -290,7 +292,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // up to rows_alloc are written as zeros, rows past rows_alloc not at all.
 // smax: 128 words of shared memory.
 // With panel2 != NULL the three-part split is written ([hi | mid] into
-// panel, [lo3 | 0] into panel2 at the same offsets).
+// panel, lo3 into the compact panel2: block kc / 2, half kc % 2).
 template <bool KCONTIG, int G = 1>
 __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                            uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
@@ -317,6 +319,7 @@ __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float*
   for (int c = 0; c < G; ++c) {
     if (kc0 + c >= nkc) break;
     const size_t boff = ((size_t)(kc0 + c) * rows_alloc + r0) * 128;
+    const size_t boff2 = ((size_t)((kc0 + c) >> 1) * rows_alloc + r0) * 128;  // compact [lo3 | lo3] block
     uint8_t* blk = panel + boff;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
@@ -325,7 +328,7 @@ __device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float*
 #pragma unroll
       for (int q = 0; q < 8; ++q) mxr[it] = max(mxr[it], __float_as_uint(x[c][it][q]) & 0x7FFFFFFFu);
       if (r0 + rr < rows_alloc) {
-        if (panel2) store_split8_3(blk, panel2 + boff, rr, cc, x[c][it]);
+        if (panel2) store_split8_3(blk, panel2 + boff2, (int)((kc0 + c) & 1), rr, cc, x[c][it]);
         else store_split8(blk, rr, cc, x[c][it]);
       }
     }
@@ -361,6 +364,7 @@ __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const flo
   if (!__syncthreads_or(e != 0)) return;
   for (int64_t kc = 0; kc < nkc; ++kc) {
     const size_t boff = ((size_t)kc * rows_alloc + r0) * 128;
+    const size_t boff2 = ((size_t)(kc >> 1) * rows_alloc + r0) * 128;
     uint8_t* blk = panel + boff;
     for (int it = 0; it < 2; ++it) {
       const int idx = tid + 256 * it, rr = idx >> 2, cc = idx & 3;
@@ -373,7 +377,7 @@ __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const flo
         const float v = (r < rows && p + q < k) ? (kcontig ? X[r * ld + p + q] : X[r + (p + q) * ld]) : 0.f;
         x[q] = isfinite(v) ? scale_pow2(v, er) : v;
       }
-      if (panel2) store_split8_3(blk, panel2 + boff, rr, cc, x);
+      if (panel2) store_split8_3(blk, panel2 + boff2, (int)(kc & 1), rr, cc, x);
       else store_split8(blk, rr, cc, x);
     }
   }

@@ -223,8 +223,24 @@ def unpack_panel(panel: np.ndarray, rows: int, k: int):
     return hi, lo
 
 
+def unpack_compact_lo3(panel2: np.ndarray, rows: int, k: int):
+    """lo3 (rows padded as in the panel) x (k chunks of 32): block (j, rb) holds
+    k chunk 2j in logical chunks 0-3 and chunk 2j+1 in 4-7."""
+    RB = (rows + 255) // 256 * 2
+    KC = (k + 31) // 32
+    KP = (KC + 1) // 2
+    P = panel2[: KP * RB * 16384].view(np.uint16).reshape(KP, RB, 128, 8, 8)
+    r = np.arange(128)[:, None]
+    pos = np.arange(8)[None, :] ^ (r & 7)
+    L = P[:, :, r, pos, :]                                  # [pair][rb][row][logical chunk][element]
+    even = L[:, :, :, 0:4, :].reshape(KP, RB, 128, 32)
+    odd = L[:, :, :, 4:8, :].reshape(KP, RB, 128, 32)
+    both = np.stack([even, odd], axis=1).reshape(2 * KP, RB, 128, 32)[:KC]   # [kc][rb][row][32]
+    return both.transpose(1, 2, 0, 3).reshape(RB * 128, KC * 32)
+
+
 @pytest.mark.parametrize("which,trans", [("A", "N"), ("A", "T"), ("B", "N"), ("B", "T")])
-@pytest.mark.parametrize("rows,k", [(1, 1), (130, 37), (300, 300), (257, 1000), (200, 600)])
+@pytest.mark.parametrize("rows,k", [(1, 1), (130, 37), (300, 300), (257, 1000), (200, 600), (70, 160), (90, 480)])
 def test_split_pack_bit_exact(h, which, trans, rows, k):
     import torch
     from paper_1608_05265_gb300 import gbgemm
@@ -244,10 +260,11 @@ def test_split_pack_bit_exact(h, which, trans, rows, k):
     assert np.array_equal(glo[:rows, :k], lo)
     assert np.all(ghi[rows:] == 0) and np.all(glo[rows:] == 0)
     assert np.all(ghi[:, k:] == 0) and np.all(glo[:, k:] == 0)
-    if k < 512:  # three-part split: [lo3 | 0] in the second panel
-        g3, gz = unpack_panel(panel2.cpu().numpy(), rows, k)
+    if k < 512:  # three-part split: lo3 in the compact second panel
+        KC = (k + 31) // 32
+        g3 = unpack_compact_lo3(panel2.cpu().numpy(), rows, k)
         assert np.array_equal(g3[:rows, :k], lo3)
-        assert np.all(g3[rows:] == 0) and np.all(g3[:, k:] == 0) and np.all(gz == 0)
+        assert np.all(g3[rows:, :KC * 32] == 0) and np.all(g3[:, k:KC * 32] == 0)
     am = amax.cpu().numpy().view(np.uint32)
     L = synth.logical(X, sr, sc, ld)
     vec = L.T if kcontig else L
