@@ -527,6 +527,7 @@ def run_extras(h, stream, flop8192):
         from paper_1608_05265_gb300 import predictor
         h.predictor_set(predictor.load_weights(weights)[0])
         sources.append(("predicted", gbgemm.CONFIG_PREDICTED))
+    sources.append(("tuned", gbgemm.CONFIG_TUNED))  # exhaustive tuner: seconds of plan time
     for name, src in sources:
         t0 = time.time()
         plan = gbgemm.GroupedPlan(h, probs, config_source=src)

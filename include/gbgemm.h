@@ -203,6 +203,9 @@ typedef enum {
   GBGEMM_NUM_CONFIGS = 6
 } gbgemm_config;
 
+/* Every source keeps the default rule's path for a problem (split from
+ * k = 128, SIMT below); the tuner and the predictor choose the tile shape
+ * within that path. */
 typedef enum {
   GBGEMM_CONFIG_PREDICTED = 0,  /* learned predictor, tuner as fallback */
   GBGEMM_CONFIG_TUNED = 1,      /* exhaustive autotuner (timed on the GPU) */

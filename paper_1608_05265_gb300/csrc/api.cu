@@ -351,6 +351,13 @@ uint8_t legal_mask(const gbgemm_handle* h, const gbgemm_problem& q) {
   return m;
 }
 
+// Grouped plans keep the default rule's path for every problem (split from
+// k = 128, SIMT below) and let the tuner or the predictor pick the tile shape
+// within it: chosen per problem in isolation, moving problems between the
+// paths made whole batches slower (per-problem batch costs do not add up
+// across the graph's SIMT branches and split chain).
+uint8_t family_mask(int cfg) { return cfg >= GBGEMM_CFG_SPLIT_BN64 ? 0x38u : 0x07u; }
+
 bool in_training_range(const gbgemm_problem& q) {
   auto ok = [](int64_t v) { return v >= 8 && v <= 16384; };
   return ok(q.m) && ok(q.n) && ok(q.k);
@@ -368,7 +375,7 @@ int predict_configs(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count
     float f[8];
     gbg::predictor_features(probs[g], f);
     x.insert(x.end(), f, f + 8);
-    legal.push_back(legal_mask(h, probs[g]));
+    legal.push_back(legal_mask(h, probs[g]) & family_mask(gbg::default_config(probs[g])));
     which.push_back(g);
   }
   out.assign((size_t)count, -1);
@@ -421,7 +428,10 @@ int choose_configs(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count,
       h->tuner.bind(h->stream, h->d_status, h->num_sms);
       const int rc = h->tuner.measure(q, 3, &r);
       if (rc != GBGEMM_OK) return rc;
-      const int b = gbg::best_config(r, true);
+      const uint8_t fam = family_mask(cfg[g]);
+      int b = -1;
+      for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c)
+        if (((fam >> c) & 1u) && r.cost_us[c] >= 0.f && (b < 0 || r.cost_us[c] < r.cost_us[b])) b = c;
       if (b >= 0) cfg[g] = b;
     }
     if (cfg[g] >= GBGEMM_CFG_SPLIT_BN64 && !split_supported(h)) cfg[g] = GBGEMM_CFG_SIMT_128x128;
