@@ -31,56 +31,85 @@ struct SimtTile {
   static constexpr int B_REG = VEC ? B_VEC * 4 : B_SCL;
 };
 
-// Load one BM x BK slice of op(A) (or, with the roles swapped, one BK x BN
-// slice of op(B)) into registers.  `rowcontig` means consecutive tile rows
-// (the M or N index) are consecutive in memory; otherwise the k index is.
-// Elements outside [0, rows) x [0, kdim) read as zero.
+// Loads of one operand's BK-deep slices into registers.  A thread's load v
+// (v = 0 .. NL-1) of slice kt reads tile row r and k offset p with
+//   rowcontig (consecutive tile rows consecutive in memory, element (r, p) at
+//     X[r + p*ld]):  r = (tid % PER) W fixed,  p = tid / PER + v STRIDE;
+//   otherwise (element (r, p) at X[p + r*ld]):  p = (tid % PER) W fixed,
+//     r = tid / PER + v STRIDE,
+// W floats per load (4 with VEC).  One coordinate is fixed for the whole
+// tile and the other advances by a compile-time stride, so a base pointer
+// and counts of in-range loads, set up once per tile, replace per-element
+// index arithmetic and bounds checks.  Elements outside [0, rows) x [0, kdim)
+// read as zero; a float4 of rows (rowcontig VEC) is read when its first row
+// is in range (gr % 4 == 0 and ld % 4 == 0 keep it inside its column; rows
+// >= rows only feed outputs that are never stored).
 template <int ROWS, int NT, bool VEC, bool ROWCONTIG>
-__device__ __forceinline__ void load_slice(float* reg, const float* __restrict__ X, int64_t ld,
-                                           int64_t row0, int64_t rows, int64_t k0, int64_t kdim, int tid) {
-  if constexpr (VEC) {
-    constexpr int NV = ROWS * BK / 4 / NT;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int f = tid + v * NT;
-      int64_t r, p;
-      if constexpr (ROWCONTIG) { p = f / (ROWS / 4); r = (f % (ROWS / 4)) * 4; }
-      else { r = f / (BK / 4); p = (f % (BK / 4)) * 4; }
-      const int64_t gr = row0 + r, gp = k0 + p;
-      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-      if constexpr (ROWCONTIG) {
-        // Four consecutive rows of one k column.  gr % 4 == 0 and ld % 4 == 0
-        // keep the vector inside column gp; rows >= `rows` only feed outputs
-        // that are never stored.
-        if (gr < rows && gp < kdim) val = *reinterpret_cast<const float4*>(X + gr + gp * ld);
-      } else {
-        // Four consecutive k of one row; k beyond kdim is zeroed.
-        if (gr < rows && gp < kdim) {
-          val = *reinterpret_cast<const float4*>(X + gp + gr * ld);
-          if (gp + 1 >= kdim) val.y = 0.f;
-          if (gp + 2 >= kdim) val.z = 0.f;
-          if (gp + 3 >= kdim) val.w = 0.f;
-        }
-      }
-      reg[4 * v + 0] = val.x; reg[4 * v + 1] = val.y; reg[4 * v + 2] = val.z; reg[4 * v + 3] = val.w;
-    }
-  } else {
-    constexpr int NS = ROWS * BK / NT;
-#pragma unroll
-    for (int v = 0; v < NS; ++v) {
-      const int f = tid + v * NT;
-      int64_t r, p;
-      if constexpr (ROWCONTIG) { p = f / ROWS; r = f % ROWS; }
-      else { r = f / BK; p = f % BK; }
-      const int64_t gr = row0 + r, gp = k0 + p;
-      float val = 0.f;
-      if (gr < rows && gp < kdim) val = ROWCONTIG ? X[gr + gp * ld] : X[gp + gr * ld];
-      reg[v] = val;
+struct SliceLoader {
+  static constexpr int W = VEC ? 4 : 1;
+  static constexpr int PER = ROWCONTIG ? ROWS / W : BK / W;
+  static constexpr int STRIDE = NT / PER;
+  static constexpr int NL = ROWS * BK / W / NT;
+  static_assert(NT % PER == 0 && (STRIDE & (STRIDE - 1)) == 0, "load mapping");
+  static constexpr int KSHIFT = ROWCONTIG ? (STRIDE == 1 ? 4 : STRIDE == 2 ? 3 : STRIDE == 4 ? 2 : STRIDE == 8 ? 1 : 0) : 0;
+  static_assert(!ROWCONTIG || (BK >> KSHIFT) == STRIDE, "slice step = BK / STRIDE load steps");
+  const float* base;   // load v = 0 of slice 0
+  int64_t vstep;       // elements between a thread's consecutive loads (STRIDE ld)
+  int kfix;            // k offset of load v = 0 within a slice (rowcontig) or of every load (otherwise)
+  int nrow;            // loads whose row is in range
+
+  __device__ __forceinline__ SliceLoader(const float* X, int64_t ld, int64_t row0, int64_t rows, int tid) {
+    const int fx = (tid % PER) * W, vr = tid / PER;
+    vstep = (int64_t)STRIDE * ld;
+    if constexpr (ROWCONTIG) {
+      const int64_t r = row0 + fx;
+      base = X + r + (int64_t)vr * ld;
+      kfix = vr;
+      nrow = r < rows ? NL : 0;
+    } else {
+      const int64_t r = row0 + vr;
+      base = X + fx + r * ld;
+      kfix = fx;
+      const int64_t nv = r < rows ? (rows - r + STRIDE - 1) / STRIDE : 0;
+      nrow = nv < NL ? (int)nv : NL;
     }
   }
-}
 
-// Store the registers of load_slice into the k-major shared tile S[p][r].
+  // Slice kt of an operand with kdim k indices into reg[0 .. NL*W - 1].
+  __device__ __forceinline__ void load(float* reg, int64_t kt, int64_t kdim) const {
+    // one slice is BK / STRIDE load steps (rowcontig) or BK elements along the row
+    const float* p = ROWCONTIG ? base + ((kt * vstep) << KSHIFT) : base + kt * BK;
+    const int64_t krem = kdim - kt * BK - kfix;  // in-range k offsets from this thread's first one
+    int nv;
+    if constexpr (ROWCONTIG) {
+      const int64_t nk = krem <= 0 ? 0 : (krem + STRIDE - 1) / STRIDE;
+      nv = nk < nrow ? (int)nk : nrow;
+    } else {
+      nv = krem > 0 ? nrow : 0;
+    }
+#pragma unroll
+    for (int v = 0; v < NL; ++v) {
+      if constexpr (VEC) {
+        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v < nv) {
+          val = *reinterpret_cast<const float4*>(p);
+          if constexpr (!ROWCONTIG) {
+            // four consecutive k of one row; k beyond kdim is zeroed
+            if (krem < 2) val.y = 0.f;
+            if (krem < 3) val.z = 0.f;
+            if (krem < 4) val.w = 0.f;
+          }
+        }
+        reg[4 * v + 0] = val.x; reg[4 * v + 1] = val.y; reg[4 * v + 2] = val.z; reg[4 * v + 3] = val.w;
+      } else {
+        reg[v] = v < nv ? *p : 0.f;
+      }
+      p += vstep;
+    }
+  }
+};
+
+// Store the registers of SliceLoader::load into the k-major shared tile S[p][r].
 template <int ROWS, int NT, int LDS, bool VEC, bool ROWCONTIG>
 __device__ __forceinline__ void store_slice(float* S, const float* reg, int tid) {
   if constexpr (VEC) {
@@ -133,8 +162,10 @@ __device__ __forceinline__ void simt_tile(const Problem& P, int64_t m0, int64_t 
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-  load_slice<BM, NT, VEC, !TA>(ra, P.A, P.lda, m0, P.m, 0, P.k, tid);
-  load_slice<BN, NT, VEC, TB>(rb, P.B, P.ldb, n0, P.n, 0, P.k, tid);
+  const SliceLoader<BM, NT, VEC, !TA> LA(P.A, P.lda, m0, P.m, tid);
+  const SliceLoader<BN, NT, VEC, TB> LB(P.B, P.ldb, n0, P.n, tid);
+  LA.load(ra, 0, P.k);
+  LB.load(rb, 0, P.k);
   store_slice<BM, NT, T::LDS_A, VEC, !TA>(As[0], ra, tid);
   store_slice<BN, NT, T::LDS_B, VEC, TB>(Bs[0], rb, tid);
   __syncthreads();
@@ -142,8 +173,8 @@ __device__ __forceinline__ void simt_tile(const Problem& P, int64_t m0, int64_t 
   for (int64_t kt = 0; kt < nk; ++kt) {
     const int cur = (int)(kt & 1);
     if (kt + 1 < nk) {
-      load_slice<BM, NT, VEC, !TA>(ra, P.A, P.lda, m0, P.m, (kt + 1) * BK, P.k, tid);
-      load_slice<BN, NT, VEC, TB>(rb, P.B, P.ldb, n0, P.n, (kt + 1) * BK, P.k, tid);
+      LA.load(ra, kt + 1, P.k);
+      LB.load(rb, kt + 1, P.k);
     }
     const float* a_s = As[cur];
     const float* b_s = Bs[cur];
