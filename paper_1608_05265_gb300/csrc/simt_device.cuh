@@ -6,9 +6,10 @@
 // slices, and a register-tiled micro-kernel accumulates each thread's 8 x 8
 // piece over all slices before alpha and beta are applied once (the
 // "Accumulator" of Section III-C: clear once, accumulate, write the result
-// once).  Slices are staged through shared memory in two buffers, the next
-// slice's global loads in flight while the current one is multiplied (the
-// double-buffered input staging of Section III-C, within one thread block).
+// once).  Slices are staged in shared memory in two buffers by asynchronous
+// copies, the next slice's copies in flight while the current one is
+// multiplied (the double-buffered input staging of Section III-C, within one
+// thread block).
 #pragma once
 
 #include "internal.h"
@@ -23,15 +24,18 @@ struct SimtTile {
   static constexpr int NT = (BM / 8) * (BN / 8);
   static constexpr int LDS_A = BM + 4;
   static constexpr int LDS_B = BN + 4;
-  static constexpr int A_VEC = BM * BK / 4 / NT;   // float4 loads per thread
-  static constexpr int B_VEC = BN * BK / 4 / NT;
-  static constexpr int A_SCL = BM * BK / NT;       // scalar loads per thread
-  static constexpr int B_SCL = BN * BK / NT;
-  static constexpr int A_REG = VEC ? A_VEC * 4 : A_SCL;
-  static constexpr int B_REG = VEC ? B_VEC * 4 : B_SCL;
 };
 
-// Loads of one operand's BK-deep slices into registers.  A thread's load v
+__device__ __forceinline__ void cp_async4s(uint32_t dst, const float* src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Loads of one operand's BK-deep slices into shared memory.  A thread's load v
 // (v = 0 .. NL-1) of slice kt reads tile row r and k offset p with
 //   rowcontig (consecutive tile rows consecutive in memory, element (r, p) at
 //     X[r + p*ld]):  r = (tid % PER) W fixed,  p = tid / PER + v STRIDE;
@@ -75,9 +79,43 @@ struct SliceLoader {
     }
   }
 
-  // Slice kt of an operand with kdim k indices into reg[0 .. NL*W - 1].
+  // Register staging, used for the VEC k-contiguous case only (its float4 of
+  // four k values lands in four rows of the k-major tile, which a 16-byte
+  // asynchronous copy cannot do): slice kt into reg[0 .. 4 NL - 1] ...
   __device__ __forceinline__ void load(float* reg, int64_t kt, int64_t kdim) const {
-    // one slice is BK / STRIDE load steps (rowcontig) or BK elements along the row
+    static_assert(VEC && !ROWCONTIG, "register staging serves the VEC k-contiguous case");
+    const float* p = base + kt * BK;
+    const int64_t krem = kdim - kt * BK - kfix;
+    const int nv = krem > 0 ? nrow : 0;
+#pragma unroll
+    for (int v = 0; v < NL; ++v) {
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (v < nv) {
+        val = *reinterpret_cast<const float4*>(p);
+        if (krem < 2) val.y = 0.f;  // k beyond kdim is zeroed
+        if (krem < 3) val.z = 0.f;
+        if (krem < 4) val.w = 0.f;
+      }
+      reg[4 * v + 0] = val.x; reg[4 * v + 1] = val.y; reg[4 * v + 2] = val.z; reg[4 * v + 3] = val.w;
+      p += vstep;
+    }
+  }
+  // ... and from the registers into the k-major shared tile S[p][r].
+  template <int LDS>
+  __device__ __forceinline__ void store(float* S, const float* reg, int tid) const {
+    const int fx = (tid % PER) * W, vr = tid / PER;
+#pragma unroll
+    for (int v = 0; v < NL; ++v)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) S[(fx + q) * LDS + vr + v * STRIDE] = reg[4 * v + q];
+  }
+
+  // Copy slice kt of an operand with kdim k indices into the k-major shared
+  // tile S[p][r] (row pitch LDS floats, at shared address s_addr) with
+  // asynchronous copies: out-of-range elements are zero-filled without a
+  // read (and with the source pointer kept at a valid address).
+  template <int LDS>
+  __device__ __forceinline__ void issue(uint32_t s_addr, int64_t kt, int64_t kdim, const float* X, int tid) const {
     const float* p = ROWCONTIG ? base + ((kt * vstep) << KSHIFT) : base + kt * BK;
     const int64_t krem = kdim - kt * BK - kfix;  // in-range k offsets from this thread's first one
     int nv;
@@ -87,57 +125,25 @@ struct SliceLoader {
     } else {
       nv = krem > 0 ? nrow : 0;
     }
+    const int fx = (tid % PER) * W, vr = tid / PER;
 #pragma unroll
     for (int v = 0; v < NL; ++v) {
-      if constexpr (VEC) {
-        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v < nv) {
-          val = *reinterpret_cast<const float4*>(p);
-          if constexpr (!ROWCONTIG) {
-            // four consecutive k of one row; k beyond kdim is zeroed
-            if (krem < 2) val.y = 0.f;
-            if (krem < 3) val.z = 0.f;
-            if (krem < 4) val.w = 0.f;
-          }
-        }
-        reg[4 * v + 0] = val.x; reg[4 * v + 1] = val.y; reg[4 * v + 2] = val.z; reg[4 * v + 3] = val.w;
+      const bool ok = v < nv;
+      const float* src = ok ? p : X;
+      if constexpr (ROWCONTIG) {
+        // tile row fx (.. fx + W - 1), k offset vr + v STRIDE
+        const uint32_t dst = s_addr + (uint32_t)((vr + v * STRIDE) * LDS + fx) * 4u;
+        if constexpr (VEC) cp_async16(dst, src, ok ? 16u : 0u);
+        else cp_async4s(dst, src, ok ? 4u : 0u);
       } else {
-        reg[v] = v < nv ? *p : 0.f;
+        // k offset fx, tile row vr + v STRIDE (scalar: VEC goes through registers)
+        static_assert(!VEC, "the VEC k-contiguous case uses load() and store()");
+        cp_async4s(s_addr + (uint32_t)(fx * LDS + vr + v * STRIDE) * 4u, src, ok ? 4u : 0u);
       }
       p += vstep;
     }
   }
 };
-
-// Store the registers of SliceLoader::load into the k-major shared tile S[p][r].
-template <int ROWS, int NT, int LDS, bool VEC, bool ROWCONTIG>
-__device__ __forceinline__ void store_slice(float* S, const float* reg, int tid) {
-  if constexpr (VEC) {
-    constexpr int NV = ROWS * BK / 4 / NT;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int f = tid + v * NT;
-      if constexpr (ROWCONTIG) {
-        const int p = f / (ROWS / 4), r = (f % (ROWS / 4)) * 4;
-        *reinterpret_cast<float4*>(S + p * LDS + r) = make_float4(reg[4 * v], reg[4 * v + 1], reg[4 * v + 2], reg[4 * v + 3]);
-      } else {
-        const int r = f / (BK / 4), p = (f % (BK / 4)) * 4;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) S[(p + q) * LDS + r] = reg[4 * v + q];
-      }
-    }
-  } else {
-    constexpr int NS = ROWS * BK / NT;
-#pragma unroll
-    for (int v = 0; v < NS; ++v) {
-      const int f = tid + v * NT;
-      int r, p;
-      if constexpr (ROWCONTIG) { p = f / ROWS; r = f % ROWS; }
-      else { r = f / BK; p = f % BK; }
-      S[p * LDS + r] = reg[v];
-    }
-  }
-}
 
 // One BM x BN tile of C = alpha*op(A)*op(B) + beta*C starting at (m0, n0),
 // computed by the (BM/8)*(BN/8) threads of the calling block.  As and Bs are
@@ -155,27 +161,43 @@ __device__ __forceinline__ void simt_tile(const Problem& P, int64_t m0, int64_t 
 
   // op(A): rows are M (contiguous when A is not transposed).
   // op(B): rows of the staged tile are N (contiguous when B is transposed).
-  float ra[T::A_REG], rb[T::B_REG];
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-  const SliceLoader<BM, NT, VEC, !TA> LA(P.A, P.lda, m0, P.m, tid);
-  const SliceLoader<BN, NT, VEC, TB> LB(P.B, P.ldb, n0, P.n, tid);
-  LA.load(ra, 0, P.k);
-  LB.load(rb, 0, P.k);
-  store_slice<BM, NT, T::LDS_A, VEC, !TA>(As[0], ra, tid);
-  store_slice<BN, NT, T::LDS_B, VEC, TB>(Bs[0], rb, tid);
+  using LoadA = SliceLoader<BM, NT, VEC, !TA>;
+  using LoadB = SliceLoader<BN, NT, VEC, TB>;
+  constexpr bool REG_A = VEC && TA, REG_B = VEC && !TB;  // k-contiguous float4 operands stage through registers
+  const LoadA LA(P.A, P.lda, m0, P.m, tid);
+  const LoadB LB(P.B, P.ldb, n0, P.n, tid);
+  float ra[REG_A ? LoadA::NL * 4 : 1], rb[REG_B ? LoadB::NL * 4 : 1];
+  const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(As[0]), sA1 = (uint32_t)__cvta_generic_to_shared(As[1]);
+  const uint32_t sB0 = (uint32_t)__cvta_generic_to_shared(Bs[0]), sB1 = (uint32_t)__cvta_generic_to_shared(Bs[1]);
+  // slice kt into buffer b (register-staged operands: into registers only)
+  auto fetch = [&](int64_t kt, int b) {
+    if constexpr (REG_A) LA.load(ra, kt, P.k);
+    else LA.template issue<T::LDS_A>(b ? sA1 : sA0, kt, P.k, P.A, tid);
+    if constexpr (REG_B) LB.load(rb, kt, P.k);
+    else LB.template issue<T::LDS_B>(b ? sB1 : sB0, kt, P.k, P.B, tid);
+    cp_async_commit_all();
+  };
+  auto put = [&](int b) {  // register-staged operands into buffer b
+    if constexpr (REG_A) LA.template store<T::LDS_A>(As[b], ra, tid);
+    if constexpr (REG_B) LB.template store<T::LDS_B>(Bs[b], rb, tid);
+  };
+  if (nk > 0) {  // (k = 0: A and B are not read, and may be null)
+    fetch(0, 0);
+    put(0);
+    cp_async_wait_all();
+  }
   __syncthreads();
 
   for (int64_t kt = 0; kt < nk; ++kt) {
     const int cur = (int)(kt & 1);
-    if (kt + 1 < nk) {
-      LA.load(ra, kt + 1, P.k);
-      LB.load(rb, kt + 1, P.k);
-    }
+    // the other buffer was last read before the previous barrier
+    if (kt + 1 < nk) fetch(kt + 1, cur ^ 1);
     const float* a_s = As[cur];
     const float* b_s = Bs[cur];
     // Unrolled by two, not sixteen: the fully unrolled slice (about 1100
@@ -194,10 +216,8 @@ __device__ __forceinline__ void simt_tile(const Problem& P, int64_t m0, int64_t 
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (kt + 1 < nk) {
-      store_slice<BM, NT, T::LDS_A, VEC, !TA>(As[cur ^ 1], ra, tid);
-      store_slice<BN, NT, T::LDS_B, VEC, TB>(Bs[cur ^ 1], rb, tid);
-    }
+    if (kt + 1 < nk) put(cur ^ 1);
+    cp_async_wait_all();  // the next slice's copies by this thread have landed
     __syncthreads();
   }
 
