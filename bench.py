@@ -490,7 +490,34 @@ def run_extras(h, stream, flop8192):
             del A, B, C, C0
     out["linpack_updates"] = dict(lp, note=(f"bytes = 8 m n + 4 (m + n) nb; HBM peak {hbm:.0f} GB/s ({peak_src}); "
                                             "median of 10 calls; L2 flushed before each call for m = 4096"))
-    del flush
+    # -- strided batch of the paper's micro-kernel problem (Table I: m 192, n 256,
+    #    K 4096), 64 problems, NN, alpha 1, beta 0, uniform --
+    mb, nbat, kb, batch = 192, 256, 4096, 64
+    g.manual_seed(5)
+    Ab = torch.rand(mb * kb * batch, device="cuda", generator=g) * 2 - 1
+    Bb = torch.rand(kb * nbat * batch, device="cuda", generator=g) * 2 - 1
+    Cb = torch.zeros(mb * nbat * batch, device="cuda")
+    h.set_path(gbgemm.PATH_AUTO)
+    run_b = lambda: h.sgemm_strided_batched("N", "N", mb, nbat, kb, 1.0, Ab, mb, mb * kb, Bb, kb, kb * nbat, 0.0,
+                                            Cb, mb, mb * nbat, batch)
+    med_b, min_b = _time_stats(run_b, stream, 10, flush)
+    run_s = lambda: [h.sgemm("N", "N", mb, nbat, kb, 1.0, Ab[z * mb * kb:], mb, Bb[z * kb * nbat:], kb, 0.0,
+                             Cb[z * mb * nbat:], mb) for z in range(batch)]
+    med_s, _ = _time_stats(run_s, stream, 5, flush)
+    run_b()
+    torch.cuda.synchronize()
+    errb = max(h.check_error("N", "N", mb, nbat, kb, 1.0, Ab[z * mb * kb:], mb, Bb[z * kb * nbat:], kb, 0.0,
+                             Cb[z * mb * nbat:], Cb[z * mb * nbat:], mb) for z in (0, batch - 1))
+    flb = batch * metrics.gemm_flops(mb, nbat, kb)
+    out["batched_192x256x4096"] = {
+        "batch": batch, "ms_median": med_b, "tflops": flb / (med_b * 1e-3) / 1e12,
+        "tflops_best": flb / (min_b * 1e-3) / 1e12, "single_calls_ms": med_s,
+        "single_calls_tflops": flb / (med_s * 1e-3) / 1e12, "max_error_ratio": errb,
+        "path": "split" if h.last_path() == 2 else "simt",
+        "note": ("the paper's micro-kernel problem (Table I, 192 x 256 x 4096), 64 at once through "
+                 "gbgemm_sgemm_strided_batched; single_calls = the same 64 problems as gbgemm_sgemm calls; "
+                 "error ratio on problems 0 and 63 (FP64 on the GPU)")}
+    del Ab, Bb, Cb, flush
     # -- grouped uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024] (seed 3) --
     shapes = synth.grouped_shapes(3, 4096)
     bufs, probs = [], []

@@ -123,6 +123,26 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
                  float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
                  float beta, float* C, int64_t ldc);
 
+/* Strided batch of `batch` equal sgemms: problem z (0 <= z < batch) is
+ *   C_z := alpha op(A_z) op(B_z) + beta C_z,
+ *   A_z = A + z*stride_a, B_z = B + z*stride_b, C_z = C + z*stride_c (elements),
+ * each as in gbgemm_sgemm.  The paper's micro-kernel is exactly such a series
+ * of fixed-size problems fed by BLIS (Section III-A, III-C); the paper itself
+ * has no batched call.  stride_a or stride_b 0 shares one operand among all
+ * problems; the results must not overlap (stride_c >= ldc (n - 1) + m when
+ * batch > 1).  One packing launch per operand and one persistent GEMM launch
+ * serve the whole batch (split path), or one SIMT launch.  The workspace
+ * holds batch x gbgemm_split_workspace_bytes(m, n, k) bytes on the split path.
+ * Argument errors, in this order: transa -1, transb -2, m -3, n -4, k -5,
+ * lda -8, stride_a -9, ldb -11, stride_b -12, ldc -15, stride_c -16,
+ * batch (< 0 or > 65535) -17; then null A (when read) -7, null B -10,
+ * null C -14.  Then GBGEMM_ERR_NOT_INITIALIZED for a NULL handle.  batch 0
+ * returns at once.  Queues kernels on the handle's stream. */
+int gbgemm_sgemm_strided_batched(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                                 float alpha, const float* A, int64_t lda, int64_t stride_a, const float* B,
+                                 int64_t ldb, int64_t stride_b, float beta, float* C, int64_t ldc, int64_t stride_c,
+                                 int64_t batch);
+
 /* Synchronise the handle's stream, then read and clear the device status
  * word: *status = 0 when no kernel reported a failure since the last read,
  * else the first failing kernel's code (GBGEMM_ERR_DEVICE_TIMEOUT).  Returns

@@ -179,32 +179,19 @@ int gbgemm_reserve_workspace(gbgemm_handle* h, size_t bytes) {
   return ensure_workspace(h, bytes);
 }
 
-int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k,
-                 float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
-                 float beta, float* C, int64_t ldc) {
-  const int ta = trans_code(transa), tb = trans_code(transb);
-  if (ta < 0) return -1;
-  if (tb < 0) return -2;
-  if (m < 0) return -3;
-  if (n < 0) return -4;
-  if (k < 0) return -5;
-  const int64_t arows = ta ? k : m, brows = tb ? n : k;
-  if (lda < (arows > 1 ? arows : 1)) return -8;
-  if (ldb < (brows > 1 ? brows : 1)) return -10;
-  if (ldc < (m > 1 ? m : 1)) return -13;
+// The call after argument checks: one problem (batch 1) or a strided batch of
+// equal problems, problem z at A + z*sa, B + z*sb, C + z*sc.
+static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                     float alpha, const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                     int64_t ldc, int64_t batch, int64_t sa, int64_t sb, int64_t sc) {
   const bool use_ab = (alpha != 0.0f) && (k > 0);
-  if (m > 0 && n > 0) {
-    if (use_ab && !A) return -7;
-    if (use_ab && !B) return -9;
-    if (!C) return -12;
-  }
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   h->last_path = 0;
   if (m == 0 || n == 0) return GBGEMM_OK;
   if (!use_ab && beta == 1.0f) return GBGEMM_OK;
   DeviceGuard g(h->device);
   if (!use_ab) {
-    if (gbg::launch_scale_c(m, n, beta, C, ldc, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    if (gbg::launch_scale_c_batched(m, n, beta, C, ldc, batch, sc, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
     h->kernel_launches += 1;
     return GBGEMM_OK;
   }
@@ -214,11 +201,11 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   // Default tiles.  Split: the widest tile that still gives at least half of
   // the SMs a tile (measured at 2048^3: 128 BN-256 tiles beat 256 BN-128
   // tiles, 208 against 150 TFLOP/s).  SIMT: 64 x 64 for small outputs.
-  auto tiles = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn); };
+  auto tiles = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn) * batch; };
   const int64_t half_sms = h->num_sms / 2;
   int simt_cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
   int split_bn = tiles(128, 256) >= half_sms ? 256 : tiles(128, 128) >= half_sms ? 128 : 64;
-  if (h->tuning == 1) {
+  if (h->tuning == 1 && batch == 1) {
     const gbgemm_problem q{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
     gbg::TuneResult r;
     h->tuner.bind(h->stream, h->d_status, h->num_sms);
@@ -242,7 +229,7 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   }
   if (path == GBGEMM_PATH_SIMT) {
     const int cfg = simt_cfg;
-    if (gbg::launch_simt(p, cfg, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    if (gbg::launch_simt_batched(p, cfg, batch, sa, sb, sc, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
     h->kernel_launches += 1;
     h->last_path = GBGEMM_PATH_SIMT;
     return GBGEMM_OK;
@@ -250,9 +237,12 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   if (!split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
   const size_t pa = align_up(gbg::panel_bytes(m, k), 256), pb = align_up(gbg::panel_bytes(n, k), 256);
   const size_t xa = align_up((size_t)m * 4, 256);
-  int rc = ensure_workspace(h, gbgemm_split_workspace_bytes(m, n, k));
+  // workspace: per problem z, at z * block bytes:
+  //   [panel A | panel B | maxima A | maxima B | (three parts) panel A2 | panel B2]
+  const size_t block = gbgemm_split_workspace_bytes(m, n, k);
+  if (block > ((size_t)1 << 62) / (size_t)batch) return GBGEMM_ERR_ALLOC;
+  int rc = ensure_workspace(h, block * (size_t)batch);
   if (rc != GBGEMM_OK) return rc;
-  // workspace: [panel A | panel B | maxima A | maxima B | (three parts) panel A2 | panel B2]
   uint8_t* ws = static_cast<uint8_t*>(h->ws);
   void* panelA = ws;
   void* panelB = ws + pa;
@@ -263,10 +253,13 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   void* panelA2 = three ? ws + pa + pb + xa + xb : nullptr;
   void* panelB2 = three ? ws + pa + pb + xa + xb + pa : nullptr;
   // Rows of op(A): element (i, p) at A[p + i*lda] when transposed (k contiguous).
-  if (gbg::launch_split_pack(m, k, A, lda, ta == 1, amaxA, panelA, panelA2, h->stream) != cudaSuccess)
+  const int64_t bw = (int64_t)(block / 4);  // maxima stride in words
+  if (gbg::launch_split_pack_batched(m, k, A, lda, ta == 1, amaxA, panelA, panelA2, batch, sa, bw, (int64_t)block,
+                                     h->stream) != cudaSuccess)
     return GBGEMM_ERR_CUDA;
   // Columns of op(B): element (j, p) at B[p + j*ldb] when not transposed (k contiguous).
-  if (gbg::launch_split_pack(n, k, B, ldb, tb == 0, amaxB, panelB, panelB2, h->stream) != cudaSuccess)
+  if (gbg::launch_split_pack_batched(n, k, B, ldb, tb == 0, amaxB, panelB, panelB2, batch, sb, bw, (int64_t)block,
+                                     h->stream) != cudaSuccess)
     return GBGEMM_ERR_CUDA;
   gbg::SplitGemmArgs a;
   a.panelA = panelA; a.panelB = panelB; a.amaxA = amaxA; a.amaxB = amaxB;
@@ -274,6 +267,7 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
   a.status = h->d_status; a.num_sms = h->num_sms;
   a.bn = split_bn; a.raster = 16;
+  a.batch = batch; a.panel_stride = (int64_t)block; a.amax_stride = bw; a.c_stride = sc;
   h->kernel_launches += 4;  // two packing and two re-packing kernels
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (gbg::launch_split_gemm(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
@@ -282,6 +276,63 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
   h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;
   return GBGEMM_OK;
+}
+
+
+int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                 float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                 float beta, float* C, int64_t ldc) {
+  const int ta = trans_code(transa), tb = trans_code(transb);
+  if (ta < 0) return -1;
+  if (tb < 0) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  const int64_t arows = ta ? k : m, brows = tb ? n : k;
+  if (lda < (arows > 1 ? arows : 1)) return -8;
+  if (ldb < (brows > 1 ? brows : 1)) return -10;
+  if (ldc < (m > 1 ? m : 1)) return -13;
+  const bool use_ab = (alpha != 0.0f) && (k > 0);
+  if (m > 0 && n > 0) {
+    if (use_ab && !A) return -7;
+    if (use_ab && !B) return -9;
+    if (!C) return -12;
+  }
+  return run_sgemm(h, ta, tb, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 1, 0, 0, 0);
+}
+
+int gbgemm_sgemm_strided_batched(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                                 float alpha, const float* A, int64_t lda, int64_t stride_a, const float* B,
+                                 int64_t ldb, int64_t stride_b, float beta, float* C, int64_t ldc, int64_t stride_c,
+                                 int64_t batch) {
+  const int ta = trans_code(transa), tb = trans_code(transb);
+  if (ta < 0) return -1;
+  if (tb < 0) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  const int64_t arows = ta ? k : m, brows = tb ? n : k;
+  if (lda < (arows > 1 ? arows : 1)) return -8;
+  if (stride_a < 0) return -9;
+  if (ldb < (brows > 1 ? brows : 1)) return -11;
+  if (stride_b < 0) return -12;
+  if (ldc < (m > 1 ? m : 1)) return -15;
+  // results of different problems must not overlap
+  if (stride_c < 0 || (batch > 1 && m > 0 && n > 0 && stride_c < ldc * (n - 1) + m)) return -16;
+  if (batch < 0 || batch > 65535) return -17;
+  const bool use_ab = (alpha != 0.0f) && (k > 0);
+  if (m > 0 && n > 0 && batch > 0) {
+    if (use_ab && !A) return -7;
+    if (use_ab && !B) return -10;
+    if (!C) return -14;
+  }
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (batch == 0) {
+    h->last_path = 0;
+    return GBGEMM_OK;
+  }
+  return run_sgemm(h, ta, tb, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, batch, stride_a,
+                   stride_b, stride_c);
 }
 
 int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,

@@ -75,7 +75,9 @@ __device__ __forceinline__ const uint8_t* panel_rows(const uint8_t* panel, int64
   return panel + (size_t)(r0 >> 7) * kBlockBytes + (size_t)(r0 & 127) * 128;
 }
 
-// One problem, tiles of 128 x BN in groups of `raster` tile rows.
+// One problem, or a strided batch of equal problems, tiles of 128 x BN in
+// groups of `raster` tile rows; problem z has its panels at panelA/B + z*ps,
+// its row maxima at amaxA/B + z*as and its result at C + z*cs.
 struct SingleSched {
   const uint8_t* panelA; const uint8_t* panelB;
   const uint32_t* amaxA; const uint32_t* amaxB;
@@ -85,21 +87,25 @@ struct SingleSched {
   int tiles_m, tiles_n, nkc, raster, bn, parts;
   int64_t rbA, rbB;
   int64_t a_part, b_part;
-  __device__ __forceinline__ int num_items() const { return tiles_m * tiles_n; }
+  int batch;
+  int64_t ps, as, cs;
+  __device__ __forceinline__ int num_items() const { return tiles_m * tiles_n * batch; }
   __device__ __forceinline__ TileJob job(int t) const {
+    const int per = tiles_m * tiles_n;
+    const int z = t / per;
     int tm, tn;
-    tile_coords(t, tiles_m, tiles_n, raster, tm, tn);
+    tile_coords(t - z * per, tiles_m, tiles_n, raster, tm, tn);
     TileJob j;
-    j.a_src = panelA + (size_t)tm * kBlockBytes;
-    j.b_src = panel_rows(panelB, (int64_t)tn * bn);
+    j.a_src = panelA + (size_t)z * ps + (size_t)tm * kBlockBytes;
+    j.b_src = panel_rows(panelB + (size_t)z * ps, (int64_t)tn * bn);
     j.a_kstride = (size_t)rbA * kBlockBytes;
     j.b_kstride = (size_t)rbB * kBlockBytes;
     j.nkc = nkc; j.bn = bn;
     j.parts = parts; j.a_part = a_part; j.b_part = b_part;
     j.m0 = (int64_t)tm * 128; j.n0 = (int64_t)tn * bn;
     j.m = m; j.n = n;
-    j.amaxA = amaxA; j.amaxB = amaxB;
-    j.C = C; j.ldc = ldc; j.alpha = alpha; j.beta = beta;
+    j.amaxA = amaxA + (size_t)z * as; j.amaxB = amaxB + (size_t)z * as;
+    j.C = C + (size_t)z * cs; j.ldc = ldc; j.alpha = alpha; j.beta = beta;
     return j;
   }
 };

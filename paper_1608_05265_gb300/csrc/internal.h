@@ -22,8 +22,14 @@ struct Problem {
 // Tile configurations of the SIMT kernel, indexed by the autotuner.
 enum SimtConfig { SIMT_128x128 = 0, SIMT_64x64 = 1, SIMT_128x64 = 2, SIMT_NUM_CONFIGS = 3 };
 cudaError_t launch_simt(const Problem& p, int config, cudaStream_t s);
+// A strided batch of equal problems (batch <= 65535): problem z reads
+// A + z*sa, B + z*sb and writes C + z*sc.
+cudaError_t launch_simt_batched(const Problem& p, int config, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                cudaStream_t s);
 // C := beta * C over m x n (beta == 0 writes zeros without reading C).
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t s);
+cudaError_t launch_scale_c_batched(int64_t m, int64_t n, float beta, float* C, int64_t ldc, int64_t batch,
+                                   int64_t sc, cudaStream_t s);
 
 // ---- split path (split.cu) ----
 constexpr int kPanelRows = 128;     // rows per panel block
@@ -52,6 +58,11 @@ inline size_t panel_bytes(int64_t rows, int64_t k) {
 // ignored (may be NULL).
 cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
                               uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s);
+// The same for a strided batch (batch <= 65535): problem z reads X + z*xs and
+// writes amax_bits + z*as (as >= rows) and panel(2) + z*ps.
+cudaError_t launch_split_pack_batched(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
+                                      uint32_t* amax_bits, void* panel, void* panel2, int64_t batch, int64_t xs,
+                                      int64_t as, int64_t ps, cudaStream_t s);
 
 struct SplitGemmArgs {
   const void* panelA; const void* panelB;     // [hi | lo] (or [hi | mid]) panels
@@ -62,8 +73,13 @@ struct SplitGemmArgs {
   float* C; int64_t ldc;
   int* status;
   int num_sms;
-  int bn;          // 256 or 128
+  int bn;          // 256, 128 or 64
   int raster;      // tile-row group size of the tile order
+  // strided batch (batch 0 or 1: one problem): problem z's panels at
+  // panelA/B(2) + z*panel_stride bytes, maxima at amaxA/B + z*amax_stride
+  // words, result at C + z*c_stride elements
+  int64_t batch = 1;
+  int64_t panel_stride = 0, amax_stride = 0, c_stride = 0;
 };
 cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s);
 

@@ -32,41 +32,61 @@
 namespace gbg {
 namespace {
 
+// blockIdx.z selects the problem of a strided batch: its operand at
+// X + z*xs, its row maxima at amax + z*as, its panels at panel(2) + z*ps.
 template <bool KCONTIG>
 __global__ void __launch_bounds__(256) pack_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                                    uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
-                                                   uint8_t* __restrict__ panel2, int64_t rows_alloc) {
+                                                   uint8_t* __restrict__ panel2, int64_t rows_alloc, int64_t xs,
+                                                   int64_t as, int64_t ps) {
   __shared__ uint32_t smax[128];
-  pack_block<KCONTIG>(rows, k, X, ld, amax, panel, panel2, rows_alloc, blockIdx.x, blockIdx.y, smax);
+  const int64_t z = blockIdx.z;
+  pack_block<KCONTIG>(rows, k, X + z * xs, ld, amax + z * as, panel + z * ps, panel2 ? panel2 + z * ps : nullptr,
+                      rows_alloc, blockIdx.x, blockIdx.y, smax);
 }
 
 __global__ void __launch_bounds__(256) rescale_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                                       bool kcontig, const uint32_t* __restrict__ amax,
                                                       uint8_t* __restrict__ panel, uint8_t* __restrict__ panel2,
-                                                      int64_t rows_alloc, int64_t nkc) {
+                                                      int64_t rows_alloc, int64_t nkc, int64_t xs, int64_t as,
+                                                      int64_t ps) {
   __shared__ int se[128];
-  rescale_block(rows, k, X, ld, kcontig, amax, panel, panel2, rows_alloc, nkc, blockIdx.x, se);
+  const int64_t z = blockIdx.z;
+  rescale_block(rows, k, X + z * xs, ld, kcontig, amax + z * as, panel + z * ps, panel2 ? panel2 + z * ps : nullptr,
+                rows_alloc, nkc, blockIdx.x, se);
 }
 
 }  // namespace
 
 cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
                               uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s) {
-  if (rows <= 0 || k <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(amax_bits, 0, (size_t)rows * sizeof(uint32_t), s);
+  return launch_split_pack_batched(rows, k, X, ld, kcontig, amax_bits, panel, panel2, 1, 0, 0, 0, s);
+}
+
+cudaError_t launch_split_pack_batched(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
+                                      uint32_t* amax_bits, void* panel, void* panel2, int64_t batch, int64_t xs,
+                                      int64_t as, int64_t ps, cudaStream_t s) {
+  if (rows <= 0 || k <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidConfiguration;
+  if (batch > 1 && as < rows) return cudaErrorInvalidValue;
+  // every problem's row maxima start at zero (they sit between its panels)
+  cudaError_t e = batch == 1 ? cudaMemsetAsync(amax_bits, 0, (size_t)rows * sizeof(uint32_t), s)
+                             : cudaMemset2DAsync(amax_bits, (size_t)as * sizeof(uint32_t), 0,
+                                                 (size_t)rows * sizeof(uint32_t), (size_t)batch, s);
   if (e != cudaSuccess) return e;
   const int64_t rbc = panel_row_blocks(rows);
   const int64_t nkc = panel_k_chunks(k);
-  dim3 g((unsigned)rbc, (unsigned)nkc);
+  dim3 g((unsigned)rbc, (unsigned)nkc, (unsigned)batch);
   if (g.y > 65535u) return cudaErrorInvalidConfiguration;
   uint8_t* pn = static_cast<uint8_t*>(panel);
   uint8_t* pn2 = split_parts(k) == 2 ? static_cast<uint8_t*>(panel2) : nullptr;
   if (split_parts(k) == 2 && !pn2) return cudaErrorInvalidValue;
-  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128);
-  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128);
+  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128, xs, as, ps);
+  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128, xs, as, ps);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  rescale_kernel<<<(unsigned)rbc, 256, 0, s>>>(rows, k, X, ld, kcontig, amax_bits, pn, pn2, rbc * 128, nkc);
+  rescale_kernel<<<dim3((unsigned)rbc, 1, (unsigned)batch), 256, 0, s>>>(rows, k, X, ld, kcontig, amax_bits, pn, pn2,
+                                                                         rbc * 128, nkc, xs, as, ps);
   return cudaGetLastError();
 }
 
@@ -74,7 +94,8 @@ cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s) {
   if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
   if (a.bn != 64 && a.bn != 128 && a.bn != 256) return cudaErrorInvalidValue;
   const int64_t tm = (a.m + 127) / 128, tn = (a.n + a.bn - 1) / a.bn;
-  if (tm * tn > (int64_t)0x7FFFFFFF || panel_k_chunks(a.k) > (int64_t)0x7FFFFFFF) return cudaErrorInvalidValue;
+  const int64_t batch = a.batch > 0 ? a.batch : 1;
+  if (tm * tn * batch > (int64_t)0x7FFFFFFF || panel_k_chunks(a.k) > (int64_t)0x7FFFFFFF) return cudaErrorInvalidValue;
   SingleSched S;
   S.panelA = static_cast<const uint8_t*>(a.panelA);
   S.panelB = static_cast<const uint8_t*>(a.panelB);
@@ -92,9 +113,11 @@ cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s) {
   if (S.parts == 2 && (!a.panelA2 || !a.panelB2)) return cudaErrorInvalidValue;
   S.a_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelA2) - S.panelA) : 0;
   S.b_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelB2) - S.panelB) : 0;
+  S.batch = (int)batch;
+  S.ps = a.panel_stride; S.as = a.amax_stride; S.cs = a.c_stride;
   cudaError_t e = ensure_gemm_smem_attr<SingleSched>();
   if (e != cudaSuccess) return e;
-  const int64_t tiles = tm * tn;
+  const int64_t tiles = tm * tn * batch;
   const int64_t sms = a.num_sms > 0 ? a.num_sms : 148;
   const int grid = (int)(tiles < sms ? tiles : sms);
   split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, a.status, kTimeoutNs);

@@ -59,7 +59,8 @@ class Problem(ctypes.Structure):
 #: Symbols exported by libgbgemm.so, as declared in include/gbgemm.h.
 EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
-    "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_get_device_status",
+    "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_sgemm_strided_batched",
+    "gbgemm_get_device_status",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
     "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
     "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run", "gbgemm_grouped_plan_configs",
@@ -97,6 +98,8 @@ def lib():
             L.gbgemm_split_workspace_bytes.argtypes = [i64, i64, i64]
             L.gbgemm_split_workspace_bytes.restype = ctypes.c_size_t
             L.gbgemm_sgemm.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64]
+            L.gbgemm_sgemm_strided_batched.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32,
+                                                       vp, i64, i64, i64]
             L.gbgemm_get_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.gbgemm_status_string.argtypes = [ctypes.c_int]
             L.gbgemm_status_string.restype = ctypes.c_char_p
@@ -137,6 +140,7 @@ def lib():
                                              ctypes.POINTER(i64)]
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
+                         "gbgemm_sgemm_strided_batched",
                          "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
                          "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
                          "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
@@ -223,6 +227,17 @@ class Handle:
                                 float(beta), _ptr(C), int(ldc))
         if check:
             _check("gbgemm_sgemm", rc)
+        return rc
+
+    def sgemm_strided_batched(self, transa, transb, m, n, k, alpha, A, lda, stride_a, B, ldb, stride_b, beta,
+                              C, ldc, stride_c, batch, check=True) -> int:
+        rc = lib().gbgemm_sgemm_strided_batched(
+            self._h, transa.encode() if isinstance(transa, str) else transa,
+            transb.encode() if isinstance(transb, str) else transb, int(m), int(n), int(k), float(alpha), _ptr(A),
+            int(lda), int(stride_a), _ptr(B), int(ldb), int(stride_b), float(beta), _ptr(C), int(ldc), int(stride_c),
+            int(batch))
+        if check:
+            _check("gbgemm_sgemm_strided_batched", rc)
         return rc
 
     def get_device_status(self) -> int:

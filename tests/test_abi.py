@@ -57,6 +57,35 @@ def test_argument_errors_in_blas_order(L):
         assert sg(None, bytes([ta]), b"n", 1, 1, 1, 1.0, a, 1, a, 1, 0.0, a, 1) == gbgemm.ERR_NOT_INITIALIZED
 
 
+def test_batched_argument_errors_in_order(L):
+    a = ctypes.c_void_p(16)  # never dereferenced: argument checks run first
+    sb = L.gbgemm_sgemm_strided_batched
+    def call(ta=b"N", tb=b"N", m=5, n=2, k=3, alpha=1.0, A=a, lda=5, sa=15, B=a, ldb=3, sbb=6, beta=0.0, C=a,
+             ldc=5, sc=10, batch=4):
+        return sb(None, ta, tb, m, n, k, alpha, A, lda, sa, B, ldb, sbb, beta, C, ldc, sc, batch)
+    assert call(ta=b"X") == -1
+    assert call(tb=b"q") == -2
+    assert call(m=-1) == -3
+    assert call(n=-1) == -4
+    assert call(k=-1) == -5
+    assert call(lda=4) == -8
+    assert call(sa=-1) == -9
+    assert call(ldb=2) == -11
+    assert call(sbb=-3) == -12
+    assert call(ldc=4) == -15
+    assert call(sc=-1) == -16
+    assert call(sc=9) == -16          # C_1 would overlap C_0 (needs ldc (n - 1) + m = 10)
+    assert call(batch=-1) == -17
+    assert call(batch=65536) == -17
+    assert call(A=None) == -7
+    assert call(B=None) == -10
+    assert call(C=None) == -14
+    # shared operands (stride 0) and one problem (any stride_c) are fine
+    assert call(sa=0, sbb=0) == gbgemm.ERR_NOT_INITIALIZED
+    assert call(sc=0, batch=1) == gbgemm.ERR_NOT_INITIALIZED
+    assert call(batch=0) == gbgemm.ERR_NOT_INITIALIZED
+
+
 def test_null_handle_and_status_strings(L):
     assert L.gbgemm_destroy(None) == gbgemm.ERR_NOT_INITIALIZED
     assert L.gbgemm_set_path(None, 0) == gbgemm.ERR_NOT_INITIALIZED
