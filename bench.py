@@ -517,7 +517,30 @@ def run_extras(h, stream, flop8192):
         "note": ("the paper's micro-kernel problem (Table I, 192 x 256 x 4096), 64 at once through "
                  "gbgemm_sgemm_strided_batched; single_calls = the same 64 problems as gbgemm_sgemm calls; "
                  "error ratio on problems 0 and 63 (FP64 on the GPU)")}
-    del Ab, Bb, Cb, flush
+    del Ab, Bb, Cb
+    # -- split-K: a small output with a long k (512 x 512 x 65536, NN, alpha 1,
+    #    beta 0): 4 tiles of 128 x 256 without slicing, sliced over the SMs --
+    ms_, ns_, ks_ = 512, 512, 65536
+    g.manual_seed(6)
+    As_ = torch.rand(ms_ * ks_, device="cuda", generator=g) * 2 - 1
+    Bs_ = torch.rand(ks_ * ns_, device="cuda", generator=g) * 2 - 1
+    Cs_ = torch.zeros(ms_ * ns_, device="cuda")
+    h.set_path(gbgemm.PATH_SPLIT_BF16)
+    run_k = lambda: h.sgemm("N", "N", ms_, ns_, ks_, 1.0, As_, ms_, Bs_, ks_, 0.0, Cs_, ms_)
+    med_k, min_k = _time_stats(run_k, stream, 10, flush)
+    h.profile_begin()
+    run_k()
+    torch.cuda.synchronize()
+    launches_k = h.profile_end()[2]
+    errk = h.check_error("N", "N", ms_, ns_, ks_, 1.0, As_, ms_, Bs_, ks_, 0.0, Cs_, Cs_, ms_)
+    flk = metrics.gemm_flops(ms_, ns_, ks_)
+    out["splitk_512x512x65536"] = {
+        "ms_median": med_k, "tflops": flk / (med_k * 1e-3) / 1e12, "tflops_best": flk / (min_k * 1e-3) / 1e12,
+        "kernels_per_call": launches_k, "max_error_ratio": errk,
+        "note": ("split path; the k range is cut into slices so that the 4-16 output tiles fill the SMs, "
+                 "and a reduction sums the slices in order (kernels_per_call 6 = 2 packing, 2 re-packing, "
+                 "GEMM, reduction); error ratio over the whole 512 x 512 result (FP64 on the GPU)")}
+    del As_, Bs_, Cs_, flush
     # -- grouped uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024] (seed 3) --
     shapes = synth.grouped_shapes(3, 4096)
     bufs, probs = [], []

@@ -205,6 +205,8 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   const int64_t half_sms = h->num_sms / 2;
   int simt_cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
   int split_bn = tiles(128, 256) >= half_sms ? 256 : tiles(128, 128) >= half_sms ? 128 : 64;
+  // a long k with few tiles is cut into k slices instead: keep the widest tile
+  if (batch == 1 && gbg::choose_splitk(tiles(128, 256), k, h->num_sms) > 1) split_bn = 256;
   if (h->tuning == 1 && batch == 1) {
     const gbgemm_problem q{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
     gbg::TuneResult r;
@@ -239,9 +241,14 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   const size_t xa = align_up((size_t)m * 4, 256);
   // workspace: per problem z, at z * block bytes:
   //   [panel A | panel B | maxima A | maxima B | (three parts) panel A2 | panel B2]
+  // Split-K (one problem, long k, too few tiles for the SMs): after the
+  // panels, splitk x tiles raw 128 x bn accumulators, summed by a reduction.
   const size_t block = gbgemm_split_workspace_bytes(m, n, k);
   if (block > ((size_t)1 << 62) / (size_t)batch) return GBGEMM_ERR_ALLOC;
-  int rc = ensure_workspace(h, block * (size_t)batch);
+  const int64_t tiles_mn = ((m + 127) / 128) * ((n + split_bn - 1) / split_bn);
+  const int splitk = batch == 1 ? gbg::choose_splitk(tiles_mn, k, h->num_sms) : 1;
+  const size_t partial_bytes = splitk > 1 ? (size_t)splitk * (size_t)tiles_mn * 128 * (size_t)split_bn * 4 : 0;
+  int rc = ensure_workspace(h, block * (size_t)batch + partial_bytes);
   if (rc != GBGEMM_OK) return rc;
   uint8_t* ws = static_cast<uint8_t*>(h->ws);
   void* panelA = ws;
@@ -268,11 +275,17 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   a.status = h->d_status; a.num_sms = h->num_sms;
   a.bn = split_bn; a.raster = 16;
   a.batch = batch; a.panel_stride = (int64_t)block; a.amax_stride = bw; a.c_stride = sc;
+  a.splitk = splitk;
+  a.partial = splitk > 1 ? reinterpret_cast<float*>(ws + block) : nullptr;
   h->kernel_launches += 4;  // two packing and two re-packing kernels
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (gbg::launch_split_gemm(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   h->kernel_launches += 1;
+  if (splitk > 1) {
+    if (gbg::launch_splitk_reduce(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    h->kernel_launches += 1;
+  }
   h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;
   return GBGEMM_OK;

@@ -67,6 +67,10 @@ struct TileJob {
   float* C;
   int64_t ldc;
   float alpha, beta;
+  // split-K: when set, the epilogue stores the raw 128 x bn accumulator here
+  // (element (row, col) at partial[col * 128 + row]) and a reduction kernel
+  // finishes C
+  float* partial;
 };
 
 // B rows [r0, r0 + bn) of a panel start inside 128-row block r0/128 at row
@@ -89,18 +93,28 @@ struct SingleSched {
   int64_t a_part, b_part;
   int batch;
   int64_t ps, as, cs;
-  __device__ __forceinline__ int num_items() const { return tiles_m * tiles_n * batch; }
+  // split-K (batch 1, two-part panels): item = (tile, slice), slice s covering
+  // k chunks [s * slice_chunks, min(nkc, (s + 1) * slice_chunks)); partials
+  // of slice s, tile (tm, tn) at partial + ((s * tiles_m + tm) * tiles_n + tn) * 128 * bn
+  int splitk, slice_chunks;
+  float* partial;
+  __device__ __forceinline__ int num_items() const { return tiles_m * tiles_n * batch * splitk; }
   __device__ __forceinline__ TileJob job(int t) const {
     const int per = tiles_m * tiles_n;
+    const int sl = t % splitk;
+    t /= splitk;
     const int z = t / per;
     int tm, tn;
     tile_coords(t - z * per, tiles_m, tiles_n, raster, tm, tn);
+    const int kc0 = sl * slice_chunks;
     TileJob j;
-    j.a_src = panelA + (size_t)z * ps + (size_t)tm * kBlockBytes;
-    j.b_src = panel_rows(panelB + (size_t)z * ps, (int64_t)tn * bn);
     j.a_kstride = (size_t)rbA * kBlockBytes;
     j.b_kstride = (size_t)rbB * kBlockBytes;
-    j.nkc = nkc; j.bn = bn;
+    j.a_src = panelA + (size_t)z * ps + (size_t)tm * kBlockBytes + (size_t)kc0 * j.a_kstride;
+    j.b_src = panel_rows(panelB + (size_t)z * ps, (int64_t)tn * bn) + (size_t)kc0 * j.b_kstride;
+    j.nkc = (nkc - kc0 < slice_chunks) ? nkc - kc0 : slice_chunks;
+    j.bn = bn;
+    j.partial = splitk > 1 ? partial + ((size_t)(sl * tiles_m + tm) * tiles_n + tn) * 128 * bn : nullptr;
     j.parts = parts; j.a_part = a_part; j.b_part = b_part;
     j.m0 = (int64_t)tm * 128; j.n0 = (int64_t)tn * bn;
     j.m = m; j.n = n;
@@ -144,6 +158,7 @@ struct GroupedSched {
     j.m = g.m; j.n = g.n;
     j.amaxA = g.amaxA; j.amaxB = g.amaxB;
     j.C = g.C; j.ldc = g.ldc; j.alpha = g.alpha; j.beta = g.beta;
+    j.partial = nullptr;
     return j;
   }
 };
@@ -331,7 +346,17 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       float* const crow = J.C + i;
       const int cols = (J.bn / (kEpiWarps / 4)) > 32 ? J.bn / (kEpiWarps / 4) : 32;
       const int c_begin = part * cols, c_end = (c_begin + cols < J.bn) ? c_begin + cols : J.bn;
-      for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+      if (J.partial) {
+        // split-K slice: the raw accumulator, whole tile, 32 consecutive rows per warp store
+        float* pp = J.partial + q * 32 + lane;
+        for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(taddr + (uint32_t)c0, r);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) __stcg(pp + (size_t)(c0 + jj) * 128, __uint_as_float(r[jj]));
+        }
+      }
+      for (int c0 = c_begin; c0 < c_end && !J.partial; c0 += 32) {
         if (J.n0 + c0 >= J.n) break;  // warp-uniform
         const int jmax = (J.n - (J.n0 + c0) < 32) ? (int)(J.n - (J.n0 + c0)) : 32;
         float* cp = crow + (J.n0 + c0) * J.ldc;

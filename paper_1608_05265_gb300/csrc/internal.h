@@ -80,8 +80,19 @@ struct SplitGemmArgs {
   // words, result at C + z*c_stride elements
   int64_t batch = 1;
   int64_t panel_stride = 0, amax_stride = 0, c_stride = 0;
+  // split-K (batch 1, split_parts(k) == 1): splitk > 1 slices of k, their raw
+  // accumulators in `partial` (splitk x tiles x 128 x bn floats), finished by
+  // launch_splitk_reduce
+  int splitk = 1;
+  float* partial = nullptr;
 };
+
+// Number of k slices for a single split-path call with `tiles` output tiles
+// (1 when the tiles already fill half of the SMs, or k is short).
+int choose_splitk(int64_t tiles, int64_t k, int num_sms);
+// C := alpha 2^(e_i + f_j) sum_s partial_s + beta C, slices summed in order.
 cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s);
+cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s);
 
 // FP64 error check of C_out against alpha op(A) op(B) + beta C_in over a
 // block (check.cu); synchronises s.

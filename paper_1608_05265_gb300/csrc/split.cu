@@ -56,7 +56,44 @@ __global__ void __launch_bounds__(256) rescale_kernel(int64_t rows, int64_t k, c
                 rows_alloc, nkc, blockIdx.x, se);
 }
 
+// Split-K reduction: thread per C element (i, j), the slices' raw
+// accumulators summed in slice order (deterministic), then the epilogue of
+// split_gemm_kernel: x 2^(e_i + f_j), alpha, and beta C with one rounding of
+// beta C and one fused multiply-add.
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t m, int64_t n, int bn, int tiles_m, int tiles_n,
+                                                            int splitk, const float* __restrict__ partial,
+                                                            const uint32_t* __restrict__ amaxA,
+                                                            const uint32_t* __restrict__ amaxB, float alpha,
+                                                            float beta, float* __restrict__ C, int64_t ldc) {
+  const int64_t total = m * n;
+  const size_t tile_elems = (size_t)128 * bn, slice_elems = (size_t)tiles_m * tiles_n * tile_elems;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % m, j = t / m;
+    const int64_t tm = i >> 7, tn = j / bn;
+    const float* p = partial + (size_t)(tm * tiles_n + tn) * tile_elems + (size_t)(j - tn * bn) * 128 + (i & 127);
+    float acc = 0.f;
+    for (int s = 0; s < splitk; ++s) acc += p[(size_t)s * slice_elems];
+    const int e = scale_exp_from_bits(amaxA[i]) + scale_exp_from_bits(amaxB[j]);
+    const float v = (e >= -126 && e <= 127) ? acc * __int_as_float((e + 127) << 23) : scalbnf(acc, e);
+    float* c = C + i + j * ldc;
+    *c = (beta != 0.f) ? fmaf(alpha, v, beta * *c) : alpha * v;
+  }
+}
+
 }  // namespace
+
+int choose_splitk(int64_t tiles, int64_t k, int num_sms) {
+  if (split_parts(k) != 1 || tiles <= 0 || tiles * 2 > num_sms) return 1;
+  int64_t s = num_sms / tiles;                    // about one item per SM
+  const int64_t max_by_k = panel_k_chunks(k) / 4; // at least 4 k chunks (128 deep) per slice
+  if (s > max_by_k) s = max_by_k;
+  if (s > 32) s = 32;
+  if (s < 2) return 1;
+  // every slice gets at least one chunk: ceil(nkc / ceil(nkc / s)) slices
+  const int64_t nkc = panel_k_chunks(k), per = (nkc + s - 1) / s;
+  s = (nkc + per - 1) / per;
+  return s >= 2 ? (int)s : 1;
+}
 
 cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
                               uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s) {
@@ -115,12 +152,30 @@ cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s) {
   S.b_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelB2) - S.panelB) : 0;
   S.batch = (int)batch;
   S.ps = a.panel_stride; S.as = a.amax_stride; S.cs = a.c_stride;
+  S.splitk = a.splitk > 1 ? a.splitk : 1;
+  if (S.splitk > 1 && (batch != 1 || S.parts != 1 || !a.partial)) return cudaErrorInvalidValue;
+  S.slice_chunks = (S.nkc + S.splitk - 1) / S.splitk;
+  // no empty slice (an empty slice would store a stale accumulator)
+  if ((int64_t)(S.splitk - 1) * S.slice_chunks >= S.nkc) return cudaErrorInvalidValue;
+  S.partial = a.partial;
   cudaError_t e = ensure_gemm_smem_attr<SingleSched>();
   if (e != cudaSuccess) return e;
-  const int64_t tiles = tm * tn * batch;
+  const int64_t tiles = tm * tn * batch * S.splitk;
   const int64_t sms = a.num_sms > 0 ? a.num_sms : 148;
   const int grid = (int)(tiles < sms ? tiles : sms);
   split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, a.status, kTimeoutNs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s) {
+  if (a.m <= 0 || a.n <= 0 || a.splitk <= 1) return cudaSuccess;
+  const int tm = (int)((a.m + 127) / 128), tn = (int)((a.n + a.bn - 1) / a.bn);
+  const int64_t total = a.m * a.n;
+  int64_t blocks = (total + 255) / 256;
+  const int64_t cap = (int64_t)(a.num_sms > 0 ? a.num_sms : 148) * 8;
+  if (blocks > cap) blocks = cap;
+  splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.m, a.n, a.bn, tm, tn, a.splitk, a.partial, a.amaxA,
+                                                         a.amaxB, a.alpha, a.beta, a.C, a.ldc);
   return cudaGetLastError();
 }
 

@@ -115,9 +115,10 @@ def test_batched_auto_path_and_degenerate(h):
 
 def test_batched_matches_single_calls(h):
     """A batch and the same problems called one by one agree bit for bit (the
-    same kernels, tile order and configuration)."""
+    same kernels and configuration; k < 512, where single calls are not cut
+    into k slices)."""
     import torch
-    m, n, k, batch = 256, 256, 512, 3
+    m, n, k, batch = 256, 256, 384, 3
     A, lda, sa, As, B, ldb, sb, Bs, C, ldc, sc, Cs = batch_data(13, "N", "N", m, n, k, batch)
     dA, dB, dC, dC1 = dev(A), dev(B), dev(C), dev(C)
     h.set_path(SPLIT)
