@@ -540,7 +540,22 @@ def run_extras(h, stream, flop8192):
         "note": ("split path; the k range is cut into slices so that the 4-16 output tiles fill the SMs, "
                  "and a reduction sums the slices in order (kernels_per_call 6 = 2 packing, 2 re-packing, "
                  "GEMM, reduction); error ratio over the whole 512 x 512 result (FP64 on the GPU)")}
-    del As_, Bs_, Cs_, flush
+    del As_, Bs_, Cs_
+    # -- sgemv (Level 2, HBM-bound): A 32768 x 32768 (4.3 GB), both transposes --
+    mv = 32768
+    g.manual_seed(7)
+    Av = torch.rand(mv * mv, device="cuda", generator=g) * 2 - 1
+    xv = torch.rand(mv, device="cuda", generator=g) * 2 - 1
+    yv = torch.rand(mv, device="cuda", generator=g) * 2 - 1
+    gv = {}
+    for tr in ("N", "T"):
+        med_v, min_v = _time_stats(lambda: h.sgemv(tr, mv, mv, 1.0, Av, mv, xv, 1, 0.0, yv, 1), stream, 10)
+        by = 4.0 * (mv * mv + 2 * mv)
+        gv[tr] = {"ms_median": med_v, "gbs": by / (med_v * 1e-3) / 1e9, "hbm_frac": by / (med_v * 1e-3) / 1e9 / hbm,
+                  "tflops": 2.0 * mv * mv / (med_v * 1e-3) / 1e12}
+    out["sgemv_32768"] = dict(gv, note=(f"bytes = 4 (m n + m + n); HBM peak {hbm:.0f} GB/s ({peak_src}); A (4.3 GB) "
+                                        "is larger than L2, so no flush; median of 10 calls"))
+    del Av, xv, yv, flush
     # -- grouped uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024] (seed 3) --
     shapes = synth.grouped_shapes(3, 4096)
     bufs, probs = [], []

@@ -143,6 +143,24 @@ int gbgemm_sgemm_strided_batched(gbgemm_handle* h, char transa, char transb, int
                                  int64_t ldb, int64_t stride_b, float beta, float* C, int64_t ldc, int64_t stride_c,
                                  int64_t batch);
 
+/* BLAS-convention sgemv, y := alpha op(A) x + beta y.  The paper's HPL run is
+ * limited by Level-2 BLAS on the host (Sections IV-C, V); this is the GPU
+ * counterpart, memory-bound (every element of A read once).
+ * trans: 'N','n' (op(A) = A, x of length n, y of length m) or 'T','t','C','c'
+ * (op(A) = A^T, x of length m, y of length n).  A: device, m x n, lda >=
+ * max(1, m).  x, y: device vectors with increments incx, incy != 0 (negative:
+ * the vector runs backwards from the end of its storage, as in BLAS).  y is
+ * read only when beta != 0.  Sums are formed in a fixed order (run-to-run
+ * deterministic); the summed dimension is cut into slices when the other one
+ * gives too few blocks, the slices' partial sums (in the handle's workspace)
+ * added in order.
+ * Argument errors, in this order: trans -1, m -2, n -3, lda -6, incx -8,
+ * incy -11; then null A (when read) -5, null x -7, null y (len(y) > 0) -10.
+ * Then GBGEMM_ERR_NOT_INITIALIZED for a NULL handle.  Queues kernels on the
+ * handle's stream. */
+int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+                 const float* x, int64_t incx, float beta, float* y, int64_t incy);
+
 /* Synchronise the handle's stream, then read and clear the device status
  * word: *status = 0 when no kernel reported a failure since the last read,
  * else the first failing kernel's code (GBGEMM_ERR_DEVICE_TIMEOUT).  Returns

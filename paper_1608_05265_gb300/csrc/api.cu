@@ -348,6 +348,39 @@ int gbgemm_sgemm_strided_batched(gbgemm_handle* h, char transa, char transb, int
                    stride_b, stride_c);
 }
 
+int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
+                 const float* x, int64_t incx, float beta, float* y, int64_t incy) {
+  const int t = trans_code(trans);
+  if (t < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (lda < (m > 1 ? m : 1)) return -6;
+  if (incx == 0) return -8;
+  if (incy == 0) return -11;
+  const int64_t len_x = t ? m : n, len_y = t ? n : m;
+  const bool use_ax = (alpha != 0.0f) && (len_x > 0);
+  if (len_y > 0) {
+    if (use_ax && !A) return -5;
+    if (use_ax && !x) return -7;
+    if (!y) return -10;
+  }
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (len_y == 0 || (!use_ax && beta == 1.0f)) return GBGEMM_OK;
+  DeviceGuard g(h->device);
+  const int64_t slices = use_ax ? gbg::gemv_slices(t == 1, m, n, h->num_sms) : 1;
+  float* partial = nullptr;
+  if (slices > 1) {
+    const int rc = ensure_workspace(h, (size_t)slices * (size_t)len_y * sizeof(float));
+    if (rc != GBGEMM_OK) return rc;
+    partial = static_cast<float*>(h->ws);
+  }
+  if (gbg::launch_gemv(t == 1, m, n, use_ax ? alpha : 0.0f, A, lda, x, incx, beta, y, incy, slices, partial,
+                       h->num_sms, h->stream) != cudaSuccess)
+    return GBGEMM_ERR_CUDA;
+  h->kernel_launches += slices > 1 ? 2 : 1;
+  return GBGEMM_OK;
+}
+
 int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,
                       const float* X, int64_t ldx, uint32_t* amax_bits, void* panel, void* panel2) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;

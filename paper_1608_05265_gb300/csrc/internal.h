@@ -28,6 +28,12 @@ cudaError_t launch_simt_batched(const Problem& p, int config, int64_t batch, int
                                 cudaStream_t s);
 // C := beta * C over m x n (beta == 0 writes zeros without reading C).
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t s);
+// sgemv (gemv.cu): slices of the summed dimension for a launch (>= 1), and the
+// launch (partial: slices x len(y) floats when slices > 1).
+int64_t gemv_slices(bool trans, int64_t m, int64_t n, int num_sms);
+cudaError_t launch_gemv(bool trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda, const float* x,
+                        int64_t incx, float beta, float* y, int64_t incy, int64_t slices, float* partial,
+                        int num_sms, cudaStream_t s);
 cudaError_t launch_scale_c_batched(int64_t m, int64_t n, float beta, float* C, int64_t ldc, int64_t batch,
                                    int64_t sc, cudaStream_t s);
 

@@ -60,6 +60,7 @@ class Problem(ctypes.Structure):
 EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_sgemm_strided_batched",
+    "gbgemm_sgemv",
     "gbgemm_get_device_status",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
     "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
@@ -100,6 +101,7 @@ def lib():
             L.gbgemm_sgemm.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64]
             L.gbgemm_sgemm_strided_batched.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32,
                                                        vp, i64, i64, i64]
+            L.gbgemm_sgemv.argtypes = [vp, c, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64]
             L.gbgemm_get_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.gbgemm_status_string.argtypes = [ctypes.c_int]
             L.gbgemm_status_string.restype = ctypes.c_char_p
@@ -140,7 +142,7 @@ def lib():
                                              ctypes.POINTER(i64)]
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
-                         "gbgemm_sgemm_strided_batched",
+                         "gbgemm_sgemm_strided_batched", "gbgemm_sgemv",
                          "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
                          "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
                          "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
@@ -238,6 +240,13 @@ class Handle:
             int(batch))
         if check:
             _check("gbgemm_sgemm_strided_batched", rc)
+        return rc
+
+    def sgemv(self, trans, m, n, alpha, A, lda, x, incx, beta, y, incy, check=True) -> int:
+        rc = lib().gbgemm_sgemv(self._h, trans.encode() if isinstance(trans, str) else trans, int(m), int(n),
+                                float(alpha), _ptr(A), int(lda), _ptr(x), int(incx), float(beta), _ptr(y), int(incy))
+        if check:
+            _check("gbgemm_sgemv", rc)
         return rc
 
     def get_device_status(self) -> int:

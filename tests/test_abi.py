@@ -86,6 +86,26 @@ def test_batched_argument_errors_in_order(L):
     assert call(batch=0) == gbgemm.ERR_NOT_INITIALIZED
 
 
+def test_gemv_argument_errors_in_order(L):
+    a = ctypes.c_void_p(16)  # never dereferenced: argument checks run first
+    gv = L.gbgemm_sgemv
+    def call(t=b"N", m=5, n=3, alpha=1.0, A=a, lda=5, x=a, incx=1, beta=0.0, y=a, incy=1):
+        return gv(None, t, m, n, alpha, A, lda, x, incx, beta, y, incy)
+    assert call(t=b"Q") == -1
+    assert call(m=-1) == -2
+    assert call(n=-1) == -3
+    assert call(lda=4) == -6
+    assert call(incx=0) == -8
+    assert call(incy=0) == -11
+    assert call(A=None) == -5
+    assert call(x=None) == -7
+    assert call(y=None) == -10
+    assert call(alpha=0.0, A=None, x=None, beta=2.0) == gbgemm.ERR_NOT_INITIALIZED
+    assert call(incx=-2, incy=-1) == gbgemm.ERR_NOT_INITIALIZED
+    for t in b"NnTtCc":
+        assert call(t=bytes([t])) == gbgemm.ERR_NOT_INITIALIZED
+
+
 def test_null_handle_and_status_strings(L):
     assert L.gbgemm_destroy(None) == gbgemm.ERR_NOT_INITIALIZED
     assert L.gbgemm_set_path(None, 0) == gbgemm.ERR_NOT_INITIALIZED
