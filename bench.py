@@ -555,7 +555,48 @@ def run_extras(h, stream, flop8192):
                   "tflops": 2.0 * mv * mv / (med_v * 1e-3) / 1e12}
     out["sgemv_32768"] = dict(gv, note=(f"bytes = 4 (m n + m + n); HBM peak {hbm:.0f} GB/s ({peak_src}); A (4.3 GB) "
                                         "is larger than L2, so no flush; median of 10 calls"))
-    del Av, xv, yv, flush
+    del Av, xv, yv
+    # -- HPL-shaped LU (Section IV-C, Table VII: N = 4608 on the Parallella,
+    #    0.495 GFLOPS): sgetrf + sgetrs, uniform [-0.5, 0.5) matrix and right-hand
+    #    side (seed 8), default block width; rate = (2/3 N^3 + 2 N^2) / time;
+    #    HPL's scaled residual computed here in FP64 --
+    hpl = {}
+    for nh in (4608, 16384):
+        g.manual_seed(8)
+        A0h = torch.rand(nh * nh, device="cuda", generator=g) - 0.5
+        b0h = torch.rand(nh, device="cuda", generator=g) - 0.5
+        Ah, bh = A0h.clone(), b0h.clone()
+        piv = torch.empty(nh, dtype=torch.int32, device="cuda")
+        inf_ = torch.empty(1, dtype=torch.int32, device="cuda")
+        times = []
+        for it in range(4):
+            Ah.copy_(A0h)
+            bh.copy_(b0h)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            h.sgetrf(nh, Ah, nh, piv, inf_)
+            e1.record(stream)
+            h.sgetrs(nh, 1, Ah, nh, piv, bh, nh)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:  # the first call allocates the workspace
+                times.append((e0.elapsed_time(e2), e0.elapsed_time(e1)))
+        t_all = sorted(times)[len(times) // 2]
+        Ad = A0h.view(nh, nh).double().T  # column-major storage: A(i, j) = A0h[j * n + i]
+        xd, bd = bh.double(), b0h.double()
+        resid = ((Ad @ xd - bd).abs().max() /
+                 (2.0 ** -24 * (Ad.abs().sum(1).max() * xd.abs().max() + bd.abs().max()) * nh)).item()
+        flh = 2.0 / 3.0 * nh ** 3 + 2.0 * nh ** 2
+        hpl[str(nh)] = {"ms": t_all[0], "getrf_ms": t_all[1], "getrs_ms": t_all[0] - t_all[1],
+                        "tflops": flh / (t_all[0] * 1e-3) / 1e12, "info": int(inf_.item()),
+                        "scaled_residual": resid, "passed": resid < 16.0}
+        del A0h, b0h, Ah, bh, Ad, xd, bd
+    out["hpl_lu"] = dict(hpl, note=("sgetrf + sgetrs (FP32, partial pivoting, library sgemm for the trailing "
+                                    "updates), median of 3 calls after one warm-up; the paper's HPL run (N 4608, "
+                                    "NB 768, FP64 API over an FP32 gemm) took 131.81 s, 0.495 GFLOPS, residual "
+                                    "check passed at 16 with eps 2^-53; here eps = 2^-24"))
+    del flush
     # -- grouped uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024] (seed 3) --
     shapes = synth.grouped_shapes(3, 4096)
     bufs, probs = [], []

@@ -161,6 +161,55 @@ int gbgemm_sgemm_strided_batched(gbgemm_handle* h, char transa, char transb, int
 int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha, const float* A, int64_t lda,
                  const float* x, int64_t incx, float beta, float* y, int64_t incy);
 
+/* LU factorisation with partial pivoting, P A = L U, in FP32 (LAPACK sgetrf
+ * for a square matrix): the factorisation the paper's HPL run performs
+ * (Section IV-C, Table VII), right-looking and blocked by nb columns, with
+ * every trailing update A22 := A22 - L21 U12 done by this library's sgemm
+ * (the Linpack-shaped C := C - A B).
+ * A: device, n x n column-major, lda >= max(1, n), overwritten by the packed
+ * factors (L strictly below the diagonal with a unit diagonal implied, U on
+ * and above).  ipiv: device, n ints; ipiv[j] (1-based) is the row exchanged
+ * with row j at step j.  The pivot of column j is the row of largest |a_ij|
+ * on or below the diagonal, the first such row on ties.  info: device, one
+ * int, set to 0, then to j + 1 for the first exactly zero pivot U(j, j) (the
+ * factorisation still completes, as in LAPACK).  nb: block width, 1 ..
+ * GBGEMM_SGETRF_MAX_NB, or 0 for GBGEMM_SGETRF_DEFAULT_NB below n =
+ * GBGEMM_SGETRF_WIDE_N and GBGEMM_SGETRF_MAX_NB from there (the faster of the
+ * two at N 4608 and 16384 on GB300).  Each block of nb columns is factored as
+ * panels of at most 32 columns (narrower when the panel's rows outgrow the
+ * shared memory of a cluster of 8 thread blocks, which holds a panel for its
+ * whole factorisation), the exchanges and triangular solves of each panel
+ * applied across the block and the block columns updated with k = the panel
+ * width; after the block, the whole trailing matrix is updated with k = nb.  Columns are scaled by the
+ * pivot's reciprocal, as LAPACK's unblocked factorisation and HPL do, so
+ * |l_ij| <= 1 holds up to one rounding.
+ * Results are bit-identical from run to run.  Queues kernels on the
+ * handle's stream and returns without synchronising; the per-call tuner is
+ * not used for the trailing updates.
+ * Argument errors, in this order: n (< 0 or > INT_MAX) -1, null A (n > 0) -2,
+ * lda -3, null ipiv (n > 0) -4, null info -5, nb -6.  Then
+ * GBGEMM_ERR_NOT_INITIALIZED for a NULL handle, GBGEMM_ERR_ALLOC,
+ * GBGEMM_ERR_CUDA, or an error of the trailing sgemm. */
+#define GBGEMM_SGETRF_MAX_NB 128
+#define GBGEMM_SGETRF_DEFAULT_NB 32
+#define GBGEMM_SGETRF_WIDE_N 8192
+int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv, int* info, int nb);
+
+/* Solve A X = B with the factors of gbgemm_sgetrf (LAPACK sgetrs, no
+ * transpose): the row exchanges of ipiv in order, then forward substitution
+ * with unit L, then back substitution with U.  LU, ipiv: device, as
+ * gbgemm_sgetrf left them.  B: device, n x nrhs column-major, ldb >=
+ * max(1, n), overwritten by X.  The solves go by diagonal blocks of 256 rows
+ * (one thread block per right-hand side and block), the off-diagonal parts
+ * by this library's sgemv (nrhs 1) or sgemm, in the handle's workspace.
+ * Argument errors, in this order: n (< 0 or > INT_MAX) -1, nrhs (< 0 or >
+ * INT_MAX) -2, null LU (n > 0) -3, lda -4, null ipiv (n > 0) -5, null B
+ * (n, nrhs > 0) -6, ldb -7.  Then GBGEMM_ERR_NOT_INITIALIZED for a NULL
+ * handle, GBGEMM_ERR_CUDA, GBGEMM_ERR_ALLOC.  Queues kernels on the handle's
+ * stream. */
+int gbgemm_sgetrs(gbgemm_handle* h, int64_t n, int64_t nrhs, const float* LU, int64_t lda, const int* ipiv, float* B,
+                  int64_t ldb);
+
 /* Synchronise the handle's stream, then read and clear the device status
  * word: *status = 0 when no kernel reported a failure since the last read,
  * else the first failing kernel's code (GBGEMM_ERR_DEVICE_TIMEOUT).  Returns

@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbgemm.so")
 SOURCES = ["api.cu", "simt.cu", "split.cu", "noalloc.cu", "grouped.cu", "tuner.cu", "mlp.cu", "check.cu",
-           "gemv.cu"]
+           "gemv.cu", "lu.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("internal.h", "split_device.cuh", "simt_device.cuh", "gemm_kernel.cuh",
                                             "grouped.h", "tuner.h", "mlp.h")] + \
     [os.path.join(ROOT, "include", "gbgemm.h")]

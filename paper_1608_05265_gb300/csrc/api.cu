@@ -4,6 +4,7 @@
 // micro-kernel).  One handle holds the per-device state the paper keeps in
 // its long-lived service process (Section III-B): device properties, the
 // stream and a persistent workspace, set up once instead of on every call.
+#include <climits>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -26,6 +27,7 @@ struct gbgemm_handle {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* d_status = nullptr;
+  int* d_lu_perm = nullptr;  // row permutation of the current LU panel
   // profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
@@ -133,6 +135,7 @@ int gbgemm_create(gbgemm_handle** out, int device) {
   if (cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess) {
     cudaGetLastError();
     if (h->d_status) cudaFree(h->d_status);
+  if (h->d_lu_perm) cudaFree(h->d_lu_perm);
     delete h;
     return GBGEMM_ERR_ALLOC;
   }
@@ -379,6 +382,129 @@ int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha
     return GBGEMM_ERR_CUDA;
   h->kernel_launches += slices > 1 ? 2 : 1;
   return GBGEMM_OK;
+}
+
+int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv, int* info, int nb) {
+  if (n < 0 || n > INT_MAX) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < (n > 1 ? n : 1)) return -3;
+  if (n > 0 && !ipiv) return -4;
+  if (!info) return -5;
+  if (nb < 0 || nb > gbg::kLuMaxNb) return -6;
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  DeviceGuard g(h->device);
+  if (cudaMemsetAsync(info, 0, sizeof(int), h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  h->last_path = 0;
+  if (n == 0) return GBGEMM_OK;
+  if (!h->d_lu_perm && cudaMalloc(&h->d_lu_perm, gbg::kLuPermInts * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    h->d_lu_perm = nullptr;
+    return GBGEMM_ERR_ALLOC;
+  }
+  const int b = nb > 0 ? nb : (n < GBGEMM_SGETRF_WIDE_N ? GBGEMM_SGETRF_DEFAULT_NB : GBGEMM_SGETRF_MAX_NB);
+  // The trailing updates run with the handle's path choice but never through
+  // the per-call tuner (each update has a new shape).
+  const int tuning = h->tuning;
+  h->tuning = 0;
+  int rc = GBGEMM_OK;
+  auto update = [&](int64_t r, int64_t c, int64_t rows, int64_t cols, int64_t k) {
+    // A(r:r+rows, c:c+cols) -= A(r:r+rows, c-k:c) A(c-k:c, c:c+cols)
+    return run_sgemm(h, 0, 0, 'N', 'N', rows, cols, k, -1.0f, A + r + (c - k) * lda, lda, A + (r - k) + c * lda, lda,
+                     1.0f, A + r + c * lda, lda, 1, 0, 0, 0);
+  };
+  int* perm = h->d_lu_perm;
+  for (int64_t j0 = 0; j0 < n && rc == GBGEMM_OK; j0 += b) {
+    const int nbo = (int)(n - j0 < b ? n - j0 : b);
+    // panels as wide as 32 columns while the panel rows fit the cluster's shared memory
+    const int fit = gbg::lu_panel_width((int)(n - j0));
+    const int pw = b < fit ? b : fit;
+    // the block [j0, j0 + nbo) as panels of pw columns, each followed by the
+    // exchanges and triangular solve over the rest of the block and the
+    // update of the block columns right of it
+    for (int64_t j1 = j0; j1 < j0 + nbo && rc == GBGEMM_OK; j1 += pw) {
+      const int w = (int)(j0 + nbo - j1 < pw ? j0 + nbo - j1 : pw);
+      if (gbg::launch_lu_panel((int)n, A, lda, (int)j1, w, ipiv, info, perm, h->stream) != cudaSuccess) {
+        rc = GBGEMM_ERR_CUDA;
+        break;
+      }
+      h->kernel_launches += 1;
+      if (w == nbo) break;
+      if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j1, w, perm, (int)j0, (int)(j0 + nbo), h->stream) !=
+          cudaSuccess) {
+        rc = GBGEMM_ERR_CUDA;
+        break;
+      }
+      h->kernel_launches += 1;
+      const int64_t cols = j0 + nbo - j1 - w;
+      if (cols > 0) rc = update(j1 + w, j1 + w, n - j1 - w, cols, w);
+    }
+    if (rc != GBGEMM_OK) break;
+    if (nbo > pw) {  // the block's exchanges as one permutation
+      if (gbg::launch_lu_perm((int)j0, nbo, ipiv, perm, h->stream) != cudaSuccess) {
+        rc = GBGEMM_ERR_CUDA;
+        break;
+      }
+      h->kernel_launches += 1;
+    }
+    if (j0 > 0 || j0 + nbo < n) {
+      if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j0, nbo, perm, 0, (int)n, h->stream) != cudaSuccess) {
+        rc = GBGEMM_ERR_CUDA;
+        break;
+      }
+      h->kernel_launches += 1;
+    }
+    const int64_t rest = n - j0 - nbo;
+    if (rest > 0) rc = update(j0 + nbo, j0 + nbo, rest, rest, nbo);
+  }
+  h->tuning = tuning;
+  return rc;
+}
+
+int gbgemm_sgetrs(gbgemm_handle* h, int64_t n, int64_t nrhs, const float* LU, int64_t lda, const int* ipiv, float* B,
+                  int64_t ldb) {
+  if (n < 0 || n > INT_MAX) return -1;
+  if (nrhs < 0 || nrhs > INT_MAX) return -2;
+  if (n > 0 && !LU) return -3;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (n > 0 && !ipiv) return -5;
+  if (n > 0 && nrhs > 0 && !B) return -6;
+  if (ldb < (n > 1 ? n : 1)) return -7;
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (n == 0 || nrhs == 0) return GBGEMM_OK;
+  DeviceGuard g(h->device);
+  if (gbg::launch_lu_laswp_rhs((int)n, nrhs, ipiv, B, ldb, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  h->kernel_launches += 1;
+  // B(r:r+rows, :) -= LU(r:r+rows, c:c+w) B(c:c+w, :): gemv for one
+  // right-hand side, gemm for several (never through the per-call tuner)
+  const int tuning = h->tuning;
+  h->tuning = 0;
+  auto update = [&](int64_t r, int64_t rows, int64_t c, int64_t w) {
+    if (nrhs == 1) return gbgemm_sgemv(h, 'N', rows, w, -1.0f, LU + r + c * lda, lda, B + c, 1, 1.0f, B + r, 1);
+    return run_sgemm(h, 0, 0, 'N', 'N', rows, nrhs, w, -1.0f, LU + r + c * lda, lda, B + c, ldb, 1.0f, B + r, ldb,
+                     1, 0, 0, 0);
+  };
+  const int nbs = gbg::kSolveBlock;
+  int rc = GBGEMM_OK;
+  for (int64_t j0 = 0; j0 < n && rc == GBGEMM_OK; j0 += nbs) {  // L y = P b, top down
+    const int w = (int)(n - j0 < nbs ? n - j0 : nbs);
+    if (gbg::launch_lu_trsv_block(false, LU, lda, (int)j0, w, nrhs, B, ldb, h->stream) != cudaSuccess) {
+      rc = GBGEMM_ERR_CUDA;
+      break;
+    }
+    h->kernel_launches += 1;
+    if (j0 + w < n) rc = update(j0 + w, n - j0 - w, j0, w);
+  }
+  for (int64_t j0 = (n - 1) / nbs * nbs; j0 >= 0 && rc == GBGEMM_OK; j0 -= nbs) {  // U x = y, bottom up
+    const int w = (int)(n - j0 < nbs ? n - j0 : nbs);
+    if (gbg::launch_lu_trsv_block(true, LU, lda, (int)j0, w, nrhs, B, ldb, h->stream) != cudaSuccess) {
+      rc = GBGEMM_ERR_CUDA;
+      break;
+    }
+    h->kernel_launches += 1;
+    if (j0 > 0) rc = update(0, j0, j0, w);
+  }
+  h->tuning = tuning;
+  return rc;
 }
 
 int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, int64_t k,

@@ -150,7 +150,7 @@ int64_t gemv_slices(bool trans, int64_t m, int64_t n, int num_sms) {
   if (!trans) {
     const int64_t rb = ceil_div(m, kGemvThreads);
     int64_t s = ceil_div(want, rb);
-    const int64_t cap = ceil_div(n, 256);  // at least 256 columns a slice
+    const int64_t cap = ceil_div(n, 32);  // at least 32 columns a slice
     if (s > cap) s = cap;
     if (s > 65535) s = 65535;
     return s < 1 ? 1 : s;

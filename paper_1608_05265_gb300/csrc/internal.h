@@ -37,6 +37,37 @@ cudaError_t launch_gemv(bool trans, int64_t m, int64_t n, float alpha, const flo
 cudaError_t launch_scale_c_batched(int64_t m, int64_t n, float beta, float* C, int64_t ldc, int64_t batch,
                                    int64_t sc, cudaStream_t s);
 
+// ---- LU factorisation (lu.cu) ----
+constexpr int kLuMaxNb = GBGEMM_SGETRF_MAX_NB;  // widest panel
+constexpr int kLuSolveSmemN = 32768; // the row exchanges of the solve run in shared memory up to this n
+constexpr int kLuPermInts = 1 + 3 * kLuMaxNb;  // a block's row permutation
+constexpr int kLuPanelNb = 32;      // columns per panel inside a block
+// Factor the panel rows [j0, n) x columns [j0, j0 + nbp) in place (a
+// cluster of up to kLuPanelCluster blocks holding the panel in shared
+// memory), writing ipiv[j0 ..) (1-based), the first zero pivot into *info
+// (when *info is 0) and the panel's row permutation into perm.  nbp must not
+// exceed lu_panel_width(n - j0), the widest panel whose rows fit.
+constexpr int kLuPanelCluster = 8;
+constexpr int kLuPanelSlabBytes = 192 * 1024;
+int lu_panel_width(int rows);
+cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,
+                            cudaStream_t s);
+// The permutation of pivot rows [j0, j0 + nbp), rebuilt from ipiv (for a
+// block factored as several panels).
+cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStream_t s);
+// The permutation of pivot rows [j0, j0 + nbp) applied to columns [c_lo, j0)
+// and [j0 + nbp, c_hi), then U12 = L11^-1 A12 for the latter.
+cudaError_t launch_lu_swap_trsm(int n, float* A, int64_t lda, int j0, int nbp, const int* perm, int c_lo, int c_hi,
+                                cudaStream_t s);
+// The solve with the packed factors: the row exchanges of ipiv on each of
+// nrhs columns of B, then per diagonal block of kSolveBlock rows the
+// triangular solve of that block (UPPER: back substitution with U, else
+// forward with unit L); the off-diagonal updates are gemv/gemm calls.
+constexpr int kSolveBlock = 256;
+cudaError_t launch_lu_laswp_rhs(int n, int64_t nrhs, const int* ipiv, float* B, int64_t ldb, cudaStream_t s);
+cudaError_t launch_lu_trsv_block(bool upper, const float* LU, int64_t lda, int j0, int w, int64_t nrhs, float* B,
+                                 int64_t ldb, cudaStream_t s);
+
 // ---- split path (split.cu) ----
 constexpr int kPanelRows = 128;     // rows per panel block
 constexpr int kPanelK = 32;         // k per panel block (hi and lo: 64 BF16 = 128 bytes per row)

@@ -1,0 +1,529 @@
+// FP32 LU factorisation with partial pivoting, and the solve that follows it:
+// the HPL run of the paper (Section IV-C, Table VII) on one GPU, with the
+// library's own sgemm doing the trailing updates (the Linpack-shaped
+// C := C - A B of the benchmark).
+//
+// Right-looking, blocked by nb columns.  For each block column j0:
+//   panel    rows [j0, n) x columns [j0, j0 + nb), factored by one
+//            1024-thread block in inner blocks of 8 columns.  An inner block
+//            is staged in shared memory when its rows fit (8 x 6144 floats),
+//            else worked on in place.  Per column: the pivot is the first row
+//            of largest |a| (block argmax, smallest row on ties, fused into
+//            the previous column's update pass), the two rows are exchanged
+//            within the inner block, the column is divided by the pivot and
+//            the rest of the inner block updated.  After each inner block its
+//            row exchanges are applied to the other panel columns as one
+//            gather, then the rest of the panel gets an 8-row triangular
+//            solve and a rank-8 update.  At the end the panel's exchanges are
+//            written out as a row permutation of the rows they touch.
+//   swap+U12 every column outside the panel gets the permutation (one
+//            gather per column: all sources read before any row is written);
+//            right of the panel, U12 = L11^-1 A12 follows in shared memory.
+//   update   A22 := A22 - L21 U12 by gbgemm's sgemm.
+// The row exchanges of earlier panels reach the left columns at the same
+// time as the right ones, so the result is LAPACK's packed P A = L U.  Every
+// sum is formed in a fixed order: runs are bit-identical.
+#include <cfloat>
+#include <climits>
+
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace gbg {
+namespace {
+
+constexpr int kPanelThreads = 512;
+constexpr int kTrsmCols = 128;    // columns per block of the swap + triangular solve kernel
+constexpr int kXP = kTrsmCols + 1;
+
+struct MaxLoc {
+  float v;
+  int i;
+};
+
+__device__ __forceinline__ void maxloc_merge(float& v, int& i, float v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+// Largest v over the block (smallest i on ties), returned to every thread.
+// Callers alternate between two `red` buffers, so no closing barrier is needed.
+__device__ MaxLoc block_argmax(float v, int i, MaxLoc* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxloc_merge(v, i, __shfl_xor_sync(0xFFFFFFFFu, v, o), __shfl_xor_sync(0xFFFFFFFFu, i, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = MaxLoc{v, i};
+  __syncthreads();
+  if (warp == 0) {
+    MaxLoc m = lane < (int)(blockDim.x >> 5) ? red[lane] : MaxLoc{-1.f, INT_MAX};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      maxloc_merge(m.v, m.i, __shfl_xor_sync(0xFFFFFFFFu, m.v, o), __shfl_xor_sync(0xFFFFFFFFu, m.i, o));
+    if (lane == 0) red[32] = m;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// The exchanges of pivot rows [j0, j0 + nbp) (row j0 + q with piv[q],
+// 0-based, q ascending) as a permutation of the rows they touch: slot s holds
+// row prow[s] and receives the original row pcont[s].  Slots 0 .. nbp-1 are
+// rows j0 ..; rows below that an exchange touches get slots after them.  Run
+// by one full warp, serial in q.  Writes perm = [extras, source row of row
+// j0 + q (nbp), (row, source) per extra].
+__device__ void build_perm(int j0, int nbp, const int* piv, int* prow, int* pcont, int* __restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  for (int s = lane; s < nbp; s += 32) prow[s] = pcont[s] = j0 + s;
+  __syncwarp();
+  int next = nbp;
+  for (int q = 0; q < nbp; ++q) {
+    const int p = piv[q];
+    if (p == j0 + q) continue;
+    int slot = -1;
+    if (p < j0 + nbp) {
+      slot = p - j0;
+    } else {
+      for (int base = nbp; base < next && slot < 0; base += 32) {
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, base + lane < next && prow[base + lane] == p);
+        if (hit) slot = base + __ffs(hit) - 1;
+      }
+      if (slot < 0) {
+        slot = next++;
+        if (lane == 0) prow[slot] = pcont[slot] = p;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const int t = pcont[q];
+      pcont[q] = pcont[slot];
+      pcont[slot] = t;
+    }
+    __syncwarp();
+  }
+  for (int s = lane; s < nbp; s += 32) perm[1 + s] = pcont[s];
+  for (int s = nbp + lane; s < next; s += 32) {
+    perm[1 + nbp + 2 * (s - nbp)] = prow[s];
+    perm[2 + nbp + 2 * (s - nbp)] = pcont[s];
+  }
+  if (lane == 0) perm[0] = next - nbp;
+}
+
+// The permutation of pivot rows [j0, j0 + nbp) from ipiv (one warp).
+__global__ void lu_perm_kernel(int j0, int nbp, const int* __restrict__ ipiv, int* __restrict__ perm) {
+  __shared__ int piv[kLuMaxNb];
+  __shared__ int prow[2 * kLuMaxNb], pcont[2 * kLuMaxNb];
+  for (int q = threadIdx.x; q < nbp; q += 32) piv[q] = ipiv[j0 + q] - 1;
+  __syncwarp();
+  build_perm(j0, nbp, piv, prow, pcont, perm);
+}
+
+// Panel rows [j0, n) x columns [j0, j0 + nbp) (nbp <= 32), resident in the
+// shared memory of a cluster of C blocks for the whole factorisation: block c
+// holds panel rows [c RS, c RS + RS) (counted from j0), row-major, row rr at
+// Sp + rr * pitch (lu_slab_pitch: rows of 16-byte multiples whose quarter
+// warps touch distinct banks).  Per column q, one cluster barrier:
+//   every block finds its candidate (largest |a| in column q among its rows
+//   below q, the first such row on ties; tracked during the previous
+//   column's update) and publishes it, the candidate's row and, from the
+//   block holding it, row q;
+//   after the barrier every block reads, in one round, all C candidates,
+//   their rows and row q, and reduces the candidates in the same order to
+//   the pivot row p.  The block holding q writes the pivot row there; the
+//   thread holding row p writes row q's values into it while it updates it;
+//   every block scales its rows below q by the pivot's reciprocal (as
+//   LAPACK's unblocked factorisation and HPL scale; by the pivot itself when
+//   the reciprocal would overflow) and updates the rest of them: a row's
+//   values are loaded as float4 before any is stored, and the pivot row is
+//   held in registers, zero up to column q + 1.
+// Published values are double-buffered by the parity of q: a buffer is
+// rewritten two columns later, after a barrier every reader has passed.
+__global__ void __launch_bounds__(kPanelThreads, 1)
+    lu_panel_kernel(int n, float* __restrict__ A, int64_t lda, int j0, int nbp, int RS, int pitch,
+                    int* __restrict__ ipiv, int* __restrict__ info, int* __restrict__ perm) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int c = (int)cl.block_rank();
+  extern __shared__ float4 Sp4[];
+  float* Sp = reinterpret_cast<float*>(Sp4);
+  __shared__ MaxLoc red[2][33];
+  __shared__ MaxLoc pub_cand[2];
+  __shared__ __align__(16) float pub_row[2][kLuPanelNb];  // the candidate's row
+  __shared__ __align__(16) float pub_q[2][kLuPanelNb];    // row q, from the block holding it
+  __shared__ MaxLoc cand_all[kLuPanelCluster];
+  __shared__ __align__(16) float rows_all[kLuPanelCluster][kLuPanelNb];
+  __shared__ __align__(16) float qrow[kLuPanelNb];
+  __shared__ int piv_s[kLuPanelNb];
+  __shared__ int prow_s[2 * kLuPanelNb], pcont_s[2 * kLuPanelNb];
+  const int tid = threadIdx.x;
+  const int R = n - j0;
+  const int rlo = c * RS;
+  const int nr = max(0, min(R, rlo + RS) - rlo);  // rows of this block's slab
+  const bool vec = nbp > 2;                       // rows in float4 groups
+  const int groups = (nbp + 3) / 4;
+  float* G = A + j0 + (int64_t)j0 * lda;
+  for (int q = 0; q < nbp; ++q) {
+#pragma unroll 4
+    for (int rr = tid; rr < nr; rr += kPanelThreads) Sp[rr * pitch + q] = G[(rlo + rr) + (int64_t)q * lda];
+  }
+  __syncthreads();
+  float best = -1.f;
+  int bi = INT_MAX;  // candidate as a panel row
+  for (int rr = tid; rr < nr; rr += kPanelThreads) {
+    const float v = fabsf(Sp[rr * pitch]);
+    if (v > best) { best = v; bi = rlo + rr; }  // rows ascend: the first maximum stays
+  }
+  for (int q = 0; q < nbp; ++q) {
+    const int par = q & 1;
+    const MaxLoc m = block_argmax(best, bi, red[par]);
+    if (tid == 0) pub_cand[par] = m;
+    if (tid < nbp) {
+      if (m.i != INT_MAX) pub_row[par][tid] = Sp[(m.i - rlo) * pitch + tid];
+      if (q >= rlo && q < rlo + nr) pub_q[par][tid] = Sp[(q - rlo) * pitch + tid];
+    }
+    cl.sync();
+    const int oq = q / RS;  // the block holding row q
+    // one round of remote reads: every candidate, every candidate's row, row q
+    for (int e = tid; e < C * kLuPanelNb + C + kLuPanelNb; e += kPanelThreads) {
+      if (e < C * kLuPanelNb) {
+        const int r = e / kLuPanelNb, col = e % kLuPanelNb;
+        if (col < nbp) rows_all[r][col] = *cl.map_shared_rank(&pub_row[par][col], r);
+      } else if (e < C * kLuPanelNb + C) {
+        cand_all[e - C * kLuPanelNb] = *cl.map_shared_rank(&pub_cand[par], e - C * kLuPanelNb);
+      } else {
+        const int col = e - C * kLuPanelNb - C;
+        if (col < nbp) qrow[col] = *cl.map_shared_rank(&pub_q[par][col], oq);
+      }
+    }
+    __syncthreads();
+    MaxLoc w{-1.f, INT_MAX};
+    int wr = 0;
+    for (int r = 0; r < C; ++r) {  // the same order in every block: the same pivot
+      const MaxLoc x = cand_all[r];
+      if (x.v > w.v || (x.v == w.v && x.i < w.i)) { w = x; wr = r; }
+    }
+    const int p = (w.i == INT_MAX) ? q : w.i;  // (a column of NaNs keeps its row)
+    const float* prow = (w.i == INT_MAX) ? qrow : rows_all[wr];
+    if (c == 0 && tid == 0) {
+      ipiv[j0 + q] = j0 + p + 1;
+      piv_s[q] = j0 + p;
+    }
+    // row q <- the pivot row (in the block holding q); row p <- row q (in the
+    // update below, by the thread holding row p)
+    if (p != q && c == oq && tid < nbp) Sp[(q - rlo) * pitch + tid] = prow[tid];
+    const float d = prow[q];
+    best = -1.f;
+    bi = INT_MAX;
+    const int rs = max(q + 1 - rlo, 0);  // this block's first row below q
+    if (d == 0.f) {
+      if (c == 0 && tid == 0 && *info == 0) *info = j0 + q + 1;  // the first exactly zero pivot, 1-based
+      if (p != q && p >= rlo && p < rlo + nr && tid < nbp) Sp[(p - rlo) * pitch + tid] = qrow[tid];
+      __syncthreads();
+      if (q + 1 < nbp)
+        for (int rr = rs + tid; rr < nr; rr += kPanelThreads) {
+          const float v = fabsf(Sp[rr * pitch + q + 1]);
+          if (v > best) { best = v; bi = rlo + rr; }
+        }
+    } else {
+      const bool use_rcp = fabsf(d) >= FLT_MIN;  // 1 / d is finite
+      const float rcp = 1.0f / d;
+      float4 u[kLuPanelNb / 4];  // the pivot row, zero up to column q + 1
+#pragma unroll
+      for (int j = 0; j < kLuPanelNb / 4; ++j) {
+        float t[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 4 * j + e;
+          t[e] = (k > q + 1 && k < nbp) ? prow[k] : 0.f;
+        }
+        u[j] = make_float4(t[0], t[1], t[2], t[3]);
+      }
+      const float p1 = q + 1 < nbp ? prow[q + 1] : 0.f;
+      for (int rr = rs + tid; rr < nr; rr += kPanelThreads) {
+        const bool isp = rlo + rr == p;  // this row receives row q
+        float* row = Sp + rr * pitch;
+        const float* src = isp ? qrow : row;  // the row's values before the update
+        const float a = src[q];
+        const float l = use_rcp ? a * rcp : a / d;
+        const float v1 = q + 1 < nbp ? fmaf(-l, p1, src[q + 1]) : 0.f;
+        if (vec) {
+          float4 x[kLuPanelNb / 4];
+#pragma unroll
+          for (int j = 0; j < kLuPanelNb / 4; ++j)
+            if (j < groups) x[j] = reinterpret_cast<const float4*>(src)[j];
+#pragma unroll
+          for (int j = 0; j < kLuPanelNb / 4; ++j) {
+            // groups holding a column beyond q + 1 are updated; row p takes
+            // every group (row q's values)
+            if (j < groups && (isp || 4 * j + 3 > q + 1)) {
+              x[j].x = fmaf(-l, u[j].x, x[j].x);
+              x[j].y = fmaf(-l, u[j].y, x[j].y);
+              x[j].z = fmaf(-l, u[j].z, x[j].z);
+              x[j].w = fmaf(-l, u[j].w, x[j].w);
+              if (!isp && 4 * j <= q + 1) {  // keep columns <= q + 1 exactly as they were
+                const float4 o = reinterpret_cast<const float4*>(src)[j];
+                if (4 * j + 0 <= q + 1) x[j].x = o.x;
+                if (4 * j + 1 <= q + 1) x[j].y = o.y;
+                if (4 * j + 2 <= q + 1) x[j].z = o.z;
+              }
+              reinterpret_cast<float4*>(row)[j] = x[j];
+            }
+          }
+        } else if (isp) {
+          for (int k = 0; k < nbp; ++k) row[k] = qrow[k];
+        }
+        row[q] = l;
+        if (q + 1 < nbp) {  // the next column: its largest |a| is the next candidate
+          row[q + 1] = v1;
+          if (fabsf(v1) > best) { best = fabsf(v1); bi = rlo + rr; }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < nbp; ++q)
+    for (int rr = tid; rr < nr; rr += kPanelThreads) G[(rlo + rr) + (int64_t)q * lda] = Sp[rr * pitch + q];
+  if (c == 0 && tid < 32) build_perm(j0, nbp, piv_s, prow_s, pcont_s, perm);
+  cl.sync();  // no block leaves while another may still read its published values
+}
+
+// Columns [c_lo, j0) and [j0 + nbp, c_hi): apply the row permutation of
+// pivot rows [j0, j0 + nbp) (all sources read before any row is written);
+// right of them, then U12 = L11^-1 A12, one thread per column, L11 and the
+// block's columns staged in shared memory.  Blocks [0, left_tiles) cover the
+// left range.
+__global__ void __launch_bounds__(kTrsmCols) lu_swap_trsm_kernel(int n, float* __restrict__ A, int64_t lda, int j0,
+                                                                 int nbp, const int* __restrict__ perm, int c_lo,
+                                                                 int c_hi, int left_tiles) {
+  extern __shared__ float sm[];
+  const int next = perm[0];
+  const int* src = perm + 1;
+  const int* ext = perm + 1 + nbp;
+  float* V = sm;                   // permuted panel rows: V[q * kXP + col]
+  float* W = V + nbp * kXP;        // extra rows: W[x * kXP + col]
+  float* Ls = W + nbp * kXP;       // L11: Ls[i * (nbp + 1) + p]
+  const bool left = (int)blockIdx.x < left_tiles;
+  const int c0 = left ? c_lo + (int)blockIdx.x * kTrsmCols : j0 + nbp + ((int)blockIdx.x - left_tiles) * kTrsmCols;
+  const int cend = left ? min(c0 + kTrsmCols, j0) : min(c0 + kTrsmCols, c_hi);
+  const int ncol = cend - c0;
+  const int tid = threadIdx.x;
+#pragma unroll 8
+  for (int e = tid; e < nbp * ncol; e += kTrsmCols) {  // eight loads in flight per thread
+    const int q = e % nbp, col = e / nbp;
+    V[q * kXP + col] = A[src[q] + (int64_t)(c0 + col) * lda];
+  }
+#pragma unroll 8
+  for (int e = tid; e < next * ncol; e += kTrsmCols) {
+    const int x = e % next, col = e / next;
+    W[x * kXP + col] = A[ext[2 * x + 1] + (int64_t)(c0 + col) * lda];
+  }
+  if (!left)
+#pragma unroll 8
+    for (int e = tid; e < nbp * nbp; e += kTrsmCols) {
+      const int i = e % nbp, p = e / nbp;
+      Ls[i * (nbp + 1) + p] = A[(j0 + i) + (int64_t)(j0 + p) * lda];
+    }
+  __syncthreads();
+  for (int e = tid; e < next * ncol; e += kTrsmCols) {
+    const int x = e % next, col = e / next;
+    A[ext[2 * x] + (int64_t)(c0 + col) * lda] = W[x * kXP + col];
+  }
+  if (!left && tid < ncol) {
+    for (int i = 1; i < nbp; ++i) {
+      float s = V[i * kXP + tid];
+      for (int p = 0; p < i; ++p) s = fmaf(-Ls[i * (nbp + 1) + p], V[p * kXP + tid], s);
+      V[i * kXP + tid] = s;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nbp * ncol; e += kTrsmCols) {
+    const int q = e % nbp, col = e / nbp;
+    A[(j0 + q) + (int64_t)(c0 + col) * lda] = V[q * kXP + col];
+  }
+}
+
+// The row exchanges of ipiv applied to one right-hand side per block, in
+// order, the column staged in shared memory when SMEM.  An entry out of range
+// is skipped, never followed.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) lu_laswp_rhs_kernel(int n, const int* __restrict__ ipiv, float* __restrict__ B,
+                                                           int64_t ldb) {
+  extern __shared__ float ys[];
+  float* b = B + (int64_t)blockIdx.x * ldb;
+  float* y = SMEM ? ys : b;
+  if (SMEM) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = b[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < n; ++j) {
+      const int p = ipiv[j] - 1;
+      if (p != j && p >= 0 && p < n) {
+        const float t = y[j];
+        y[j] = y[p];
+        y[p] = t;
+      }
+    }
+  if (SMEM) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = ys[i];
+  }
+}
+
+// One diagonal block of the triangular solves, rows [j0, j0 + w) (w <= 256)
+// of one right-hand side per block: forward substitution with the unit lower
+// triangle (UPPER false) or back substitution with the upper one (UPPER true),
+// in steps of 32 rows, each 32 x 32 triangle solved by one warp from
+// registers and the rest of the block updated by all threads.
+template <bool UPPER>
+__global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float* __restrict__ LU, int64_t lda, int j0,
+                                                                   int w, float* __restrict__ B, int64_t ldb) {
+  __shared__ float ys[kSolveBlock];
+  float* b = B + (int64_t)blockIdx.x * ldb + j0;
+  const float* T = LU + j0 + (int64_t)j0 * lda;  // the diagonal block: (i, q) at T[i + q * lda]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < w) ys[tid] = b[tid];
+  __syncthreads();
+  const int nsub = (w + 31) / 32;
+  for (int t = 0; t < nsub; ++t) {
+    const int s0 = UPPER ? (nsub - 1 - t) * 32 : t * 32;
+    const int ws = min(32, w - s0);
+    if (warp == 0) {
+      float M[32];
+      float v = lane < ws ? ys[s0 + lane] : 0.f;
+      if (!UPPER) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) M[q] = (q < lane && lane < ws) ? T[(s0 + lane) + (int64_t)(s0 + q) * lda] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 31; ++q) {
+          const float yq = __shfl_sync(0xFFFFFFFFu, v, q);
+          if (q < lane) v = fmaf(-M[q], yq, v);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) M[q] = (lane <= q && q < ws) ? T[(s0 + lane) + (int64_t)(s0 + q) * lda] : 0.f;
+#pragma unroll
+        for (int q = 31; q >= 0; --q) {
+          if (q < ws) {
+            if (lane == q) v = v / M[q];
+            const float xq = __shfl_sync(0xFFFFFFFFu, v, q);
+            if (lane < q) v = fmaf(-M[q], xq, v);
+          }
+        }
+      }
+      if (lane < ws) ys[s0 + lane] = v;
+    }
+    __syncthreads();
+    // rows of the block beyond the 32 just solved (below for L, above for U)
+    const int i = tid;
+    if (UPPER ? i < s0 : (i >= s0 + 32 && i < w)) {
+      float acc = ys[i];
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (q < ws) acc = fmaf(-T[i + (int64_t)(s0 + q) * lda], ys[s0 + q], acc);
+      ys[i] = acc;
+    }
+    __syncthreads();
+  }
+  if (tid < w) b[tid] = ys[tid];
+}
+
+bool g_attr_done[64][3];
+
+cudaError_t set_smem_once(const void* fn, int which, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && g_attr_done[dev][which]) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_done[dev][which] = true;
+  return e;
+}
+
+}  // namespace
+
+int lu_slab_pitch(int nbp) { return nbp <= 2 ? nbp : 4 * (((nbp + 3) / 4) | 1); }
+
+int lu_panel_width(int rows) {
+  for (int w = kLuPanelNb; w > 1; w /= 2)
+    if ((int64_t)rows <= (int64_t)kLuPanelCluster * (kLuPanelSlabBytes / (4 * lu_slab_pitch(w)))) return w;
+  return 1;
+}
+
+cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,
+                            cudaStream_t s) {
+  if (nbp <= 0 || nbp > kLuPanelNb) return cudaErrorInvalidValue;
+  const int R = n - j0;
+  const int pitch = lu_slab_pitch(nbp);
+  const int cap = kLuPanelSlabBytes / (4 * pitch);  // slab rows a block holds
+  const int C = R <= 256 ? 1 : kLuPanelCluster;
+  const int RS = (R + C - 1) / C;
+  if (RS > cap) return cudaErrorInvalidValue;
+  cudaError_t e = set_smem_once((const void*)lu_panel_kernel, 0, kLuPanelSlabBytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(kPanelThreads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)RS * pitch * sizeof(float);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm);
+}
+
+cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStream_t s) {
+  if (nbp <= 0 || nbp > kLuMaxNb) return cudaErrorInvalidValue;
+  lu_perm_kernel<<<1, 32, 0, s>>>(j0, nbp, ipiv, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_swap_trsm(int n, float* A, int64_t lda, int j0, int nbp, const int* perm, int c_lo, int c_hi,
+                                cudaStream_t s) {
+  if (nbp <= 0 || nbp > kLuMaxNb || c_lo < 0 || c_lo > j0 || c_hi < j0 + nbp || c_hi > n)
+    return cudaErrorInvalidValue;
+  const int left_tiles = (j0 - c_lo + kTrsmCols - 1) / kTrsmCols;
+  const int right_tiles = (c_hi - j0 - nbp + kTrsmCols - 1) / kTrsmCols;
+  if (left_tiles + right_tiles == 0) return cudaSuccess;
+  const size_t max_smem = ((size_t)2 * kLuMaxNb * kXP + (size_t)kLuMaxNb * (kLuMaxNb + 1)) * sizeof(float);
+  cudaError_t e = set_smem_once((const void*)lu_swap_trsm_kernel, 1, max_smem);
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t)2 * nbp * kXP + (size_t)nbp * (nbp + 1)) * sizeof(float);
+  lu_swap_trsm_kernel<<<left_tiles + right_tiles, kTrsmCols, smem, s>>>(n, A, lda, j0, nbp, perm, c_lo, c_hi,
+                                                                         left_tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_laswp_rhs(int n, int64_t nrhs, const int* ipiv, float* B, int64_t ldb, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  if (nrhs > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+  if (n <= kLuSolveSmemN) {
+    cudaError_t e = set_smem_once((const void*)lu_laswp_rhs_kernel<true>, 2, (size_t)kLuSolveSmemN * sizeof(float));
+    if (e != cudaSuccess) return e;
+    lu_laswp_rhs_kernel<true><<<(unsigned)nrhs, 256, (size_t)n * sizeof(float), s>>>(n, ipiv, B, ldb);
+  } else {
+    lu_laswp_rhs_kernel<false><<<(unsigned)nrhs, 256, 0, s>>>(n, ipiv, B, ldb);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_trsv_block(bool upper, const float* LU, int64_t lda, int j0, int w, int64_t nrhs, float* B,
+                                 int64_t ldb, cudaStream_t s) {
+  if (w <= 0 || nrhs <= 0) return cudaSuccess;
+  if (w > kSolveBlock || nrhs > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  if (upper)
+    lu_trsv_block_kernel<true><<<(unsigned)nrhs, kSolveBlock, 0, s>>>(LU, lda, j0, w, B, ldb);
+  else
+    lu_trsv_block_kernel<false><<<(unsigned)nrhs, kSolveBlock, 0, s>>>(LU, lda, j0, w, B, ldb);
+  return cudaGetLastError();
+}
+
+}  // namespace gbg

@@ -60,7 +60,7 @@ class Problem(ctypes.Structure):
 EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_sgemm_strided_batched",
-    "gbgemm_sgemv",
+    "gbgemm_sgemv", "gbgemm_sgetrf", "gbgemm_sgetrs",
     "gbgemm_get_device_status",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
     "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
@@ -102,6 +102,8 @@ def lib():
             L.gbgemm_sgemm_strided_batched.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32,
                                                        vp, i64, i64, i64]
             L.gbgemm_sgemv.argtypes = [vp, c, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64]
+            L.gbgemm_sgetrf.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.c_int]
+            L.gbgemm_sgetrs.argtypes = [vp, i64, i64, vp, i64, vp, vp, i64]
             L.gbgemm_get_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.gbgemm_status_string.argtypes = [ctypes.c_int]
             L.gbgemm_status_string.restype = ctypes.c_char_p
@@ -142,7 +144,7 @@ def lib():
                                              ctypes.POINTER(i64)]
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
-                         "gbgemm_sgemm_strided_batched", "gbgemm_sgemv",
+                         "gbgemm_sgemm_strided_batched", "gbgemm_sgemv", "gbgemm_sgetrf", "gbgemm_sgetrs",
                          "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
                          "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
                          "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
@@ -247,6 +249,20 @@ class Handle:
                                 float(alpha), _ptr(A), int(lda), _ptr(x), int(incx), float(beta), _ptr(y), int(incy))
         if check:
             _check("gbgemm_sgemv", rc)
+        return rc
+
+    def sgetrf(self, n, A, lda, ipiv, info, nb=0, check=True) -> int:
+        """P A = L U in place (ipiv: n int32, info: one int32, both on the device)."""
+        rc = lib().gbgemm_sgetrf(self._h, int(n), _ptr(A), int(lda), _ptr(ipiv), _ptr(info), int(nb))
+        if check:
+            _check("gbgemm_sgetrf", rc)
+        return rc
+
+    def sgetrs(self, n, nrhs, LU, lda, ipiv, B, ldb, check=True) -> int:
+        """B := A^-1 B from the factors of sgetrf."""
+        rc = lib().gbgemm_sgetrs(self._h, int(n), int(nrhs), _ptr(LU), int(lda), _ptr(ipiv), _ptr(B), int(ldb))
+        if check:
+            _check("gbgemm_sgetrs", rc)
         return rc
 
     def get_device_status(self) -> int:

@@ -106,6 +106,33 @@ def test_gemv_argument_errors_in_order(L):
         assert call(t=bytes([t])) == gbgemm.ERR_NOT_INITIALIZED
 
 
+def test_getrf_getrs_argument_errors_in_order(L):
+    a = ctypes.c_void_p(16)  # never dereferenced: argument checks run first
+    def getrf(n=5, A=a, lda=5, ipiv=a, info=a, nb=0):
+        return L.gbgemm_sgetrf(None, n, A, lda, ipiv, info, nb)
+    assert getrf(n=-1) == -1
+    assert getrf(n=2**31) == -1
+    assert getrf(A=None) == -2
+    assert getrf(lda=4) == -3
+    assert getrf(ipiv=None) == -4
+    assert getrf(info=None) == -5
+    assert getrf(nb=-1) == -6
+    assert getrf(nb=129) == -6
+    assert getrf(n=0, A=None, lda=1, ipiv=None) == gbgemm.ERR_NOT_INITIALIZED
+    assert getrf(nb=128) == gbgemm.ERR_NOT_INITIALIZED
+    def getrs(n=5, nrhs=2, LU=a, lda=5, ipiv=a, B=a, ldb=5):
+        return L.gbgemm_sgetrs(None, n, nrhs, LU, lda, ipiv, B, ldb)
+    assert getrs(n=-1) == -1
+    assert getrs(nrhs=-1) == -2
+    assert getrs(LU=None) == -3
+    assert getrs(lda=4) == -4
+    assert getrs(ipiv=None) == -5
+    assert getrs(B=None) == -6
+    assert getrs(ldb=4) == -7
+    assert getrs(nrhs=0, B=None) == gbgemm.ERR_NOT_INITIALIZED
+    assert getrs() == gbgemm.ERR_NOT_INITIALIZED
+
+
 def test_null_handle_and_status_strings(L):
     assert L.gbgemm_destroy(None) == gbgemm.ERR_NOT_INITIALIZED
     assert L.gbgemm_set_path(None, 0) == gbgemm.ERR_NOT_INITIALIZED
