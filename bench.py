@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "sgemm TFLOP/s at 8192^3: 3xBF16 tensor vs FP32 SIMT, same GPU, same error bound"
 # DRAM bytes (read + write) of one split_gemm_kernel launch at 8192^3 NN, ld 8200,
 # from one ncu capture of the current kernel (profiles/split_gemm_8192_nn_traffic.md).
-GEMM_TRAFFIC_8192 = 2544064768 + 259988480
+GEMM_TRAFFIC_8192 = 2562743296 + 255532544
 UNIT = "TFLOP/s"
 N = 8192
 LD = N + 8

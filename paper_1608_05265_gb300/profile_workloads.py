@@ -1,0 +1,98 @@
+"""Fixed workloads for profiling the library under ncu (one GPU).
+
+    python -m paper_1608_05265_gb300.profile_workloads <name> [--reps R]
+
+runs one workload R times on cuda:0 through the C-ABI binding and exits 0.
+Inputs are seeded and generated on the device; nothing is timed or printed
+beyond a one-line summary.  Names:
+
+  split4096   sgemm 4096^3 NN, ld 4104, split path (alpha 1.5, beta -0.25)
+  simt4096    the same on the FP32 SIMT path
+  split8192   sgemm 8192^3 NN, ld 8200, split path (the headline shape)
+  grouped     the 4096-problem uneven batch (m, n, k log-uniform in
+              [16, 1024], seed 3), one plan with the default configurations
+  lu4608      sgetrf + sgetrs, N 4608 (the paper's HPL size), default block
+"""
+
+from __future__ import annotations
+
+import argparse
+
+
+def _split_or_simt(h, path, reps, n=4096):
+    import torch
+    from paper_1608_05265_gb300 import gbgemm
+    ld = n + 8
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.rand(ld * n, device="cuda", generator=g) * 2 - 1
+    B = torch.rand(ld * n, device="cuda", generator=g) * 2 - 1
+    C = torch.rand(ld * n, device="cuda", generator=g) * 2 - 1
+    h.set_path(gbgemm.PATH_SPLIT_BF16 if path == "split" else gbgemm.PATH_SIMT)
+    for _ in range(reps):
+        h.sgemm("N", "N", n, n, n, 1.5, A, ld, B, ld, -0.25, C, ld)
+    torch.cuda.synchronize()
+
+
+def _grouped(h, reps):
+    import torch
+    from paper_1608_05265_gb300 import gbgemm, synth
+    shapes = synth.grouped_shapes(3, 4096)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    bufs, probs = [], []
+    for (ta, tb, m, n, k) in shapes:
+        ar, ac = synth.op_shape(ta, m, k)
+        br, bc = synth.op_shape(tb, k, n)
+        A = torch.rand(ar * ac, device="cuda", generator=g) * 2 - 1
+        B = torch.rand(br * bc, device="cuda", generator=g) * 2 - 1
+        C = torch.empty(m * n, device="cuda")
+        bufs.append((A, B, C))
+        probs.append(gbgemm.problem(ta, tb, m, n, k, 1.0, A, ar, B, br, 0.0, C, m))
+    plan = gbgemm.GroupedPlan(h, probs, config_source=gbgemm.CONFIG_DEFAULT)
+    stream = torch.cuda.current_stream()
+    for _ in range(reps):
+        plan.run(stream)
+    torch.cuda.synchronize()
+    plan.close()
+
+
+def _lu(h, reps):
+    import torch
+    n = 4608
+    g = torch.Generator(device="cuda").manual_seed(8)
+    A0 = torch.rand(n * n, device="cuda", generator=g) - 0.5
+    b0 = torch.rand(n, device="cuda", generator=g) - 0.5
+    piv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = torch.empty(1, dtype=torch.int32, device="cuda")
+    for _ in range(reps):
+        A, b = A0.clone(), b0.clone()
+        h.sgetrf(n, A, n, piv, info)
+        h.sgetrs(n, 1, A, n, piv, b, n)
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError(f"sgetrf info {int(info.item())}")
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("name", choices=["split4096", "simt4096", "split8192", "grouped", "lu4608"])
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args(argv)
+    import torch
+    from paper_1608_05265_gb300 import build, gbgemm
+    build.build()
+    h = gbgemm.Handle(0)
+    h.set_stream(torch.cuda.current_stream())
+    if args.name in ("split4096", "simt4096", "split8192"):
+        _split_or_simt(h, args.name[:-4], args.reps, int(args.name[-4:]))
+    elif args.name == "grouped":
+        _grouped(h, args.reps)
+    else:
+        _lu(h, args.reps)
+    status = h.get_device_status()
+    h.close()
+    print(f"{args.name}: {args.reps} runs, device status {status}")
+    return 0 if status == 0 else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
