@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   __shared__ MaxLoc pub_cand[2];
   __shared__ __align__(16) float pub_row[2][kLuPanelNb];  // the candidate's row
   __shared__ __align__(16) float pub_q[2][kLuPanelNb];    // row q, from the block holding it
-  __shared__ MaxLoc cand_all[kLuPanelCluster];
+  __shared__ int sh_p, sh_w;
   __shared__ __align__(16) float rows_all[kLuPanelCluster][kLuPanelNb];
   __shared__ __align__(16) float qrow[kLuPanelNb];
   __shared__ int piv_s[kLuPanelNb];
@@ -187,27 +187,40 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     }
     cl.sync();
     const int oq = q / RS;  // the block holding row q
-    // one round of remote reads: every candidate, every candidate's row, row q
-    for (int e = tid; e < C * kLuPanelNb + C + kLuPanelNb; e += kPanelThreads) {
-      if (e < C * kLuPanelNb) {
-        const int r = e / kLuPanelNb, col = e % kLuPanelNb;
-        if (col < nbp) rows_all[r][col] = *cl.map_shared_rank(&pub_row[par][col], r);
-      } else if (e < C * kLuPanelNb + C) {
-        cand_all[e - C * kLuPanelNb] = *cl.map_shared_rank(&pub_cand[par], e - C * kLuPanelNb);
-      } else {
-        const int col = e - C * kLuPanelNb - C;
-        if (col < nbp) qrow[col] = *cl.map_shared_rank(&pub_q[par][col], oq);
+    // one round of remote reads: every candidate's row and row q; warp 0 also
+    // reads the candidates and reduces them (the same order in every block:
+    // the same pivot) while the others load
+    for (int e = tid; e < C * kLuPanelNb + kLuPanelNb; e += kPanelThreads) {
+      const int r = e / kLuPanelNb, col = e % kLuPanelNb;
+      if (col < nbp) {
+        if (r < C)
+          rows_all[r][col] = *cl.map_shared_rank(&pub_row[par][col], r);
+        else
+          qrow[col] = *cl.map_shared_rank(&pub_q[par][col], oq);
+      }
+    }
+    if (tid < 32) {
+      MaxLoc mm{-1.f, INT_MAX};
+      int who = -1;
+      if (tid < C) {
+        mm = *cl.map_shared_rank(&pub_cand[par], tid);
+        who = tid;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xFFFFFFFFu, mm.v, o);
+        const int i2 = __shfl_xor_sync(0xFFFFFFFFu, mm.i, o);
+        const int w2 = __shfl_xor_sync(0xFFFFFFFFu, who, o);
+        if (v2 > mm.v || (v2 == mm.v && i2 < mm.i)) { mm.v = v2; mm.i = i2; who = w2; }
+      }
+      if (tid == 0) {
+        sh_p = (mm.i == INT_MAX) ? q : mm.i;  // (a column of NaNs keeps its row)
+        sh_w = (mm.i == INT_MAX) ? -1 : who;
       }
     }
     __syncthreads();
-    MaxLoc w{-1.f, INT_MAX};
-    int wr = 0;
-    for (int r = 0; r < C; ++r) {  // the same order in every block: the same pivot
-      const MaxLoc x = cand_all[r];
-      if (x.v > w.v || (x.v == w.v && x.i < w.i)) { w = x; wr = r; }
-    }
-    const int p = (w.i == INT_MAX) ? q : w.i;  // (a column of NaNs keeps its row)
-    const float* prow = (w.i == INT_MAX) ? qrow : rows_all[wr];
+    const int p = sh_p;
+    const float* prow = sh_w < 0 ? qrow : rows_all[sh_w];
     if (c == 0 && tid == 0) {
       ipiv[j0 + q] = j0 + p + 1;
       piv_s[q] = j0 + p;
@@ -230,56 +243,54 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         }
     } else {
       const bool use_rcp = fabsf(d) >= FLT_MIN;  // 1 / d is finite
-      const float rcp = 1.0f / d;
-      float4 u[kLuPanelNb / 4];  // the pivot row, zero up to column q + 1
-#pragma unroll
-      for (int j = 0; j < kLuPanelNb / 4; ++j) {
-        float t[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int k = 4 * j + e;
-          t[e] = (k > q + 1 && k < nbp) ? prow[k] : 0.f;
-        }
-        u[j] = make_float4(t[0], t[1], t[2], t[3]);
-      }
+      const float rcp = __frcp_rn(d);            // correctly rounded, as 1.0f / d
       const float p1 = q + 1 < nbp ? prow[q + 1] : 0.f;
+      const int jb = (q + 2) / 4;  // the first group holding a column beyond q + 1
+      float4 u[kLuPanelNb / 4];    // the pivot row
+      if (vec) {
+#pragma unroll
+        for (int j = 0; j < kLuPanelNb / 4; ++j)
+          if (j < groups) u[j] = reinterpret_cast<const float4*>(prow)[j];
+      }
       for (int rr = rs + tid; rr < nr; rr += kPanelThreads) {
-        const bool isp = rlo + rr == p;  // this row receives row q
         float* row = Sp + rr * pitch;
-        const float* src = isp ? qrow : row;  // the row's values before the update
-        const float a = src[q];
-        const float l = use_rcp ? a * rcp : a / d;
-        const float v1 = q + 1 < nbp ? fmaf(-l, p1, src[q + 1]) : 0.f;
-        if (vec) {
-          float4 x[kLuPanelNb / 4];
+        if (rlo + rr != p) {
+          const float a = row[q];
+          const float l = use_rcp ? a * rcp : a / d;
+          const float v1 = q + 1 < nbp ? fmaf(-l, p1, row[q + 1]) : 0.f;
+          if (vec) {
+            float4 x[kLuPanelNb / 4];  // every load issued before any store
 #pragma unroll
-          for (int j = 0; j < kLuPanelNb / 4; ++j)
-            if (j < groups) x[j] = reinterpret_cast<const float4*>(src)[j];
+            for (int j = 0; j < kLuPanelNb / 4; ++j)
+              if (j >= jb && j < groups) x[j] = reinterpret_cast<const float4*>(row)[j];
 #pragma unroll
-          for (int j = 0; j < kLuPanelNb / 4; ++j) {
-            // groups holding a column beyond q + 1 are updated; row p takes
-            // every group (row q's values)
-            if (j < groups && (isp || 4 * j + 3 > q + 1)) {
-              x[j].x = fmaf(-l, u[j].x, x[j].x);
-              x[j].y = fmaf(-l, u[j].y, x[j].y);
-              x[j].z = fmaf(-l, u[j].z, x[j].z);
-              x[j].w = fmaf(-l, u[j].w, x[j].w);
-              if (!isp && 4 * j <= q + 1) {  // keep columns <= q + 1 exactly as they were
-                const float4 o = reinterpret_cast<const float4*>(src)[j];
-                if (4 * j + 0 <= q + 1) x[j].x = o.x;
-                if (4 * j + 1 <= q + 1) x[j].y = o.y;
-                if (4 * j + 2 <= q + 1) x[j].z = o.z;
+            for (int j = 0; j < kLuPanelNb / 4; ++j) {
+              if (j > jb && j < groups) {
+                x[j].x = fmaf(-l, u[j].x, x[j].x);
+                x[j].y = fmaf(-l, u[j].y, x[j].y);
+                x[j].z = fmaf(-l, u[j].z, x[j].z);
+                x[j].w = fmaf(-l, u[j].w, x[j].w);
+                reinterpret_cast<float4*>(row)[j] = x[j];
+              } else if (j == jb && j < groups) {  // columns <= q + 1 keep their values
+                if (4 * j + 0 > q + 1) x[j].x = fmaf(-l, u[j].x, x[j].x);
+                if (4 * j + 1 > q + 1) x[j].y = fmaf(-l, u[j].y, x[j].y);
+                if (4 * j + 2 > q + 1) x[j].z = fmaf(-l, u[j].z, x[j].z);
+                x[j].w = fmaf(-l, u[j].w, x[j].w);
+                reinterpret_cast<float4*>(row)[j] = x[j];
               }
-              reinterpret_cast<float4*>(row)[j] = x[j];
             }
           }
-        } else if (isp) {
-          for (int k = 0; k < nbp; ++k) row[k] = qrow[k];
-        }
-        row[q] = l;
-        if (q + 1 < nbp) {  // the next column: its largest |a| is the next candidate
-          row[q + 1] = v1;
-          if (fabsf(v1) > best) { best = fabsf(v1); bi = rlo + rr; }
+          row[q] = l;
+          if (q + 1 < nbp) {  // the next column: its largest |a| is the next candidate
+            row[q + 1] = v1;
+            if (fabsf(v1) > best) { best = fabsf(v1); bi = rlo + rr; }
+          }
+        } else {  // row p: receives row q's values, updated
+          const float a = qrow[q];
+          const float l = use_rcp ? a * rcp : a / d;
+          for (int k = 0; k < nbp; ++k) row[k] = k > q ? fmaf(-l, prow[k], qrow[k]) : qrow[k];
+          row[q] = l;
+          if (q + 1 < nbp && fabsf(row[q + 1]) > best) { best = fabsf(row[q + 1]); bi = rlo + rr; }
         }
       }
     }
