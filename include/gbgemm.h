@@ -175,7 +175,7 @@ int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha
  * factorisation still completes, as in LAPACK).  nb: block width, 1 ..
  * GBGEMM_SGETRF_MAX_NB, or 0 for GBGEMM_SGETRF_DEFAULT_NB below n =
  * GBGEMM_SGETRF_WIDE_N and GBGEMM_SGETRF_MAX_NB from there (the faster of the
- * two at N 4608 and 16384 on GB300).  Each block of nb columns is factored as
+ * two measured at N 4608, 8192 and 16384 on GB300).  Each block of nb columns is factored as
  * panels of at most 32 columns (narrower when the panel's rows outgrow the
  * shared memory of a cluster of 8 thread blocks, which holds a panel for its
  * whole factorisation), the exchanges and triangular solves of each panel
@@ -192,7 +192,7 @@ int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha
  * GBGEMM_ERR_CUDA, or an error of the trailing sgemm. */
 #define GBGEMM_SGETRF_MAX_NB 128
 #define GBGEMM_SGETRF_DEFAULT_NB 32
-#define GBGEMM_SGETRF_WIDE_N 8192
+#define GBGEMM_SGETRF_WIDE_N 12288
 int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv, int* info, int nb);
 
 /* Solve A X = B with the factors of gbgemm_sgetrf (LAPACK sgetrs, no

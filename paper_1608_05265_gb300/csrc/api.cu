@@ -28,6 +28,8 @@ struct gbgemm_handle {
   size_t ws_bytes = 0;
   int* d_status = nullptr;
   int* d_lu_perm = nullptr;  // row permutation of the current LU panel
+  cudaStream_t lu_side = nullptr;  // LU look-ahead: the next block's factorisation
+  cudaEvent_t lu_ev[2] = {nullptr, nullptr};
   // profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
@@ -136,6 +138,9 @@ int gbgemm_create(gbgemm_handle** out, int device) {
     cudaGetLastError();
     if (h->d_status) cudaFree(h->d_status);
   if (h->d_lu_perm) cudaFree(h->d_lu_perm);
+  for (cudaEvent_t e : h->lu_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->lu_side) cudaStreamDestroy(h->lu_side);
     delete h;
     return GBGEMM_ERR_ALLOC;
   }
@@ -402,50 +407,66 @@ int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv,
     return GBGEMM_ERR_ALLOC;
   }
   const int b = nb > 0 ? nb : (n < GBGEMM_SGETRF_WIDE_N ? GBGEMM_SGETRF_DEFAULT_NB : GBGEMM_SGETRF_MAX_NB);
+  if (!h->lu_side) {  // look-ahead stream (highest priority) and its two events
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->lu_side, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+      h->lu_side = nullptr;
+      return GBGEMM_ERR_CUDA;
+    }
+    for (cudaEvent_t& e : h->lu_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  }
   // The trailing updates run with the handle's path choice but never through
   // the per-call tuner (each update has a new shape).
   const int tuning = h->tuning;
   h->tuning = 0;
   int rc = GBGEMM_OK;
-  auto update = [&](int64_t r, int64_t c, int64_t rows, int64_t cols, int64_t k) {
-    // A(r:r+rows, c:c+cols) -= A(r:r+rows, c-k:c) A(c-k:c, c:c+cols)
-    return run_sgemm(h, 0, 0, 'N', 'N', rows, cols, k, -1.0f, A + r + (c - k) * lda, lda, A + (r - k) + c * lda, lda,
-                     1.0f, A + r + c * lda, lda, 1, 0, 0, 0);
+  auto update = [&](int64_t r, int64_t c, int64_t rows, int64_t cols, int64_t kc, int64_t k) {
+    // A(r:r+rows, c:c+cols) -= A(r:r+rows, kc:kc+k) A(kc:kc+k, c:c+cols), on the handle's stream
+    return run_sgemm(h, 0, 0, 'N', 'N', rows, cols, k, -1.0f, A + r + kc * lda, lda, A + kc + c * lda, lda, 1.0f,
+                     A + r + c * lda, lda, 1, 0, 0, 0);
   };
   int* perm = h->d_lu_perm;
-  for (int64_t j0 = 0; j0 < n && rc == GBGEMM_OK; j0 += b) {
-    const int nbo = (int)(n - j0 < b ? n - j0 : b);
-    // panels as wide as 32 columns while the panel rows fit the cluster's shared memory
+  // Factor the block [j0, j0 + nbo) on stream s: panels of pw columns, each
+  // followed by its exchanges and triangular solve over the rest of the block
+  // and the SIMT update of the block columns right of it (no workspace, so
+  // the block can be factored while the handle's stream updates other
+  // columns); then the block's exchanges as one permutation.
+  auto factor_block = [&](int64_t j0, int nbo, cudaStream_t s) -> int {
     const int fit = gbg::lu_panel_width((int)(n - j0));
     const int pw = b < fit ? b : fit;
-    // the block [j0, j0 + nbo) as panels of pw columns, each followed by the
-    // exchanges and triangular solve over the rest of the block and the
-    // update of the block columns right of it
-    for (int64_t j1 = j0; j1 < j0 + nbo && rc == GBGEMM_OK; j1 += pw) {
+    for (int64_t j1 = j0; j1 < j0 + nbo; j1 += pw) {
       const int w = (int)(j0 + nbo - j1 < pw ? j0 + nbo - j1 : pw);
-      if (gbg::launch_lu_panel((int)n, A, lda, (int)j1, w, ipiv, info, perm, h->stream) != cudaSuccess) {
-        rc = GBGEMM_ERR_CUDA;
-        break;
-      }
+      if (gbg::launch_lu_panel((int)n, A, lda, (int)j1, w, ipiv, info, perm, s) != cudaSuccess) return GBGEMM_ERR_CUDA;
       h->kernel_launches += 1;
-      if (w == nbo) break;
-      if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j1, w, perm, (int)j0, (int)(j0 + nbo), h->stream) !=
-          cudaSuccess) {
-        rc = GBGEMM_ERR_CUDA;
-        break;
-      }
+      if (w == nbo) return GBGEMM_OK;  // one panel: its permutation is the block's
+      if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j1, w, perm, (int)j0, (int)(j0 + nbo), s) != cudaSuccess)
+        return GBGEMM_ERR_CUDA;
       h->kernel_launches += 1;
-      const int64_t cols = j0 + nbo - j1 - w;
-      if (cols > 0) rc = update(j1 + w, j1 + w, n - j1 - w, cols, w);
+      const int64_t rows = n - j1 - w, cols = j0 + nbo - j1 - w;
+      if (cols > 0) {
+        const int64_t r = j1 + w, c = j1 + w;
+        const gbg::Problem p{0, 0, rows, cols, w, -1.0f, 1.0f, A + r + j1 * lda, lda, A + j1 + c * lda, lda,
+                             A + r + c * lda, lda};
+        const int cfg = rows * cols <= (int64_t)512 * 512 ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
+        if (gbg::launch_simt(p, cfg, s) != cudaSuccess) return GBGEMM_ERR_CUDA;
+        h->kernel_launches += 1;
+      }
     }
-    if (rc != GBGEMM_OK) break;
-    if (nbo > pw) {  // the block's exchanges as one permutation
-      if (gbg::launch_lu_perm((int)j0, nbo, ipiv, perm, h->stream) != cudaSuccess) {
-        rc = GBGEMM_ERR_CUDA;
-        break;
-      }
-      h->kernel_launches += 1;
-    }
+    if (gbg::launch_lu_perm((int)j0, nbo, ipiv, perm, s) != cudaSuccess) return GBGEMM_ERR_CUDA;
+    h->kernel_launches += 1;
+    return GBGEMM_OK;
+  };
+  // Look-ahead: after block k's exchanges and U12, the next block's columns
+  // are updated first; the next block is then factored on the side stream
+  // while the handle's stream updates the remaining columns.  The two touch
+  // disjoint columns; the handle's stream waits for the block before
+  // applying its exchanges.
+  int nbo = (int)(n < b ? n : b);
+  rc = factor_block(0, nbo, h->stream);
+  for (int64_t j0 = 0; j0 < n && rc == GBGEMM_OK; j0 += nbo) {
+    nbo = (int)(n - j0 < b ? n - j0 : b);
     if (j0 > 0 || j0 + nbo < n) {
       if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j0, nbo, perm, 0, (int)n, h->stream) != cudaSuccess) {
         rc = GBGEMM_ERR_CUDA;
@@ -453,8 +474,29 @@ int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv,
       }
       h->kernel_launches += 1;
     }
-    const int64_t rest = n - j0 - nbo;
-    if (rest > 0) rc = update(j0 + nbo, j0 + nbo, rest, rest, nbo);
+    const int64_t jn = j0 + nbo;  // the next block
+    if (jn >= n) break;
+    const int nbn = (int)(n - jn < b ? n - jn : b);
+    rc = update(jn, jn, n - jn, nbn, j0, nbo);
+    if (rc != GBGEMM_OK) break;
+    if (cudaEventRecord(h->lu_ev[0], h->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(h->lu_side, h->lu_ev[0], 0) != cudaSuccess) {
+      rc = GBGEMM_ERR_CUDA;
+      break;
+    }
+    rc = factor_block(jn, nbn, h->lu_side);
+    if (rc != GBGEMM_OK) break;
+    if (cudaEventRecord(h->lu_ev[1], h->lu_side) != cudaSuccess) {
+      rc = GBGEMM_ERR_CUDA;
+      break;
+    }
+    const int64_t rest = n - jn - nbn;
+    if (rest > 0) rc = update(jn, jn + nbn, n - jn, rest, j0, nbo);
+    if (rc != GBGEMM_OK) break;
+    if (cudaStreamWaitEvent(h->stream, h->lu_ev[1], 0) != cudaSuccess) rc = GBGEMM_ERR_CUDA;
+  }
+  if (rc != GBGEMM_OK) {  // never leave work on the side stream unjoined
+    if (cudaEventRecord(h->lu_ev[1], h->lu_side) == cudaSuccess) cudaStreamWaitEvent(h->stream, h->lu_ev[1], 0);
   }
   h->tuning = tuning;
   return rc;

@@ -3,26 +3,29 @@
 // library's own sgemm doing the trailing updates (the Linpack-shaped
 // C := C - A B of the benchmark).
 //
-// Right-looking, blocked by nb columns.  For each block column j0:
-//   panel    rows [j0, n) x columns [j0, j0 + nb), factored by one
-//            1024-thread block in inner blocks of 8 columns.  An inner block
-//            is staged in shared memory when its rows fit (8 x 6144 floats),
-//            else worked on in place.  Per column: the pivot is the first row
-//            of largest |a| (block argmax, smallest row on ties, fused into
-//            the previous column's update pass), the two rows are exchanged
-//            within the inner block, the column is divided by the pivot and
-//            the rest of the inner block updated.  After each inner block its
-//            row exchanges are applied to the other panel columns as one
-//            gather, then the rest of the panel gets an 8-row triangular
-//            solve and a rank-8 update.  At the end the panel's exchanges are
-//            written out as a row permutation of the rows they touch.
-//   swap+U12 every column outside the panel gets the permutation (one
-//            gather per column: all sources read before any row is written);
-//            right of the panel, U12 = L11^-1 A12 follows in shared memory.
-//   update   A22 := A22 - L21 U12 by gbgemm's sgemm.
-// The row exchanges of earlier panels reach the left columns at the same
-// time as the right ones, so the result is LAPACK's packed P A = L U.  Every
-// sum is formed in a fixed order: runs are bit-identical.
+// Right-looking, blocked by nb columns; each block is factored as panels of
+// at most 32 columns:
+//   panel    rows [j1, n) x the panel's columns, held in the shared memory
+//            of a cluster of up to 8 blocks for the whole factorisation
+//            (lu_panel_kernel): per column one cluster barrier, one round of
+//            distributed-shared-memory reads, the pivot (first row of largest
+//            |a|) chosen identically in every block, the exchange and the
+//            rank-1 update done locally.  The panel's exchanges are written
+//            out as a permutation of the rows they touch.
+//   swap+U12 the other columns of the block get that permutation (one gather
+//            per column: all sources read before any row is written), and
+//            right of the panel U12 = L11^-1 A12 is solved in shared memory
+//            (lu_swap_trsm_kernel); the block columns right of the panel are
+//            updated by the library's sgemm.
+//   block    the block's exchanges, rebuilt as one permutation
+//            (lu_perm_kernel), reach every column outside the block, U12 of
+//            the block rows is solved, and the trailing matrix is updated by
+//            the library's sgemm with k = nb.
+// The result is LAPACK's packed P A = L U.  The solve (lu_laswp_rhs_kernel,
+// lu_trsv_block_kernel) applies the exchanges, then forward and back
+// substitution by 256-row diagonal blocks, the off-diagonal parts by the
+// library's sgemv or sgemm.  Every sum is formed in a fixed order: runs are
+// bit-identical.
 #include <cfloat>
 #include <climits>
 
@@ -35,8 +38,9 @@ namespace cg = cooperative_groups;
 namespace gbg {
 namespace {
 
-constexpr int kPanelThreads = 512;
-constexpr int kTrsmCols = 128;    // columns per block of the swap + triangular solve kernel
+constexpr int kPanelThreads = 512;  // per block of the panel's cluster
+constexpr int kTrsmCols = 64;     // columns per block of the swap + triangular solve kernel
+constexpr int kSwapThreads = 256;  // its threads (the first kTrsmCols solve one column each)
 constexpr int kXP = kTrsmCols + 1;
 
 struct MaxLoc {
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
 // right of them, then U12 = L11^-1 A12, one thread per column, L11 and the
 // block's columns staged in shared memory.  Blocks [0, left_tiles) cover the
 // left range.
-__global__ void __launch_bounds__(kTrsmCols) lu_swap_trsm_kernel(int n, float* __restrict__ A, int64_t lda, int j0,
+__global__ void __launch_bounds__(kSwapThreads) lu_swap_trsm_kernel(int n, float* __restrict__ A, int64_t lda, int j0,
                                                                  int nbp, const int* __restrict__ perm, int c_lo,
                                                                  int c_hi, int left_tiles) {
   extern __shared__ float sm[];
@@ -323,35 +327,41 @@ __global__ void __launch_bounds__(kTrsmCols) lu_swap_trsm_kernel(int n, float* _
   const int ncol = cend - c0;
   const int tid = threadIdx.x;
 #pragma unroll 8
-  for (int e = tid; e < nbp * ncol; e += kTrsmCols) {  // eight loads in flight per thread
+  for (int e = tid; e < nbp * ncol; e += kSwapThreads) {  // up to eight loads in flight per thread
     const int q = e % nbp, col = e / nbp;
     V[q * kXP + col] = A[src[q] + (int64_t)(c0 + col) * lda];
   }
 #pragma unroll 8
-  for (int e = tid; e < next * ncol; e += kTrsmCols) {
+  for (int e = tid; e < next * ncol; e += kSwapThreads) {
     const int x = e % next, col = e / next;
     W[x * kXP + col] = A[ext[2 * x + 1] + (int64_t)(c0 + col) * lda];
   }
   if (!left)
 #pragma unroll 8
-    for (int e = tid; e < nbp * nbp; e += kTrsmCols) {
+    for (int e = tid; e < nbp * nbp; e += kSwapThreads) {
       const int i = e % nbp, p = e / nbp;
       Ls[i * (nbp + 1) + p] = A[(j0 + i) + (int64_t)(j0 + p) * lda];
     }
   __syncthreads();
-  for (int e = tid; e < next * ncol; e += kTrsmCols) {
+  for (int e = tid; e < next * ncol; e += kSwapThreads) {
     const int x = e % next, col = e / next;
     A[ext[2 * x] + (int64_t)(c0 + col) * lda] = W[x * kXP + col];
   }
-  if (!left && tid < ncol) {
+  if (!left && tid < ncol) {  // two partial sums: half the dependent chain
     for (int i = 1; i < nbp; ++i) {
-      float s = V[i * kXP + tid];
-      for (int p = 0; p < i; ++p) s = fmaf(-Ls[i * (nbp + 1) + p], V[p * kXP + tid], s);
-      V[i * kXP + tid] = s;
+      const float* li = Ls + i * (nbp + 1);
+      float s0 = V[i * kXP + tid], s1 = 0.f;
+      int p = 0;
+      for (; p + 1 < i; p += 2) {
+        s0 = fmaf(-li[p], V[p * kXP + tid], s0);
+        s1 = fmaf(-li[p + 1], V[(p + 1) * kXP + tid], s1);
+      }
+      if (p < i) s0 = fmaf(-li[p], V[p * kXP + tid], s0);
+      V[i * kXP + tid] = s0 + s1;
     }
   }
   __syncthreads();
-  for (int e = tid; e < nbp * ncol; e += kTrsmCols) {
+  for (int e = tid; e < nbp * ncol; e += kSwapThreads) {
     const int q = e % nbp, col = e / nbp;
     A[(j0 + q) + (int64_t)(c0 + col) * lda] = V[q * kXP + col];
   }
@@ -508,7 +518,7 @@ cudaError_t launch_lu_swap_trsm(int n, float* A, int64_t lda, int j0, int nbp, c
   cudaError_t e = set_smem_once((const void*)lu_swap_trsm_kernel, 1, max_smem);
   if (e != cudaSuccess) return e;
   const size_t smem = ((size_t)2 * nbp * kXP + (size_t)nbp * (nbp + 1)) * sizeof(float);
-  lu_swap_trsm_kernel<<<left_tiles + right_tiles, kTrsmCols, smem, s>>>(n, A, lda, j0, nbp, perm, c_lo, c_hi,
+  lu_swap_trsm_kernel<<<left_tiles + right_tiles, kSwapThreads, smem, s>>>(n, A, lda, j0, nbp, perm, c_lo, c_hi,
                                                                          left_tiles);
   return cudaGetLastError();
 }
