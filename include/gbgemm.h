@@ -175,17 +175,21 @@ int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha
  * factorisation still completes, as in LAPACK).  nb: block width, 1 ..
  * GBGEMM_SGETRF_MAX_NB, or 0 for GBGEMM_SGETRF_DEFAULT_NB below n =
  * GBGEMM_SGETRF_WIDE_N and GBGEMM_SGETRF_MAX_NB from there (the faster of the
- * two measured at N 4608, 8192 and 16384 on GB300).  Each block of nb columns is factored as
- * panels of at most 32 columns (narrower when the panel's rows outgrow the
- * shared memory of a cluster of 8 thread blocks, which holds a panel for its
- * whole factorisation), the exchanges and triangular solves of each panel
- * applied across the block and the block columns updated with k = the panel
- * width; after the block, the whole trailing matrix is updated with k = nb.  Columns are scaled by the
- * pivot's reciprocal, as LAPACK's unblocked factorisation and HPL do, so
- * |l_ij| <= 1 holds up to one rounding.
+ * two measured at N 4608, 8192 and 16384 on GB300).  Each block of nb
+ * columns is factored as panels of at most 32 columns (narrower when the
+ * panel's rows outgrow the shared memory of a cluster of 8 thread blocks,
+ * which holds a panel for its whole factorisation), the exchanges and
+ * triangular solves of each panel applied across the block and the block
+ * columns updated with k = the panel width; after the block, the whole
+ * trailing matrix is updated with k = nb.  The next block is factored on a
+ * second stream of the handle while the trailing matrix is updated (the two
+ * touch disjoint columns; the handle's stream waits for it).  Columns are
+ * scaled by the pivot's reciprocal, as LAPACK's unblocked factorisation and
+ * HPL do, so |l_ij| <= 1 holds up to one rounding.
  * Results are bit-identical from run to run.  Queues kernels on the
- * handle's stream and returns without synchronising; the per-call tuner is
- * not used for the trailing updates.
+ * handle's stream (and its look-ahead stream, joined back to it) and returns
+ * without synchronising; the per-call tuner is not used for the trailing
+ * updates.
  * Argument errors, in this order: n (< 0 or > INT_MAX) -1, null A (n > 0) -2,
  * lda -3, null ipiv (n > 0) -4, null info -5, nb -6.  Then
  * GBGEMM_ERR_NOT_INITIALIZED for a NULL handle, GBGEMM_ERR_ALLOC,
