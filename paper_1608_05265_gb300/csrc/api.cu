@@ -438,7 +438,8 @@ int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv,
     const int pw = b < fit ? b : fit;
     for (int64_t j1 = j0; j1 < j0 + nbo; j1 += pw) {
       const int w = (int)(j0 + nbo - j1 < pw ? j0 + nbo - j1 : pw);
-      if (gbg::launch_lu_panel((int)n, A, lda, (int)j1, w, ipiv, info, perm, s) != cudaSuccess) return GBGEMM_ERR_CUDA;
+      if (gbg::launch_lu_panel((int)n, A, lda, (int)j1, w, ipiv, info, perm, h->d_status, s) != cudaSuccess)
+        return GBGEMM_ERR_CUDA;
       h->kernel_launches += 1;
       if (w == nbo) return GBGEMM_OK;  // one panel: its permutation is the block's
       if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j1, w, perm, (int)j0, (int)(j0 + nbo), s) != cudaSuccess)

@@ -45,13 +45,14 @@ constexpr int kLuPanelNb = 32;      // columns per panel inside a block
 // Factor the panel rows [j0, n) x columns [j0, j0 + nbp) in place (a
 // cluster of up to kLuPanelCluster blocks holding the panel in shared
 // memory), writing ipiv[j0 ..) (1-based), the first zero pivot into *info
-// (when *info is 0) and the panel's row permutation into perm.  nbp must not
+// (when *info is 0) and the panel's row permutation into perm; a wait between
+// the cluster's blocks that runs out sets *status.  nbp must not
 // exceed lu_panel_width(n - j0), the widest panel whose rows fit.
 constexpr int kLuPanelCluster = 8;
 constexpr int kLuPanelSlabBytes = 192 * 1024;
 int lu_panel_width(int rows);
 cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,
-                            cudaStream_t s);
+                            int* status, cudaStream_t s);
 // The permutation of pivot rows [j0, j0 + nbp), rebuilt from ipiv (for a
 // block factored as several panels).
 cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStream_t s);

@@ -39,6 +39,7 @@ namespace gbg {
 namespace {
 
 constexpr int kPanelThreads = 512;  // per block of the panel's cluster
+static_assert(kPanelThreads - 2 >= 32 * kLuPanelCluster, "the last two threads never push");
 constexpr int kTrsmCols = 64;     // columns per block of the swap + triangular solve kernel
 constexpr int kSwapThreads = 256;  // its threads (the first kTrsmCols solve one column each)
 constexpr int kXP = kTrsmCols + 1;
@@ -126,41 +127,98 @@ __global__ void lu_perm_kernel(int j0, int nbp, const int* __restrict__ ipiv, in
   build_perm(j0, nbp, piv, prow, pcont, perm);
 }
 
+// PTX helpers of the panel's exchange between the blocks of a cluster.
+__device__ __forceinline__ uint32_t lu_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t lu_mapa(uint32_t a, int rank) {  // the same variable in block `rank`
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// Remote store into block `rank`'s shared memory that completes its bytes on
+// that block's mbarrier.
+__device__ __forceinline__ void lu_push4(uint32_t raddr, float4 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void lu_push1(uint32_t raddr, float v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];"
+               ::"r"(raddr), "f"(v), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void lu_push2(uint32_t raddr, uint32_t a, uint32_t b, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.u32 [%0], {%1, %2}, [%3];"
+               ::"r"(raddr), "r"(a), "r"(b), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void lu_mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void lu_mbar_arm(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool lu_mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Wait for the phase of parity `parity`; false after 2 s of %globaltimer.
+__device__ __noinline__ bool lu_mbar_wait(uint32_t bar, uint32_t parity) {
+  if (lu_mbar_try(bar, parity)) return true;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t it = 1;; ++it) {
+    if (lu_mbar_try(bar, parity)) return true;
+    if ((it & 63u) == 0u) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 2000000000ull) return false;
+    }
+  }
+}
+
 // Panel rows [j0, n) x columns [j0, j0 + nbp) (nbp <= 32), resident in the
 // shared memory of a cluster of C blocks for the whole factorisation: block c
 // holds panel rows [c RS, c RS + RS) (counted from j0), row-major, row rr at
 // Sp + rr * pitch (lu_slab_pitch: rows of 16-byte multiples whose quarter
-// warps touch distinct banks).  Per column q, one cluster barrier:
+// warps touch distinct banks).  Per column q:
 //   every block finds its candidate (largest |a| in column q among its rows
 //   below q, the first such row on ties; tracked during the previous
-//   column's update) and publishes it, the candidate's row and, from the
-//   block holding it, row q;
-//   after the barrier every block reads, in one round, all C candidates,
-//   their rows and row q, and reduces the candidates in the same order to
-//   the pivot row p.  The block holding q writes the pivot row there; the
-//   thread holding row p writes row q's values into it while it updates it;
-//   every block scales its rows below q by the pivot's reciprocal (as
-//   LAPACK's unblocked factorisation and HPL scale; by the pivot itself when
-//   the reciprocal would overflow) and updates the rest of them: a row's
-//   values are loaded as float4 before any is stored, and the pivot row is
-//   held in registers, zero up to column q + 1.
-// Published values are double-buffered by the parity of q: a buffer is
-// rewritten two columns later, after a barrier every reader has passed.
+//   column's update) and pushes it, with the candidate's row and, from the
+//   block holding it, row q, into every block's receive buffers with remote
+//   stores that complete bytes on the receiver's mbarrier;
+//   each block waits on its own mbarrier (no cluster-wide barrier), reduces
+//   the C candidates in the same order to the pivot row p, and takes its
+//   values from its buffers.  The block holding q writes the pivot row
+//   there; the thread holding row p writes row q's values into it while it
+//   updates it; every block scales its rows below q by the pivot's
+//   reciprocal (as LAPACK's unblocked factorisation and HPL scale; by the
+//   pivot itself when the reciprocal would overflow) and updates the rest of
+//   them: a row's values are loaded as float4 before any is stored, and the
+//   pivot row is held in registers.
+// The receive buffers and their mbarriers alternate with the parity of q.  A
+// buffer is refilled for column q + 2 only by a block that has received
+// every block's column q + 1 values, which each block sends after it has
+// finished column q: no buffer is overwritten before it has been read.  A
+// wait that runs out (2 s) sets *status, and the block stops factoring but
+// still reaches the final cluster barrier, so no block leaves while another
+// may still write to it.
 __global__ void __launch_bounds__(kPanelThreads, 1)
     lu_panel_kernel(int n, float* __restrict__ A, int64_t lda, int j0, int nbp, int RS, int pitch,
-                    int* __restrict__ ipiv, int* __restrict__ info, int* __restrict__ perm) {
+                    int* __restrict__ ipiv, int* __restrict__ info, int* __restrict__ perm, int* __restrict__ status) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int c = (int)cl.block_rank();
   extern __shared__ float4 Sp4[];
   float* Sp = reinterpret_cast<float*>(Sp4);
   __shared__ MaxLoc red[2][33];
-  __shared__ MaxLoc pub_cand[2];
-  __shared__ __align__(16) float pub_row[2][kLuPanelNb];  // the candidate's row
-  __shared__ __align__(16) float pub_q[2][kLuPanelNb];    // row q, from the block holding it
-  __shared__ int sh_p, sh_w;
-  __shared__ __align__(16) float rows_all[kLuPanelCluster][kLuPanelNb];
-  __shared__ __align__(16) float qrow[kLuPanelNb];
+  __shared__ __align__(8) MaxLoc rx_cand[2][kLuPanelCluster];               // from each block
+  __shared__ __align__(16) float rx_row[2][kLuPanelCluster][kLuPanelNb];   // each candidate's row
+  __shared__ __align__(16) float rx_q[2][kLuPanelNb];                      // row q
+  __shared__ __align__(8) uint64_t rx_bar[2];
   __shared__ int piv_s[kLuPanelNb];
   __shared__ int prow_s[2 * kLuPanelNb], pcont_s[2 * kLuPanelNb];
   const int tid = threadIdx.x;
@@ -169,63 +227,103 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   const int nr = max(0, min(R, rlo + RS) - rlo);  // rows of this block's slab
   const bool vec = nbp > 2;                       // rows in float4 groups
   const int groups = (nbp + 3) / 4;
+  const int row_bytes = vec ? 16 * groups : 4 * nbp;
+  // bytes other blocks push for column q: a candidate and its row from each,
+  // and row q unless this block holds it (a block writes its own values
+  // into its buffers with plain stores)
+  auto rx_bytes = [&](int q) -> uint32_t {
+    return (uint32_t)((C - 1) * (8 + row_bytes) + (q / RS == c ? 0 : row_bytes));
+  };
   float* G = A + j0 + (int64_t)j0 * lda;
+  if (tid == 0) {
+    lu_mbar_init(lu_smem(&rx_bar[0]));
+    lu_mbar_init(lu_smem(&rx_bar[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    lu_mbar_arm(lu_smem(&rx_bar[0]), rx_bytes(0));
+    if (nbp > 1) lu_mbar_arm(lu_smem(&rx_bar[1]), rx_bytes(1));
+  }
   for (int q = 0; q < nbp; ++q) {
 #pragma unroll 4
     for (int rr = tid; rr < nr; rr += kPanelThreads) Sp[rr * pitch + q] = G[(rlo + rr) + (int64_t)q * lda];
   }
-  __syncthreads();
+  cl.sync();  // every block's mbarriers are initialised before any value is pushed
   float best = -1.f;
   int bi = INT_MAX;  // candidate as a panel row
   for (int rr = tid; rr < nr; rr += kPanelThreads) {
     const float v = fabsf(Sp[rr * pitch]);
     if (v > best) { best = v; bi = rlo + rr; }  // rows ascend: the first maximum stays
   }
-  for (int q = 0; q < nbp; ++q) {
+  bool ok = true;
+  for (int q = 0; q < nbp && ok; ++q) {
     const int par = q & 1;
     const MaxLoc m = block_argmax(best, bi, red[par]);
-    if (tid == 0) pub_cand[par] = m;
-    if (tid < nbp) {
-      if (m.i != INT_MAX) pub_row[par][tid] = Sp[(m.i - rlo) * pitch + tid];
-      if (q >= rlo && q < rlo + nr) pub_q[par][tid] = Sp[(q - rlo) * pitch + tid];
-    }
-    cl.sync();
     const int oq = q / RS;  // the block holding row q
-    // one round of remote reads: every candidate's row and row q; warp 0 also
-    // reads the candidates and reduces them (the same order in every block:
-    // the same pivot) while the others load
-    for (int e = tid; e < C * kLuPanelNb + kLuPanelNb; e += kPanelThreads) {
-      const int r = e / kLuPanelNb, col = e % kLuPanelNb;
-      if (col < nbp) {
-        if (r < C)
-          rows_all[r][col] = *cl.map_shared_rank(&pub_row[par][col], r);
+    // push: warp d sends to block d; lane 0 the candidate, lanes 1 .. the
+    // candidate's row, the following lanes row q (from the block holding it)
+    if (tid < 32 * C) {
+      const int d = tid >> 5, l = tid & 31;
+      const bool self = d == c;
+      const uint32_t rbar = self ? 0u : lu_mapa(lu_smem(&rx_bar[par]), d);
+      const int nchunk = vec ? groups : nbp;
+      if (l == 0) {
+        if (self)
+          rx_cand[par][c] = m;
         else
-          qrow[col] = *cl.map_shared_rank(&pub_q[par][col], oq);
+          lu_push2(lu_mapa(lu_smem(&rx_cand[par][c]), d), __float_as_uint(m.v), (uint32_t)m.i, rbar);
+      } else if (l <= nchunk) {
+        const int k = l - 1;
+        const float* src = Sp + (m.i != INT_MAX ? (m.i - rlo) : 0) * pitch;  // any row when there is no candidate
+        if (vec) {
+          const float4 v = reinterpret_cast<const float4*>(src)[k];
+          if (self)
+            reinterpret_cast<float4*>(rx_row[par][c])[k] = v;
+          else
+            lu_push4(lu_mapa(lu_smem(&rx_row[par][c][4 * k]), d), v, rbar);
+        } else {
+          if (self)
+            rx_row[par][c][k] = src[k];
+          else
+            lu_push1(lu_mapa(lu_smem(&rx_row[par][c][k]), d), src[k], rbar);
+        }
+      } else if (l <= 2 * nchunk && c == oq) {
+        const int k = l - 1 - nchunk;
+        const float* src = Sp + (q - rlo) * pitch;
+        if (vec) {
+          const float4 v = reinterpret_cast<const float4*>(src)[k];
+          if (self)
+            reinterpret_cast<float4*>(rx_q[par])[k] = v;
+          else
+            lu_push4(lu_mapa(lu_smem(&rx_q[par][4 * k]), d), v, rbar);
+        } else {
+          if (self)
+            rx_q[par][k] = src[k];
+          else
+            lu_push1(lu_mapa(lu_smem(&rx_q[par][k]), d), src[k], rbar);
+        }
       }
     }
-    if (tid < 32) {
-      MaxLoc mm{-1.f, INT_MAX};
-      int who = -1;
-      if (tid < C) {
-        mm = *cl.map_shared_rank(&pub_cand[par], tid);
-        who = tid;
-      }
+    const bool got = lu_mbar_wait(lu_smem(&rx_bar[par]), (uint32_t)((q >> 1) & 1));
+    ok = __syncthreads_and(got) != 0;  // the same decision in every thread; every thread has seen the phase ...
+    if (!ok) {
+      if (tid == 0) atomicCAS(status, 0, GBGEMM_ERR_DEVICE_TIMEOUT);
+      break;
+    }
+    // ... before it is re-armed, by a thread with no global stores of its own
+    // to wait for (the arrive releases the arriving thread's earlier writes)
+    if (tid == kPanelThreads - 1 && q + 2 < nbp) lu_mbar_arm(lu_smem(&rx_bar[par]), rx_bytes(q + 2));
+    MaxLoc w{-1.f, INT_MAX};
+    int wr = -1;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float v2 = __shfl_xor_sync(0xFFFFFFFFu, mm.v, o);
-        const int i2 = __shfl_xor_sync(0xFFFFFFFFu, mm.i, o);
-        const int w2 = __shfl_xor_sync(0xFFFFFFFFu, who, o);
-        if (v2 > mm.v || (v2 == mm.v && i2 < mm.i)) { mm.v = v2; mm.i = i2; who = w2; }
-      }
-      if (tid == 0) {
-        sh_p = (mm.i == INT_MAX) ? q : mm.i;  // (a column of NaNs keeps its row)
-        sh_w = (mm.i == INT_MAX) ? -1 : who;
+    for (int r = 0; r < kLuPanelCluster; ++r) {  // the same order in every block: the same pivot
+      if (r < C) {
+        const MaxLoc x = rx_cand[par][r];
+        if (x.v > w.v || (x.v == w.v && x.i < w.i)) { w = x; wr = r; }
       }
     }
-    __syncthreads();
-    const int p = sh_p;
-    const float* prow = sh_w < 0 ? qrow : rows_all[sh_w];
-    if (c == 0 && tid == 0) {
+    const int p = (w.i == INT_MAX) ? q : w.i;  // (a column of NaNs keeps its row)
+    const float* qrow = rx_q[par];
+    const float* prow = (w.i == INT_MAX) ? qrow : rx_row[par][wr];
+    if (c == 0 && tid == kPanelThreads - 2) {
       ipiv[j0 + q] = j0 + p + 1;
       piv_s[q] = j0 + p;
     }
@@ -289,12 +387,32 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
             row[q + 1] = v1;
             if (fabsf(v1) > best) { best = fabsf(v1); bi = rlo + rr; }
           }
-        } else {  // row p: receives row q's values, updated
+        } else {  // row p: receives row q's values, updated beyond column q
           const float a = qrow[q];
           const float l = use_rcp ? a * rcp : a / d;
-          for (int k = 0; k < nbp; ++k) row[k] = k > q ? fmaf(-l, prow[k], qrow[k]) : qrow[k];
+          float v1 = 0.f;
+          if (vec) {
+            float4 x[kLuPanelNb / 4];  // every load issued before any store
+#pragma unroll
+            for (int j = 0; j < kLuPanelNb / 4; ++j)
+              if (j < groups) x[j] = reinterpret_cast<const float4*>(qrow)[j];
+#pragma unroll
+            for (int j = 0; j < kLuPanelNb / 4; ++j) {
+              if (j < groups) {
+                if (4 * j + 0 > q) x[j].x = fmaf(-l, u[j].x, x[j].x);
+                if (4 * j + 1 > q) x[j].y = fmaf(-l, u[j].y, x[j].y);
+                if (4 * j + 2 > q) x[j].z = fmaf(-l, u[j].z, x[j].z);
+                if (4 * j + 3 > q) x[j].w = fmaf(-l, u[j].w, x[j].w);
+                reinterpret_cast<float4*>(row)[j] = x[j];
+              }
+            }
+            if (q + 1 < nbp) v1 = row[q + 1];
+          } else {
+            for (int k = 0; k < nbp; ++k) row[k] = k > q ? fmaf(-l, prow[k], qrow[k]) : qrow[k];
+            if (q + 1 < nbp) v1 = row[q + 1];
+          }
           row[q] = l;
-          if (q + 1 < nbp && fabsf(row[q + 1]) > best) { best = fabsf(row[q + 1]); bi = rlo + rr; }
+          if (q + 1 < nbp && fabsf(v1) > best) { best = fabsf(v1); bi = rlo + rr; }
         }
       }
     }
@@ -476,7 +594,7 @@ int lu_panel_width(int rows) {
 }
 
 cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,
-                            cudaStream_t s) {
+                            int* status, cudaStream_t s) {
   if (nbp <= 0 || nbp > kLuPanelNb) return cudaErrorInvalidValue;
   const int R = n - j0;
   const int pitch = lu_slab_pitch(nbp);
@@ -498,7 +616,7 @@ cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm);
+  return cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm, status);
 }
 
 cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStream_t s) {
