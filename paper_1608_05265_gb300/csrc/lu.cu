@@ -58,7 +58,7 @@ __device__ __forceinline__ void maxloc_merge(float& v, int& i, float v2, int i2)
 
 // Largest v over the block (smallest i on ties), returned to every thread.
 // Callers alternate between two `red` buffers, so no closing barrier is needed.
-__device__ MaxLoc block_argmax(float v, int i, MaxLoc* red) {
+__device__ __forceinline__ MaxLoc block_argmax(float v, int i, MaxLoc* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) maxloc_merge(v, i, __shfl_xor_sync(0xFFFFFFFFu, v, o), __shfl_xor_sync(0xFFFFFFFFu, i, o));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   float* Sp = reinterpret_cast<float*>(Sp4);
   __shared__ MaxLoc red[2][33];
   __shared__ __align__(8) MaxLoc rx_cand[2][kLuPanelCluster];               // from each block
-  __shared__ __align__(16) float rx_row[2][kLuPanelCluster][kLuPanelNb];   // each candidate's row
-  __shared__ __align__(16) float rx_q[2][kLuPanelNb];                      // row q
+  // rows received: each block's candidate row, then (slot kLuPanelCluster) row q
+  __shared__ __align__(16) float rx_row[2][kLuPanelCluster + 1][kLuPanelNb];
   __shared__ __align__(8) uint64_t rx_bar[2];
   __shared__ int piv_s[kLuPanelNb];
   __shared__ int prow_s[2 * kLuPanelNb], pcont_s[2 * kLuPanelNb];
@@ -291,14 +291,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         if (vec) {
           const float4 v = reinterpret_cast<const float4*>(src)[k];
           if (self)
-            reinterpret_cast<float4*>(rx_q[par])[k] = v;
+            reinterpret_cast<float4*>(rx_row[par][kLuPanelCluster])[k] = v;
           else
-            lu_push4(lu_mapa(lu_smem(&rx_q[par][4 * k]), d), v, rbar);
+            lu_push4(lu_mapa(lu_smem(&rx_row[par][kLuPanelCluster][4 * k]), d), v, rbar);
         } else {
           if (self)
-            rx_q[par][k] = src[k];
+            rx_row[par][kLuPanelCluster][k] = src[k];
           else
-            lu_push1(lu_mapa(lu_smem(&rx_q[par][k]), d), src[k], rbar);
+            lu_push1(lu_mapa(lu_smem(&rx_row[par][kLuPanelCluster][k]), d), src[k], rbar);
         }
       }
     }
@@ -321,8 +321,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       }
     }
     const int p = (w.i == INT_MAX) ? q : w.i;  // (a column of NaNs keeps its row)
-    const float* qrow = rx_q[par];
-    const float* prow = (w.i == INT_MAX) ? qrow : rx_row[par][wr];
+    const int ps = (w.i == INT_MAX) ? kLuPanelCluster : wr;  // the pivot row's slot
+    float* const qrow = rx_row[par][kLuPanelCluster];
+    float* const prow = rx_row[par][ps];
     if (c == 0 && tid == kPanelThreads - 2) {
       ipiv[j0 + q] = j0 + p + 1;
       piv_s[q] = j0 + p;
