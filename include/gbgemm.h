@@ -177,7 +177,7 @@ int gbgemm_sgemv(gbgemm_handle* h, char trans, int64_t m, int64_t n, float alpha
  * GBGEMM_SGETRF_WIDE_N and GBGEMM_SGETRF_MAX_NB from there (the faster of the
  * two measured at N 4608, 8192 and 16384 on GB300).  Each block of nb
  * columns is factored as panels of at most 32 columns (narrower when the
- * panel's rows outgrow the shared memory of a cluster of 8 thread blocks,
+ * panel's rows outgrow the shared memory of a cluster of 16 thread blocks,
  * which holds a panel for its whole factorisation), the exchanges and
  * triangular solves of each panel applied across the block and the block
  * columns updated with k = the panel width; after the block, the whole

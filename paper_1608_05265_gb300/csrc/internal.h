@@ -48,7 +48,7 @@ constexpr int kLuPanelNb = 32;      // columns per panel inside a block
 // (when *info is 0) and the panel's row permutation into perm; a wait between
 // the cluster's blocks that runs out sets *status.  nbp must not
 // exceed lu_panel_width(n - j0), the widest panel whose rows fit.
-constexpr int kLuPanelCluster = 8;
+constexpr int kLuPanelCluster = 16;  // largest cluster (8 is the portable size)
 constexpr int kLuPanelSlabBytes = 192 * 1024;
 int lu_panel_width(int rows);
 cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,

@@ -6,7 +6,7 @@
 // Right-looking, blocked by nb columns; each block is factored as panels of
 // at most 32 columns:
 //   panel    rows [j1, n) x the panel's columns, held in the shared memory
-//            of a cluster of up to 8 blocks for the whole factorisation
+//            of a cluster of up to 16 blocks for the whole factorisation
 //            (lu_panel_kernel): per column one cluster barrier, one round of
 //            distributed-shared-memory reads, the pivot (first row of largest
 //            |a|) chosen identically in every block, the exchange and the
@@ -39,7 +39,8 @@ namespace gbg {
 namespace {
 
 constexpr int kPanelThreads = 512;  // per block of the panel's cluster
-static_assert(kPanelThreads - 2 >= 32 * kLuPanelCluster, "the last two threads never push");
+constexpr int kPushLanes = 1 + 2 * (kLuPanelNb / 4);  // threads sending to one block: candidate, its row, row q
+static_assert(kPanelThreads - 2 >= kPushLanes * kLuPanelCluster, "the last two threads never push");
 constexpr int kTrsmCols = 64;     // columns per block of the swap + triangular solve kernel
 constexpr int kSwapThreads = 256;  // its threads (the first kTrsmCols solve one column each)
 constexpr int kXP = kTrsmCols + 1;
@@ -258,10 +259,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     const int par = q & 1;
     const MaxLoc m = block_argmax(best, bi, red[par]);
     const int oq = q / RS;  // the block holding row q
-    // push: warp d sends to block d; lane 0 the candidate, lanes 1 .. the
-    // candidate's row, the following lanes row q (from the block holding it)
-    if (tid < 32 * C) {
-      const int d = tid >> 5, l = tid & 31;
+    // push: threads [d kPushLanes, (d + 1) kPushLanes) send to block d: the
+    // first the candidate, the next ones the candidate's row, the following
+    // ones row q (from the block holding it)
+    if (tid < kPushLanes * C) {
+      const int d = tid / kPushLanes, l = tid % kPushLanes;
       const bool self = d == c;
       const uint32_t rbar = self ? 0u : lu_mapa(lu_smem(&rx_bar[par]), d);
       const int nchunk = vec ? groups : nbp;
@@ -600,24 +602,39 @@ cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* 
   const int R = n - j0;
   const int pitch = lu_slab_pitch(nbp);
   const int cap = kLuPanelSlabBytes / (4 * pitch);  // slab rows a block holds
-  const int C = R <= 256 ? 1 : kLuPanelCluster;
-  const int RS = (R + C - 1) / C;
-  if (RS > cap) return cudaErrorInvalidValue;
+  // one block up to 256 rows; 8 while a block's slab has at most 512 rows
+  // (a row per thread), else 16 (a cluster size the GPU allows by opt-in)
+  int C = R <= 256 ? 1 : ((R + 7) / 8 <= kPanelThreads ? 8 : kLuPanelCluster);
   cudaError_t e = set_smem_once((const void*)lu_panel_kernel, 0, kLuPanelSlabBytes);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C, 1, 1);
-  cfg.blockDim = dim3(kPanelThreads, 1, 1);
-  cfg.dynamicSmemBytes = (size_t)RS * pitch * sizeof(float);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm, status);
+  static bool wide_set[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !wide_set[dev]) {
+    e = cudaFuncSetAttribute((const void*)lu_panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    wide_set[dev] = true;
+  }
+  for (;;) {
+    const int RS = (R + C - 1) / C;
+    if (RS > cap) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kPanelThreads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)RS * pitch * sizeof(float);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm, status);
+    if (e == cudaSuccess || C != kLuPanelCluster) return e;
+    cudaGetLastError();  // a cluster of 16 could not be launched: 8, if the rows fit
+    C = 8;
+  }
 }
 
 cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStream_t s) {

@@ -130,9 +130,10 @@ def test_hpl_size_of_the_paper(h):
         assert O.hpl_residual(A, X[r], B[r].astype(np.float64), EPS32) < 16
 
 
-def test_cluster_of_eight(h):
-    """n = 6400: every panel spread over a cluster of eight blocks, rows in
-    slabs of 800 (the last ones of the factorisation on a single block)."""
+def test_cluster_sizes(h):
+    """n = 6400: panels on clusters of 16 blocks while a block of 8 would
+    hold more than 512 rows, then of 8, and on a single block for the last
+    256 rows."""
     n = 6400
     Af = synth.uniform_matrix(6400, 0, n, n, n)
     A = synth.logical(Af, n, n, n).astype(np.float64)
@@ -145,17 +146,17 @@ def test_cluster_of_eight(h):
 
 
 def test_narrow_panels_for_tall_matrices(h):
-    """n = 12800: more panel rows than 32-column panels fit in the cluster's
-    shared memory, so the first blocks are factored as 16-column panels.
-    Checked by HPL's scaled residual (the O(n^3) factor residual is left to
-    the smaller cases)."""
-    n = 12800
-    Af = synth.uniform_matrix(12800, 0, n, n, n)
+    """n = 22000: more panel rows than 32-column panels fit in the shared
+    memory of a cluster of 16 blocks (21840), so the first block is factored
+    as 16-column panels.  Checked by HPL's scaled residual (the O(n^3) factor
+    residual is left to the smaller cases)."""
+    n = 22000
+    Af = synth.uniform_matrix(22000, 0, n, n, n)
     lu, ipiv, info, out = factor(h, Af, n, n, 128)
     assert info == 0
     assert all(j + 1 <= p <= n for j, p in enumerate(ipiv))
     A = synth.logical(Af, n, n, n).astype(np.float64)
-    b = synth.uniform_pm1(synth.draws(12800, 5, n)).astype(np.float32)
+    b = synth.uniform_pm1(synth.draws(22000, 5, n)).astype(np.float32)
     x = solve(h, out, n, n, ipiv, b)
     assert O.hpl_residual(A, x, b.astype(np.float64), EPS32) < 16
 
