@@ -516,30 +516,67 @@ __global__ void __launch_bounds__(256) lu_laswp_rhs_kernel(int n, const int* __r
   }
 }
 
+// Strip t of a diagonal block of w rows holds its columns [32t, 32t + 32)
+// (fewer in the last strip), column-major, rows [32t, w) for the lower
+// triangle or [0, 32t + 32) for the upper one: the entries a triangular
+// solve reads, packed.
+__device__ __forceinline__ int strip_rows(bool upper, int w, int t) {
+  const int ws = min(32, w - 32 * t);
+  return upper ? 32 * t + ws : w - 32 * t;
+}
+
 // One diagonal block of the triangular solves, rows [j0, j0 + w) (w <= 256)
 // of one right-hand side per block: forward substitution with the unit lower
-// triangle (UPPER false) or back substitution with the upper one (UPPER true),
-// in steps of 32 rows, each 32 x 32 triangle solved by one warp from
-// registers and the rest of the block updated by all threads.
+// triangle (UPPER false) or back substitution with the upper one (UPPER true).
+// The triangle is first copied into shared memory (4-byte asynchronous
+// copies, all in flight at once, no alignment needed), then solved in steps
+// of 32 rows: each 32 x 32 triangle by one warp from registers, the rest of
+// the block by all threads.
 template <bool UPPER>
 __global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float* __restrict__ LU, int64_t lda, int j0,
                                                                    int w, float* __restrict__ B, int64_t ldb) {
+  extern __shared__ float tri[];  // the packed strips
   __shared__ float ys[kSolveBlock];
+  __shared__ int soff[kSolveBlock / 32 + 1];
   float* b = B + (int64_t)blockIdx.x * ldb + j0;
   const float* T = LU + j0 + (int64_t)j0 * lda;  // the diagonal block: (i, q) at T[i + q * lda]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nsub = (w + 31) / 32;
+  if (tid == 0) {
+    int o = 0;
+    for (int t = 0; t < nsub; ++t) {
+      soff[t] = o;
+      o += min(32, w - 32 * t) * strip_rows(UPPER, w, t);
+    }
+    soff[nsub] = o;
+  }
   if (tid < w) ys[tid] = b[tid];
   __syncthreads();
-  const int nsub = (w + 31) / 32;
-  for (int t = 0; t < nsub; ++t) {
-    const int s0 = UPPER ? (nsub - 1 - t) * 32 : t * 32;
+  for (int t = 0; t < nsub; ++t) {  // issue every copy, then wait once
+    const int h = strip_rows(UPPER, w, t), r0 = UPPER ? 0 : 32 * t;
+    const int cnt = min(32, w - 32 * t) * h;
+    for (int e = tid; e < cnt; e += kSolveBlock) {
+      const int col = e / h, r = e % h;
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tri + soff[t] + e);
+      const float* src = T + (r0 + r) + (int64_t)(32 * t + col) * lda;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  for (int k = 0; k < nsub; ++k) {
+    const int t = UPPER ? nsub - 1 - k : k;
+    const int s0 = 32 * t;
     const int ws = min(32, w - s0);
+    const int h = strip_rows(UPPER, w, t);
+    const float* S = tri + soff[t];  // (i, s0 + q) at S[q * h + i - (UPPER ? 0 : s0)]
+    const int ri = UPPER ? 0 : s0;
     if (warp == 0) {
       float M[32];
       float v = lane < ws ? ys[s0 + lane] : 0.f;
       if (!UPPER) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) M[q] = (q < lane && lane < ws) ? T[(s0 + lane) + (int64_t)(s0 + q) * lda] : 0.f;
+        for (int q = 0; q < 32; ++q) M[q] = (q < lane && lane < ws) ? S[q * h + lane] : 0.f;
 #pragma unroll
         for (int q = 0; q < 31; ++q) {
           const float yq = __shfl_sync(0xFFFFFFFFu, v, q);
@@ -547,7 +584,7 @@ __global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float*
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) M[q] = (lane <= q && q < ws) ? T[(s0 + lane) + (int64_t)(s0 + q) * lda] : 0.f;
+        for (int q = 0; q < 32; ++q) M[q] = (lane <= q && q < ws) ? S[q * h + s0 + lane] : 0.f;
 #pragma unroll
         for (int q = 31; q >= 0; --q) {
           if (q < ws) {
@@ -566,7 +603,7 @@ __global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float*
       float acc = ys[i];
 #pragma unroll
       for (int q = 0; q < 32; ++q)
-        if (q < ws) acc = fmaf(-T[i + (int64_t)(s0 + q) * lda], ys[s0 + q], acc);
+        if (q < ws) acc = fmaf(-S[q * h + i - ri], ys[s0 + q], acc);
       ys[i] = acc;
     }
     __syncthreads();
@@ -574,7 +611,7 @@ __global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float*
   if (tid < w) b[tid] = ys[tid];
 }
 
-bool g_attr_done[64][3];
+bool g_attr_done[64][5];
 
 cudaError_t set_smem_once(const void* fn, int which, size_t bytes) {
   int dev = 0;
@@ -676,10 +713,20 @@ cudaError_t launch_lu_trsv_block(bool upper, const float* LU, int64_t lda, int j
                                  int64_t ldb, cudaStream_t s) {
   if (w <= 0 || nrhs <= 0) return cudaSuccess;
   if (w > kSolveBlock || nrhs > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  // packed triangle: sum over strips of (columns x rows), at most 36864 floats for w = 256
+  size_t floats = 0;
+  for (int t = 0; 32 * t < w; ++t) {
+    const int ws = w - 32 * t < 32 ? w - 32 * t : 32;
+    floats += (size_t)ws * (upper ? 32 * t + ws : w - 32 * t);
+  }
+  const size_t max_bytes = (size_t)kSolveBlock * (kSolveBlock + 32) / 2 * sizeof(float);
+  cudaError_t e = set_smem_once(upper ? (const void*)lu_trsv_block_kernel<true> : (const void*)lu_trsv_block_kernel<false>,
+                                upper ? 3 : 4, max_bytes);
+  if (e != cudaSuccess) return e;
   if (upper)
-    lu_trsv_block_kernel<true><<<(unsigned)nrhs, kSolveBlock, 0, s>>>(LU, lda, j0, w, B, ldb);
+    lu_trsv_block_kernel<true><<<(unsigned)nrhs, kSolveBlock, floats * sizeof(float), s>>>(LU, lda, j0, w, B, ldb);
   else
-    lu_trsv_block_kernel<false><<<(unsigned)nrhs, kSolveBlock, 0, s>>>(LU, lda, j0, w, B, ldb);
+    lu_trsv_block_kernel<false><<<(unsigned)nrhs, kSolveBlock, floats * sizeof(float), s>>>(LU, lda, j0, w, B, ldb);
   return cudaGetLastError();
 }
 
