@@ -57,23 +57,21 @@ __device__ __forceinline__ void maxloc_merge(float& v, int& i, float v2, int i2)
   }
 }
 
-// Largest v over the block (smallest i on ties), returned to every thread.
-// Callers alternate between two `red` buffers, so no closing barrier is needed.
+// Largest v over the block (smallest i on ties), returned to every thread:
+// each warp reduces its lanes, then every warp reduces the per-warp results
+// itself (one barrier, no broadcast).  Callers alternate between two `red`
+// buffers, so no closing barrier is needed.
 __device__ __forceinline__ MaxLoc block_argmax(float v, int i, MaxLoc* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) maxloc_merge(v, i, __shfl_xor_sync(0xFFFFFFFFu, v, o), __shfl_xor_sync(0xFFFFFFFFu, i, o));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) red[warp] = MaxLoc{v, i};
   __syncthreads();
-  if (warp == 0) {
-    MaxLoc m = lane < (int)(blockDim.x >> 5) ? red[lane] : MaxLoc{-1.f, INT_MAX};
+  MaxLoc m = lane < (int)(blockDim.x >> 5) ? red[lane] : MaxLoc{-1.f, INT_MAX};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      maxloc_merge(m.v, m.i, __shfl_xor_sync(0xFFFFFFFFu, m.v, o), __shfl_xor_sync(0xFFFFFFFFu, m.i, o));
-    if (lane == 0) red[32] = m;
-  }
-  __syncthreads();
-  return red[32];
+  for (int o = 16; o > 0; o >>= 1)
+    maxloc_merge(m.v, m.i, __shfl_xor_sync(0xFFFFFFFFu, m.v, o), __shfl_xor_sync(0xFFFFFFFFu, m.i, o));
+  return m;
 }
 
 // The exchanges of pivot rows [j0, j0 + nbp) (row j0 + q with piv[q],
