@@ -39,8 +39,9 @@ namespace gbg {
 namespace {
 
 constexpr int kPanelThreads = 512;  // per block of the panel's cluster
-constexpr int kPushLanes = 1 + 2 * (kLuPanelNb / 4);  // threads sending to one block: candidate, its row, row q
-static_assert(kPanelThreads - 2 >= kPushLanes * kLuPanelCluster, "the last two threads never push");
+constexpr int kPushLanes = 1 + 2 * (kLuPanelNb / 4);  // lanes sending to one block: candidate, its row, row q
+static_assert(kPanelThreads == 32 * kLuPanelCluster && kPushLanes <= 30,
+              "a warp per destination block; the last two threads (lanes 30, 31 of the last warp) never push");
 constexpr int kTrsmCols = 64;     // columns per block of the swap + triangular solve kernel
 constexpr int kSwapThreads = 256;  // its threads (the first kTrsmCols solve one column each)
 constexpr int kXP = kTrsmCols + 1;
@@ -257,11 +258,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     const int par = q & 1;
     const MaxLoc m = block_argmax(best, bi, red[par]);
     const int oq = q / RS;  // the block holding row q
-    // push: threads [d kPushLanes, (d + 1) kPushLanes) send to block d: the
-    // first the candidate, the next ones the candidate's row, the following
-    // ones row q (from the block holding it)
-    if (tid < kPushLanes * C) {
-      const int d = tid / kPushLanes, l = tid % kPushLanes;
+    // push: warp d sends to block d: lane 0 the candidate, the next lanes the
+    // candidate's row, the following ones row q (from the block holding it)
+    if ((tid >> 5) < C && (tid & 31) < kPushLanes) {
+      const int d = tid >> 5, l = tid & 31;
       const bool self = d == c;
       const uint32_t rbar = self ? 0u : lu_mapa(lu_smem(&rx_bar[par]), d);
       const int nchunk = vec ? groups : nbp;
@@ -311,13 +311,22 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     // ... before it is re-armed, by a thread with no global stores of its own
     // to wait for (the arrive releases the arriving thread's earlier writes)
     if (tid == kPanelThreads - 1 && q + 2 < nbp) lu_mbar_arm(lu_smem(&rx_bar[par]), rx_bytes(q + 2));
+    // the pivot: every warp reduces the C candidates with shuffles (largest
+    // |a|, smallest row on ties: the same choice in every block)
     MaxLoc w{-1.f, INT_MAX};
     int wr = -1;
+    {
+      const int lane = tid & 31;
+      if (lane < C) {
+        w = rx_cand[par][lane];
+        wr = lane;
+      }
 #pragma unroll
-    for (int r = 0; r < kLuPanelCluster; ++r) {  // the same order in every block: the same pivot
-      if (r < C) {
-        const MaxLoc x = rx_cand[par][r];
-        if (x.v > w.v || (x.v == w.v && x.i < w.i)) { w = x; wr = r; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xFFFFFFFFu, w.v, o);
+        const int i2 = __shfl_xor_sync(0xFFFFFFFFu, w.i, o);
+        const int r2 = __shfl_xor_sync(0xFFFFFFFFu, wr, o);
+        if (v2 > w.v || (v2 == w.v && i2 < w.i)) { w.v = v2; w.i = i2; wr = r2; }
       }
     }
     const int p = (w.i == INT_MAX) ? q : w.i;  // (a column of NaNs keeps its row)
