@@ -401,7 +401,7 @@ int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv,
   if (cudaMemsetAsync(info, 0, sizeof(int), h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
   h->last_path = 0;
   if (n == 0) return GBGEMM_OK;
-  if (!h->d_lu_perm && cudaMalloc(&h->d_lu_perm, gbg::kLuPermInts * sizeof(int)) != cudaSuccess) {
+  if (!h->d_lu_perm && cudaMalloc(&h->d_lu_perm, 2 * gbg::kLuPermInts * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     h->d_lu_perm = nullptr;
     return GBGEMM_ERR_ALLOC;
@@ -459,6 +459,54 @@ int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv,
     h->kernel_launches += 1;
     return GBGEMM_OK;
   };
+  if (b <= gbg::kLuPanelNb && gbg::lu_panel_width((int)n) >= b) {
+    // Every block is one panel.  Look-ahead with a fused prologue: the next
+    // panel, on the side stream, applies block k's exchanges, U12 and update
+    // to its own columns itself and factors them, while the handle's stream
+    // applies block k to every other column (exchanges, U12, trailing
+    // update).  The two touch disjoint columns; the two permutation buffers
+    // alternate between the blocks.
+    int* pbuf[2] = {h->d_lu_perm, h->d_lu_perm + gbg::kLuPermInts};
+    int nbo = (int)(n < b ? n : b);
+    if (gbg::launch_lu_panel((int)n, A, lda, 0, nbo, ipiv, info, pbuf[0], h->d_status, h->stream) != cudaSuccess)
+      rc = GBGEMM_ERR_CUDA;
+    h->kernel_launches += 1;
+    int k = 0;
+    for (int64_t j0 = 0; j0 < n && rc == GBGEMM_OK; j0 += nbo, ++k) {
+      nbo = (int)(n - j0 < b ? n - j0 : b);
+      int* pk = pbuf[k & 1];
+      int* pn = pbuf[(k + 1) & 1];
+      const int64_t jn = j0 + nbo;
+      const int nbn = jn < n ? (int)(n - jn < b ? n - jn : b) : 0;
+      if (nbn > 0) {
+        if (cudaEventRecord(h->lu_ev[0], h->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(h->lu_side, h->lu_ev[0], 0) != cudaSuccess ||
+            gbg::launch_lu_panel((int)n, A, lda, (int)jn, nbn, ipiv, info, pn, h->d_status, h->lu_side, (int)j0, nbo,
+                                 pk) != cudaSuccess ||
+            cudaEventRecord(h->lu_ev[1], h->lu_side) != cudaSuccess) {
+          rc = GBGEMM_ERR_CUDA;
+          break;
+        }
+        h->kernel_launches += 1;
+      }
+      if (j0 > 0 || jn + nbn < n) {
+        if (gbg::launch_lu_swap_trsm((int)n, A, lda, (int)j0, nbo, pk, 0, (int)n, h->stream, (int)(jn + nbn)) !=
+            cudaSuccess) {
+          rc = GBGEMM_ERR_CUDA;
+          break;
+        }
+        h->kernel_launches += 1;
+      }
+      const int64_t rest = n - jn - nbn;
+      if (nbn > 0 && rest > 0) rc = update(jn, jn + nbn, n - jn, rest, j0, nbo);
+      if (rc != GBGEMM_OK) break;
+      if (nbn > 0 && cudaStreamWaitEvent(h->stream, h->lu_ev[1], 0) != cudaSuccess) rc = GBGEMM_ERR_CUDA;
+    }
+    if (rc != GBGEMM_OK && cudaEventRecord(h->lu_ev[1], h->lu_side) == cudaSuccess)
+      cudaStreamWaitEvent(h->stream, h->lu_ev[1], 0);  // never leave work on the side stream unjoined
+    h->tuning = tuning;
+    return rc;
+  }
   // Look-ahead: after block k's exchanges and U12, the next block's columns
   // are updated first; the next block is then factored on the side stream
   // while the handle's stream updates the remaining columns.  The two touch

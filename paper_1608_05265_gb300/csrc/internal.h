@@ -40,7 +40,7 @@ cudaError_t launch_scale_c_batched(int64_t m, int64_t n, float beta, float* C, i
 // ---- LU factorisation (lu.cu) ----
 constexpr int kLuMaxNb = GBGEMM_SGETRF_MAX_NB;  // widest panel
 constexpr int kLuSolveSmemN = 32768; // the row exchanges of the solve run in shared memory up to this n
-constexpr int kLuPermInts = 1 + 3 * kLuMaxNb;  // a block's row permutation
+constexpr int kLuPermInts = 1 + 3 * kLuMaxNb;  // a block's row permutation (the handle holds two)
 constexpr int kLuPanelNb = 32;      // columns per panel inside a block
 // Factor the panel rows [j0, n) x columns [j0, j0 + nbp) in place (a
 // cluster of up to kLuPanelCluster blocks holding the panel in shared
@@ -51,15 +51,19 @@ constexpr int kLuPanelNb = 32;      // columns per panel inside a block
 constexpr int kLuPanelCluster = 16;  // largest cluster (8 is the portable size)
 constexpr int kLuPanelSlabBytes = 192 * 1024;
 int lu_panel_width(int rows);
+// With jp >= 0 the panel first applies the previous block [jp, j0) (nbq
+// columns, its row permutation in perm_prev, its L factors final) to its own
+// columns: the exchanges, U12 = L11^-1 A12 (written to rows [jp, j0)) and
+// A22 -= L21 U12 for the panel rows.
 cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,
-                            int* status, cudaStream_t s);
+                            int* status, cudaStream_t s, int jp = -1, int nbq = 0, const int* perm_prev = nullptr);
 // The permutation of pivot rows [j0, j0 + nbp), rebuilt from ipiv (for a
 // block factored as several panels).
 cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStream_t s);
 // The permutation of pivot rows [j0, j0 + nbp) applied to columns [c_lo, j0)
-// and [j0 + nbp, c_hi), then U12 = L11^-1 A12 for the latter.
+// and [r_lo, c_hi) (r_lo < 0: j0 + nbp), then U12 = L11^-1 A12 for the latter.
 cudaError_t launch_lu_swap_trsm(int n, float* A, int64_t lda, int j0, int nbp, const int* perm, int c_lo, int c_hi,
-                                cudaStream_t s);
+                                cudaStream_t s, int r_lo = -1);
 // The solve with the packed factors: the row exchanges of ipiv on each of
 // nrhs columns of B, then per diagonal block of kSolveBlock rows the
 // triangular solve of that block (UPPER: back substitution with U, else

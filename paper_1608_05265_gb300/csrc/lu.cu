@@ -208,7 +208,8 @@ __device__ __noinline__ bool lu_mbar_wait(uint32_t bar, uint32_t parity) {
 // may still write to it.
 __global__ void __launch_bounds__(kPanelThreads, 1)
     lu_panel_kernel(int n, float* __restrict__ A, int64_t lda, int j0, int nbp, int RS, int pitch,
-                    int* __restrict__ ipiv, int* __restrict__ info, int* __restrict__ perm, int* __restrict__ status) {
+                    int* __restrict__ ipiv, int* __restrict__ info, int* __restrict__ perm, int* __restrict__ status,
+                    int jp, int nbq, const int* __restrict__ perm_prev) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int c = (int)cl.block_rank();
@@ -221,6 +222,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   __shared__ __align__(8) uint64_t rx_bar[2];
   __shared__ int piv_s[kLuPanelNb];
   __shared__ int prow_s[2 * kLuPanelNb], pcont_s[2 * kLuPanelNb];
+  __shared__ __align__(16) float Ux[kLuPanelNb][kLuPanelNb];      // prologue: U12 of this panel's columns
+  __shared__ float Lx[kLuPanelNb][kLuPanelNb + 1];                 // prologue: the previous block's L11
   const int tid = threadIdx.x;
   const int R = n - j0;
   const int rlo = c * RS;
@@ -246,7 +249,87 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
 #pragma unroll 4
     for (int rr = tid; rr < nr; rr += kPanelThreads) Sp[rr * pitch + q] = G[(rlo + rr) + (int64_t)q * lda];
   }
-  cl.sync();  // every block's mbarriers are initialised before any value is pushed
+  if (jp >= 0) {
+    // Prologue: the previous block [jp, j0) (nbq columns, its exchanges in
+    // perm_prev) has not yet touched this panel's columns.  (a) Slab rows
+    // that its exchanges replaced take their new values; (b) every block
+    // solves U12 = L11^-1 (the block's rows, exchanged) for this panel's
+    // columns; (c) the slab rows get A -= L21 U12.  Only original values of
+    // A are read here; U12 is written back after the cluster barrier below.
+    const int nx = perm_prev[0];
+    const int* psrc = perm_prev + 1;
+    const int* pext = perm_prev + 1 + nbq;
+    __syncthreads();
+    for (int e = tid; e < nx * nbp; e += kPanelThreads) {
+      const int x = e / nbp, k = e % nbp;
+      const int r = pext[2 * x] - j0 - rlo;
+      if (r >= 0 && r < nr) Sp[r * pitch + k] = A[pext[2 * x + 1] + (int64_t)(j0 + k) * lda];
+    }
+    for (int e = tid; e < nbq * kLuPanelNb; e += kPanelThreads) {
+      const int qq = e / kLuPanelNb, k = e % kLuPanelNb;
+      Ux[qq][k] = k < nbp ? A[psrc[qq] + (int64_t)(j0 + k) * lda] : 0.f;
+    }
+    for (int e = tid; e < nbq * nbq; e += kPanelThreads) {
+      const int i = e % nbq, p2 = e / nbq;
+      Lx[i][p2] = A[(jp + i) + (int64_t)(jp + p2) * lda];
+    }
+    __syncthreads();
+    if (tid < nbp)  // one thread per column, rows in order (unit lower L11)
+      for (int i = 1; i < nbq; ++i) {
+        float acc = Ux[i][tid];
+        for (int p2 = 0; p2 < i; ++p2) acc = fmaf(-Lx[i][p2], Ux[p2][tid], acc);
+        Ux[i][tid] = acc;
+      }
+    __syncthreads();
+    for (int rr = tid; rr < nr; rr += kPanelThreads) {
+      const float* lrow = A + (j0 + rlo + rr) + (int64_t)jp * lda;  // L21, row j0 + rlo + rr
+      float l[kLuPanelNb];
+#pragma unroll
+      for (int qq = 0; qq < kLuPanelNb; ++qq) l[qq] = qq < nbq ? lrow[(int64_t)qq * lda] : 0.f;
+      float* row = Sp + rr * pitch;
+      if (vec) {
+        for (int h = 0; h < 2; ++h) {  // two halves of the row's float4 groups (registers)
+          float4 x[kLuPanelNb / 8];
+#pragma unroll
+          for (int j = 0; j < kLuPanelNb / 8; ++j)
+            if (4 * h + j < groups) x[j] = reinterpret_cast<const float4*>(row)[4 * h + j];
+#pragma unroll
+          for (int qq = 0; qq < kLuPanelNb; ++qq) {
+            if (qq < nbq) {
+              const float lq = l[qq];
+#pragma unroll
+              for (int j = 0; j < kLuPanelNb / 8; ++j)
+                if (4 * h + j < groups) {
+                  const float4 u4 = reinterpret_cast<const float4*>(Ux[qq])[4 * h + j];
+                  x[j].x = fmaf(-lq, u4.x, x[j].x);
+                  x[j].y = fmaf(-lq, u4.y, x[j].y);
+                  x[j].z = fmaf(-lq, u4.z, x[j].z);
+                  x[j].w = fmaf(-lq, u4.w, x[j].w);
+                }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < kLuPanelNb / 8; ++j)
+            if (4 * h + j < groups) reinterpret_cast<float4*>(row)[4 * h + j] = x[j];
+        }
+      } else {
+        for (int k = 0; k < nbp; ++k) {
+          float acc = row[k];
+#pragma unroll
+          for (int qq = 0; qq < kLuPanelNb; ++qq)
+            if (qq < nbq) acc = fmaf(-l[qq], Ux[qq][k], acc);
+          row[k] = acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cl.sync();  // every block's mbarriers are initialised before any value is pushed; prologue reads done
+  if (jp >= 0 && c == 0)  // U12 of this panel's columns, rows [jp, j0)
+    for (int e = tid; e < nbq * nbp; e += kPanelThreads) {
+      const int qq = e / nbp, k = e % nbp;
+      A[(jp + qq) + (int64_t)(j0 + k) * lda] = Ux[qq][k];
+    }
   float best = -1.f;
   int bi = INT_MAX;  // candidate as a panel row
   for (int rr = tid; rr < nr; rr += kPanelThreads) {
@@ -441,7 +524,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
 // left range.
 __global__ void __launch_bounds__(kSwapThreads) lu_swap_trsm_kernel(int n, float* __restrict__ A, int64_t lda, int j0,
                                                                  int nbp, const int* __restrict__ perm, int c_lo,
-                                                                 int c_hi, int left_tiles) {
+                                                                 int r_lo, int c_hi, int left_tiles) {
   extern __shared__ float sm[];
   const int next = perm[0];
   const int* src = perm + 1;
@@ -450,7 +533,7 @@ __global__ void __launch_bounds__(kSwapThreads) lu_swap_trsm_kernel(int n, float
   float* W = V + nbp * kXP;        // extra rows: W[x * kXP + col]
   float* Ls = W + nbp * kXP;       // L11: Ls[i * (nbp + 1) + p]
   const bool left = (int)blockIdx.x < left_tiles;
-  const int c0 = left ? c_lo + (int)blockIdx.x * kTrsmCols : j0 + nbp + ((int)blockIdx.x - left_tiles) * kTrsmCols;
+  const int c0 = left ? c_lo + (int)blockIdx.x * kTrsmCols : r_lo + ((int)blockIdx.x - left_tiles) * kTrsmCols;
   const int cend = left ? min(c0 + kTrsmCols, j0) : min(c0 + kTrsmCols, c_hi);
   const int ncol = cend - c0;
   const int tid = threadIdx.x;
@@ -641,7 +724,8 @@ int lu_panel_width(int rows) {
 }
 
 cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* ipiv, int* info, int* perm,
-                            int* status, cudaStream_t s) {
+                            int* status, cudaStream_t s, int jp, int nbq, const int* perm_prev) {
+  if (jp >= 0 && (nbq <= 0 || nbq > kLuPanelNb || jp + nbq != j0 || !perm_prev)) return cudaErrorInvalidValue;
   if (nbp <= 0 || nbp > kLuPanelNb) return cudaErrorInvalidValue;
   const int R = n - j0;
   const int pitch = lu_slab_pitch(nbp);
@@ -674,7 +758,8 @@ cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm, status);
+    e = cudaLaunchKernelEx(&cfg, lu_panel_kernel, n, A, lda, j0, nbp, RS, pitch, ipiv, info, perm, status, jp, nbq,
+                           perm_prev);
     if (e == cudaSuccess || C != kLuPanelCluster) return e;
     cudaGetLastError();  // a cluster of 16 could not be launched: 8, if the rows fit
     C = 8;
@@ -688,18 +773,19 @@ cudaError_t launch_lu_perm(int j0, int nbp, const int* ipiv, int* perm, cudaStre
 }
 
 cudaError_t launch_lu_swap_trsm(int n, float* A, int64_t lda, int j0, int nbp, const int* perm, int c_lo, int c_hi,
-                                cudaStream_t s) {
-  if (nbp <= 0 || nbp > kLuMaxNb || c_lo < 0 || c_lo > j0 || c_hi < j0 + nbp || c_hi > n)
+                                cudaStream_t s, int r_lo) {
+  if (r_lo < 0) r_lo = j0 + nbp;
+  if (nbp <= 0 || nbp > kLuMaxNb || c_lo < 0 || c_lo > j0 || r_lo < j0 + nbp || c_hi < r_lo || c_hi > n)
     return cudaErrorInvalidValue;
   const int left_tiles = (j0 - c_lo + kTrsmCols - 1) / kTrsmCols;
-  const int right_tiles = (c_hi - j0 - nbp + kTrsmCols - 1) / kTrsmCols;
+  const int right_tiles = (c_hi - r_lo + kTrsmCols - 1) / kTrsmCols;
   if (left_tiles + right_tiles == 0) return cudaSuccess;
   const size_t max_smem = ((size_t)2 * kLuMaxNb * kXP + (size_t)kLuMaxNb * (kLuMaxNb + 1)) * sizeof(float);
   cudaError_t e = set_smem_once((const void*)lu_swap_trsm_kernel, 1, max_smem);
   if (e != cudaSuccess) return e;
   const size_t smem = ((size_t)2 * nbp * kXP + (size_t)nbp * (nbp + 1)) * sizeof(float);
-  lu_swap_trsm_kernel<<<left_tiles + right_tiles, kSwapThreads, smem, s>>>(n, A, lda, j0, nbp, perm, c_lo, c_hi,
-                                                                         left_tiles);
+  lu_swap_trsm_kernel<<<left_tiles + right_tiles, kSwapThreads, smem, s>>>(n, A, lda, j0, nbp, perm, c_lo, r_lo,
+                                                                           c_hi, left_tiles);
   return cudaGetLastError();
 }
 
