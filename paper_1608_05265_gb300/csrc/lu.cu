@@ -732,6 +732,7 @@ cudaError_t launch_lu_panel(int n, float* A, int64_t lda, int j0, int nbp, int* 
   const int cap = kLuPanelSlabBytes / (4 * pitch);  // slab rows a block holds
   // one block up to 256 rows; 8 while a block's slab has at most 512 rows
   // (a row per thread), else 16 (a cluster size the GPU allows by opt-in)
+  // (one block for more rows, two or three a thread, measured slower than the cluster's exchange)
   int C = R <= 256 ? 1 : ((R + 7) / 8 <= kPanelThreads ? 8 : kLuPanelCluster);
   cudaError_t e = set_smem_once((const void*)lu_panel_kernel, 0, kLuPanelSlabBytes);
   if (e != cudaSuccess) return e;
