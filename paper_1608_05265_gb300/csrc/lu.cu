@@ -7,25 +7,29 @@
 // at most 32 columns:
 //   panel    rows [j1, n) x the panel's columns, held in the shared memory
 //            of a cluster of up to 16 blocks for the whole factorisation
-//            (lu_panel_kernel): per column one cluster barrier, one round of
-//            distributed-shared-memory reads, the pivot (first row of largest
-//            |a|) chosen identically in every block, the exchange and the
-//            rank-1 update done locally.  The panel's exchanges are written
-//            out as a permutation of the rows they touch.
-//   swap+U12 the other columns of the block get that permutation (one gather
-//            per column: all sources read before any row is written), and
-//            right of the panel U12 = L11^-1 A12 is solved in shared memory
-//            (lu_swap_trsm_kernel); the block columns right of the panel are
-//            updated by the library's sgemm.
+//            (lu_panel_kernel): per column a block argmax, one exchange of
+//            candidates between the blocks (remote stores completing on the
+//            receivers' mbarriers), the pivot (first row of largest |a|)
+//            chosen identically in every block, the exchange and the rank-1
+//            update done locally.  The panel's exchanges are written out as
+//            a permutation of the rows they touch.  When every block is one
+//            panel, the kernel first applies the previous block to its own
+//            columns (a prologue: exchanges, U12, update).
+//   swap+U12 the other columns get that permutation (one gather per column:
+//            all sources read before any row is written), and right of the
+//            panel U12 = L11^-1 A12 is solved in shared memory
+//            (lu_swap_trsm_kernel); the block columns right of a panel are
+//            updated by the SIMT sgemm.
 //   block    the block's exchanges, rebuilt as one permutation
 //            (lu_perm_kernel), reach every column outside the block, U12 of
 //            the block rows is solved, and the trailing matrix is updated by
-//            the library's sgemm with k = nb.
+//            the library's sgemm with k = nb; the next block is factored on
+//            a second stream meanwhile (look-ahead).
 // The result is LAPACK's packed P A = L U.  The solve (lu_laswp_rhs_kernel,
 // lu_trsv_block_kernel) applies the exchanges, then forward and back
-// substitution by 256-row diagonal blocks, the off-diagonal parts by the
-// library's sgemv or sgemm.  Every sum is formed in a fixed order: runs are
-// bit-identical.
+// substitution by 256-row diagonal blocks (each triangle staged in shared
+// memory), the off-diagonal parts by the library's sgemv or sgemm.  Every
+// sum is formed in a fixed order: runs are bit-identical.
 #include <cfloat>
 #include <climits>
 
