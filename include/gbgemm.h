@@ -203,9 +203,13 @@ int gbgemm_sgetrf(gbgemm_handle* h, int64_t n, float* A, int64_t lda, int* ipiv,
  * transpose): the row exchanges of ipiv in order, then forward substitution
  * with unit L, then back substitution with U.  LU, ipiv: device, as
  * gbgemm_sgetrf left them.  B: device, n x nrhs column-major, ldb >=
- * max(1, n), overwritten by X.  The solves go by diagonal blocks of 256 rows
- * (one thread block per right-hand side and block), the off-diagonal parts
- * by this library's sgemv (nrhs 1) or sgemm, in the handle's workspace.
+ * max(1, n), overwritten by X.  The solves go by diagonal blocks of 256 rows.
+ * With one right-hand side each substitution is one cooperative launch: a
+ * block of rows is solved by one CTA as soon as the blocks before it are
+ * (flags in the handle's workspace; a wait that runs out after 2 s sets the
+ * device status, see gbgemm_get_device_status).  With several, one thread
+ * block per right-hand side solves each diagonal block, and the off-diagonal
+ * parts go through this library's sgemm.
  * Argument errors, in this order: n (< 0 or > INT_MAX) -1, nrhs (< 0 or >
  * INT_MAX) -2, null LU (n > 0) -3, lda -4, null ipiv (n > 0) -5, null B
  * (n, nrhs > 0) -6, ldb -7.  Then GBGEMM_ERR_NOT_INITIALIZED for a NULL

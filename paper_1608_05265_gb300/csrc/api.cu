@@ -565,6 +565,19 @@ int gbgemm_sgetrs(gbgemm_handle* h, int64_t n, int64_t nrhs, const float* LU, in
   DeviceGuard g(h->device);
   if (gbg::launch_lu_laswp_rhs((int)n, nrhs, ipiv, B, ldb, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
   h->kernel_launches += 1;
+  if (nrhs == 1) {  // each substitution as one cooperative launch (flags in the workspace)
+    const int64_t nblk = (n + gbg::kSolveBlock - 1) / gbg::kSolveBlock;
+    const int rc = ensure_workspace(h, (size_t)nblk * sizeof(int));
+    if (rc != GBGEMM_OK) return rc;
+    int* flags = static_cast<int*>(h->ws);
+    if (gbg::launch_lu_trsv_sweep(false, (int)n, LU, lda, B, flags, h->d_status, h->num_sms, h->stream) !=
+            cudaSuccess ||
+        gbg::launch_lu_trsv_sweep(true, (int)n, LU, lda, B, flags, h->d_status, h->num_sms, h->stream) !=
+            cudaSuccess)
+      return GBGEMM_ERR_CUDA;
+    h->kernel_launches += 2;
+    return GBGEMM_OK;
+  }
   // B(r:r+rows, :) -= LU(r:r+rows, c:c+w) B(c:c+w, :): gemv for one
   // right-hand side, gemm for several (never through the per-call tuner)
   const int tuning = h->tuning;

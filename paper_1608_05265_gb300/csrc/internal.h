@@ -72,6 +72,11 @@ constexpr int kSolveBlock = 256;
 cudaError_t launch_lu_laswp_rhs(int n, int64_t nrhs, const int* ipiv, float* B, int64_t ldb, cudaStream_t s);
 cudaError_t launch_lu_trsv_block(bool upper, const float* LU, int64_t lda, int j0, int w, int64_t nrhs, float* B,
                                  int64_t ldb, cudaStream_t s);
+// One right-hand side: the whole forward (or back) substitution as one
+// cooperative launch; flags: ceil(n / kSolveBlock) ints of scratch (zeroed
+// here); a wait between CTAs that runs out sets *status.
+cudaError_t launch_lu_trsv_sweep(bool upper, int n, const float* LU, int64_t lda, float* x, int* flags, int* status,
+                                 int num_sms, cudaStream_t s);
 
 // ---- split path (split.cu) ----
 constexpr int kPanelRows = 128;     // rows per panel block

@@ -49,6 +49,7 @@ static_assert(kPanelThreads == 32 * kLuPanelCluster && kPushLanes <= 30,
 constexpr int kTrsmCols = 64;     // columns per block of the swap + triangular solve kernel
 constexpr int kSwapThreads = 256;  // its threads (the first kTrsmCols solve one column each)
 constexpr int kXP = kTrsmCols + 1;
+constexpr int kSweepThreads = 512;  // cooperative triangular solve: two thread groups per row block
 
 struct MaxLoc {
   float v;
@@ -619,45 +620,43 @@ __device__ __forceinline__ int strip_rows(bool upper, int w, int t) {
   return upper ? 32 * t + ws : w - 32 * t;
 }
 
-// One diagonal block of the triangular solves, rows [j0, j0 + w) (w <= 256)
-// of one right-hand side per block: forward substitution with the unit lower
-// triangle (UPPER false) or back substitution with the upper one (UPPER true).
-// The triangle is first copied into shared memory (4-byte asynchronous
-// copies, all in flight at once, no alignment needed), then solved in steps
-// of 32 rows: each 32 x 32 triangle by one warp from registers, the rest of
-// the block by all threads.
+// Offsets of the packed strips of a diagonal block of w rows (one thread).
 template <bool UPPER>
-__global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float* __restrict__ LU, int64_t lda, int j0,
-                                                                   int w, float* __restrict__ B, int64_t ldb) {
-  extern __shared__ float tri[];  // the packed strips
-  __shared__ float ys[kSolveBlock];
-  __shared__ int soff[kSolveBlock / 32 + 1];
-  float* b = B + (int64_t)blockIdx.x * ldb + j0;
-  const float* T = LU + j0 + (int64_t)j0 * lda;  // the diagonal block: (i, q) at T[i + q * lda]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void strip_offsets(int w, int* soff) {
   const int nsub = (w + 31) / 32;
-  if (tid == 0) {
-    int o = 0;
-    for (int t = 0; t < nsub; ++t) {
-      soff[t] = o;
-      o += min(32, w - 32 * t) * strip_rows(UPPER, w, t);
-    }
-    soff[nsub] = o;
+  int o = 0;
+  for (int t = 0; t < nsub; ++t) {
+    soff[t] = o;
+    o += min(32, w - 32 * t) * strip_rows(UPPER, w, t);
   }
-  if (tid < w) ys[tid] = b[tid];
-  __syncthreads();
-  for (int t = 0; t < nsub; ++t) {  // issue every copy, then wait once
+  soff[nsub] = o;
+}
+
+// Issue the 4-byte asynchronous copies of the packed triangle of the
+// diagonal block T (w rows) into tri (no wait; no alignment needed).
+template <bool UPPER>
+__device__ __forceinline__ void stage_triangle(const float* __restrict__ T, int64_t lda, int w, float* tri,
+                                               const int* soff) {
+  const int nsub = (w + 31) / 32;
+  for (int t = 0; t < nsub; ++t) {
     const int h = strip_rows(UPPER, w, t), r0 = UPPER ? 0 : 32 * t;
     const int cnt = min(32, w - 32 * t) * h;
-    for (int e = tid; e < cnt; e += kSolveBlock) {
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int col = e / h, r = e % h;
       const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tri + soff[t] + e);
       const float* src = T + (r0 + r) + (int64_t)(32 * t + col) * lda;
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
     }
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  __syncthreads();
+}
+
+// Solve the staged triangle in place on ys (w values), in steps of 32 rows:
+// each 32 x 32 triangle by warp 0 from registers, the rest of the block by
+// threads 0 .. w-1.  Every thread of the block calls it (it synchronises).
+template <bool UPPER>
+__device__ __forceinline__ void solve_triangle(const float* tri, const int* soff, int w, float* ys) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nsub = (w + 31) / 32;
   for (int k = 0; k < nsub; ++k) {
     const int t = UPPER ? nsub - 1 - k : k;
     const int s0 = 32 * t;
@@ -702,10 +701,121 @@ __global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float*
     }
     __syncthreads();
   }
+}
+
+// One diagonal block of the triangular solves, rows [j0, j0 + w) (w <= 256)
+// of one right-hand side per block: forward substitution with the unit lower
+// triangle (UPPER false) or back substitution with the upper one (UPPER true).
+// The triangle is first copied into shared memory (4-byte asynchronous
+// copies, all in flight at once, no alignment needed), then solved in steps
+// of 32 rows.
+template <bool UPPER>
+__global__ void __launch_bounds__(kSolveBlock) lu_trsv_block_kernel(const float* __restrict__ LU, int64_t lda, int j0,
+                                                                   int w, float* __restrict__ B, int64_t ldb) {
+  extern __shared__ float tri[];  // the packed strips
+  __shared__ float ys[kSolveBlock];
+  __shared__ int soff[kSolveBlock / 32 + 1];
+  float* b = B + (int64_t)blockIdx.x * ldb + j0;
+  const float* T = LU + j0 + (int64_t)j0 * lda;  // the diagonal block: (i, q) at T[i + q * lda]
+  const int tid = threadIdx.x;
+  if (tid == 0) strip_offsets<UPPER>(w, soff);
+  if (tid < w) ys[tid] = b[tid];
+  __syncthreads();
+  stage_triangle<UPPER>(T, lda, w, tri, soff);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  solve_triangle<UPPER>(tri, soff, w, ys);
   if (tid < w) b[tid] = ys[tid];
 }
 
-bool g_attr_done[64][5];
+// A whole triangular solve with one right-hand side in one cooperative
+// launch (the blocked substitution without host-side steps): the rows are
+// cut into blocks of 256, taken in the order of the solve (forward: first to
+// last; back: last to first), block k of that order by CTA k mod the grid.
+// A CTA takes the contribution of every earlier block c as soon as c's flag
+// is set (y_b -= A_bc x_c, the 256 x 256 product split over two thread
+// groups of 128 columns, added in a fixed order), then solves its diagonal
+// triangle (staged in shared memory while it waits) and publishes x_b and
+// its flag.  Every wait is on an earlier block of the order, so the chain
+// always progresses; a wait is bounded (2 s) and sets *status.
+template <bool UPPER>
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    lu_trsv_sweep_kernel(int n, const float* __restrict__ LU, int64_t lda, float* __restrict__ x,
+                         int* __restrict__ flags, int* __restrict__ status) {
+  extern __shared__ float tri[];
+  __shared__ float ys[kSolveBlock];
+  __shared__ float xs[kSolveBlock];
+  __shared__ float part[kSweepThreads / kSolveBlock][kSolveBlock];
+  __shared__ int soff[kSolveBlock / 32 + 1];
+  __shared__ int go;
+  const int tid = threadIdx.x;
+  const int nblk = (n + kSolveBlock - 1) / kSolveBlock;
+  for (int k = blockIdx.x; k < nblk; k += gridDim.x) {
+    const int b = UPPER ? nblk - 1 - k : k;
+    const int r0 = kSolveBlock * b, w = min(kSolveBlock, n - r0);
+    __syncthreads();  // the previous block's use of soff, tri, ys is over
+    if (tid == 0) strip_offsets<UPPER>(w, soff);
+    if (tid < w) ys[tid] = x[r0 + tid];
+    __syncthreads();
+    stage_triangle<UPPER>(LU + r0 + (int64_t)r0 * lda, lda, w, tri, soff);  // lands while the contributions run
+    for (int kk = 0; kk < k; ++kk) {
+      const int cb = UPPER ? nblk - 1 - kk : kk;
+      const int c0 = kSolveBlock * cb, wc = min(kSolveBlock, n - c0);
+      if (tid == 0) {
+        int ok = 0;
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (uint32_t it = 0;; ++it) {
+          int f;
+          asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(f) : "l"(flags + cb) : "memory");
+          if (f) { ok = 1; break; }
+          if ((it & 63u) == 63u) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 2000000000ull) break;
+          }
+        }
+        if (!ok) atomicCAS(status, 0, GBGEMM_ERR_DEVICE_TIMEOUT);
+        go = ok;
+      }
+      __syncthreads();
+      if (!go) {  // uniform: every thread read go after the barrier
+        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy lands after the block has left
+        return;
+      }
+      if (tid < wc) xs[tid] = __ldcg(x + c0 + tid);
+      __syncthreads();
+      {  // part[g][i] = sum over this group's columns of A(r0 + i, c0 + q) x_q
+        const int i = tid % kSolveBlock, g = tid / kSolveBlock;
+        constexpr int kq = kSolveBlock / (kSweepThreads / kSolveBlock);
+        float acc = 0.f;
+        if (i < w) {
+          const float* a = LU + (r0 + i) + (int64_t)(c0 + g * kq) * lda;
+#pragma unroll 16
+          for (int q = 0; q < kq; ++q)
+            if (g * kq + q < wc) acc = fmaf(a[(int64_t)q * lda], xs[g * kq + q], acc);
+        }
+        part[g][i] = acc;
+      }
+      __syncthreads();
+      if (tid < w) {
+        float v = ys[tid];
+#pragma unroll
+        for (int g = 0; g < kSweepThreads / kSolveBlock; ++g) v -= part[g][tid];
+        ys[tid] = v;
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    solve_triangle<UPPER>(tri, soff, w, ys);
+    if (tid < w) x[r0 + tid] = ys[tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flags + b), "r"(1) : "memory");
+  }
+}
+
+bool g_attr_done[64][7];
 
 cudaError_t set_smem_once(const void* fn, int which, size_t bytes) {
   int dev = 0;
@@ -805,6 +915,24 @@ cudaError_t launch_lu_laswp_rhs(int n, int64_t nrhs, const int* ipiv, float* B, 
     lu_laswp_rhs_kernel<false><<<(unsigned)nrhs, 256, 0, s>>>(n, ipiv, B, ldb);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_lu_trsv_sweep(bool upper, int n, const float* LU, int64_t lda, float* x, int* flags, int* status,
+                                 int num_sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t tri_bytes = (size_t)kSolveBlock * (kSolveBlock + 32) / 2 * sizeof(float);
+  const void* fn = upper ? (const void*)lu_trsv_sweep_kernel<true> : (const void*)lu_trsv_sweep_kernel<false>;
+  cudaError_t e = set_smem_once(fn, upper ? 5 : 6, tri_bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSweepThreads, tri_bytes)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  const int nblk = (n + kSolveBlock - 1) / kSolveBlock;
+  const int grid = nblk < per_sm * num_sms ? nblk : per_sm * num_sms;  // every CTA resident at once
+  if ((e = cudaMemsetAsync(flags, 0, (size_t)nblk * sizeof(int), s)) != cudaSuccess) return e;
+  void* args[] = {(void*)&n, (void*)&LU, (void*)&lda, (void*)&x, (void*)&flags, (void*)&status};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSweepThreads), args, tri_bytes, s);
 }
 
 cudaError_t launch_lu_trsv_block(bool upper, const float* LU, int64_t lda, int j0, int w, int64_t nrhs, float* B,
