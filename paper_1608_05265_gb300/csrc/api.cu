@@ -578,12 +578,11 @@ int gbgemm_sgetrs(gbgemm_handle* h, int64_t n, int64_t nrhs, const float* LU, in
     h->kernel_launches += 2;
     return GBGEMM_OK;
   }
-  // B(r:r+rows, :) -= LU(r:r+rows, c:c+w) B(c:c+w, :): gemv for one
-  // right-hand side, gemm for several (never through the per-call tuner)
+  // several right-hand sides: B(r:r+rows, :) -= LU(r:r+rows, c:c+w) B(c:c+w, :)
+  // by the sgemm (never through the per-call tuner)
   const int tuning = h->tuning;
   h->tuning = 0;
   auto update = [&](int64_t r, int64_t rows, int64_t c, int64_t w) {
-    if (nrhs == 1) return gbgemm_sgemv(h, 'N', rows, w, -1.0f, LU + r + c * lda, lda, B + c, 1, 1.0f, B + r, 1);
     return run_sgemm(h, 0, 0, 'N', 'N', rows, nrhs, w, -1.0f, LU + r + c * lda, lda, B + c, ldb, 1.0f, B + r, ldb,
                      1, 0, 0, 0);
   };
