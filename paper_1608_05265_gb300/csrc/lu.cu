@@ -791,9 +791,16 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
         float acc = 0.f;
         if (i < w) {
           const float* a = LU + (r0 + i) + (int64_t)(c0 + g * kq) * lda;
+          if (wc == kSolveBlock) {  // a full block of columns: 32 loads in flight, four partial sums
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 32
+            for (int q = 0; q < kq; ++q) s4[q & 3] = fmaf(a[(int64_t)q * lda], xs[g * kq + q], s4[q & 3]);
+            acc = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+          } else {
 #pragma unroll 16
-          for (int q = 0; q < kq; ++q)
-            if (g * kq + q < wc) acc = fmaf(a[(int64_t)q * lda], xs[g * kq + q], acc);
+            for (int q = 0; q < kq; ++q)
+              if (g * kq + q < wc) acc = fmaf(a[(int64_t)q * lda], xs[g * kq + q], acc);
+          }
         }
         part[g][i] = acc;
       }
