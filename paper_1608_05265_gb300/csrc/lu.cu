@@ -250,9 +250,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     lu_mbar_arm(lu_smem(&rx_bar[0]), rx_bytes(0));
     if (nbp > 1) lu_mbar_arm(lu_smem(&rx_bar[1]), rx_bytes(1));
   }
-  for (int q = 0; q < nbp; ++q) {
-#pragma unroll 4
-    for (int rr = tid; rr < nr; rr += kPanelThreads) Sp[rr * pitch + q] = G[(rlo + rr) + (int64_t)q * lda];
+  for (int rr = tid; rr < nr; rr += kPanelThreads) {  // a row per thread: its loads all in flight, then stored
+    float v[kLuPanelNb];
+#pragma unroll
+    for (int q = 0; q < kLuPanelNb; ++q)
+      if (q < nbp) v[q] = G[(rlo + rr) + (int64_t)q * lda];
+#pragma unroll
+    for (int q = 0; q < kLuPanelNb; ++q)
+      if (q < nbp) Sp[rr * pitch + q] = v[q];
   }
   if (jp >= 0) {
     // Prologue: the previous block [jp, j0) (nbq columns, its exchanges in
