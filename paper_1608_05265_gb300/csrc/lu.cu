@@ -595,25 +595,30 @@ template <bool SMEM>
 __global__ void __launch_bounds__(256) lu_laswp_rhs_kernel(int n, const int* __restrict__ ipiv, float* __restrict__ B,
                                                            int64_t ldb) {
   extern __shared__ float ys[];
+  __shared__ int pv[1024];  // a chunk of ipiv, loaded by every thread
   float* b = B + (int64_t)blockIdx.x * ldb;
   float* y = SMEM ? ys : b;
   if (SMEM) {
+#pragma unroll 8
     for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = b[i];
-    __syncthreads();
   }
-  if (threadIdx.x == 0)
-    for (int j = 0; j < n; ++j) {
-      const int p = ipiv[j] - 1;
-      if (p != j && p >= 0 && p < n) {
-        const float t = y[j];
-        y[j] = y[p];
-        y[p] = t;
+  for (int j0 = 0; j0 < n; j0 += 1024) {
+    const int cnt = min(1024, n - j0);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) pv[t] = ipiv[j0 + t];
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int j = 0; j < cnt; ++j) {
+        const int p = pv[j] - 1, r = j0 + j;
+        if (p != r && p >= 0 && p < n) {
+          const float t = y[r];
+          y[r] = y[p];
+          y[p] = t;
+        }
       }
-    }
-  if (SMEM) {
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = ys[i];
   }
+  if (SMEM)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = ys[i];
 }
 
 // Strip t of a diagonal block of w rows holds its columns [32t, 32t + 32)
