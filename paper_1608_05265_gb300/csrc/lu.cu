@@ -688,11 +688,12 @@ __device__ __forceinline__ void solve_triangle(const float* tri, const int* soff
       } else {
 #pragma unroll
         for (int q = 0; q < 32; ++q) M[q] = (lane <= q && q < ws) ? S[q * h + s0 + lane] : 0.f;
+        const float dmine = lane < ws ? S[lane * h + s0 + lane] : 1.f;  // this lane's diagonal entry
 #pragma unroll
         for (int q = 31; q >= 0; --q) {
-          if (q < ws) {
-            if (lane == q) v = v / M[q];
-            const float xq = __shfl_sync(0xFFFFFFFFu, v, q);
+          if (q < ws) {  // every lane forms the same x_q = v_q / u_qq (no divergent division)
+            const float xq = __shfl_sync(0xFFFFFFFFu, v, q) / __shfl_sync(0xFFFFFFFFu, dmine, q);
+            if (lane == q) v = xq;
             if (lane < q) v = fmaf(-M[q], xq, v);
           }
         }
