@@ -122,14 +122,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle sample (the reference arm and the cpu_baseline field)
 # ---------------------------------------------------------------------------
-def oracle_sample(steps: int, block: int = 128, warmup: int = 0):
-    """Time the FP64 oracle on `steps` blocks of the 8192^3 product (all cores)."""
+def oracle_sample(steps: int, block: int = 128, warmup: int = 0, nthreads: int = 0):
+    """Time the FP64 oracle on `steps` blocks of the 8192^3 product (all cores,
+    or `nthreads` threads)."""
     import numpy as np
 
     from oracle import oracle as O
     from paper_1608_05265_gb300 import synth
 
-    threads = O.max_threads()
+    threads = nthreads if nthreads > 0 else O.max_threads()
     times = []
     flops = 0.0
     for s in range(warmup + steps):
@@ -140,7 +141,8 @@ def oracle_sample(steps: int, block: int = 128, warmup: int = 0):
         B = synth.uniform_block(SEED, 2, N, 0, N, j0, j0 + block)
         C = synth.uniform_block(SEED, 4, N, i0, i0 + block, j0, j0 + block)
         t0 = time.perf_counter()
-        O.gemm_f64("N", "N", block, block, N, ALPHA, A, block, B, N, BETA, C, block, want_bound=False)
+        O.gemm_f64("N", "N", block, block, N, ALPHA, A, block, B, N, BETA, C, block, want_bound=False,
+                   nthreads=threads)
         dt = time.perf_counter() - t0
         if s >= warmup:
             times.append(dt)
@@ -149,6 +151,29 @@ def oracle_sample(steps: int, block: int = 128, warmup: int = 0):
     return {"value": flops / total / 1e12 if total > 0 else 0.0, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{steps} blocks of {block}x{block} of C (k={N}), FP64 triple loop, {threads} threads",
             "seconds": total}
+
+
+def host_cpu_model() -> str:
+    """The host CPU's model name and logical core count, from lscpu or /proc/cpuinfo."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return f"{name or 'unknown'} x {os.cpu_count()}"
 
 
 def run_reference(args, rank, world):
@@ -336,6 +361,10 @@ def run_ours(args, rank, world, local_rank):
         cpu = oracle_sample(steps=max(1, args.cpu_blocks)) if args.cpu_blocks > 0 else None
         if cpu:
             cpu.pop("seconds", None)
+            one = oracle_sample(steps=1, nthreads=1)
+            one.pop("seconds", None)
+            cpu["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
+            cpu["host_cpu"] = host_cpu_model()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

@@ -224,6 +224,18 @@ int gbgemm_sgetrs(gbgemm_handle* h, int64_t n, int64_t nrhs, const float* LU, in
  * GBGEMM_ERR_CUDA if the stream reported a CUDA error. */
 int gbgemm_get_device_status(gbgemm_handle* h, int* status);
 
+/* Failure-detection check (tests).  Queues on the handle's stream one thread
+ * that waits, with the same bounded mbarrier wait every kernel of this
+ * library uses, on a barrier that nothing arrives on and no copy is bound
+ * to; after timeout_ns (1 ns .. GBGEMM_DEBUG_MAX_WAIT_NS) the wait gives up,
+ * GBGEMM_ERR_DEVICE_TIMEOUT is recorded in the device status word (read it
+ * with gbgemm_get_device_status) and the kernel returns normally: the CUDA
+ * context stays usable.  The paper has no counterpart (its co-processor
+ * runs without such checks).  Errors: GBGEMM_ERR_INVALID_VALUE for a
+ * timeout out of range, GBGEMM_ERR_CUDA if the launch fails. */
+#define GBGEMM_DEBUG_MAX_WAIT_NS 100000000ull
+int gbgemm_debug_expire_wait(gbgemm_handle* h, uint64_t timeout_ns);
+
 /* Profiling (benchmark use).  Between begin and end the handle records a
  * pair of CUDA events on its stream around every launch of the split-path
  * GEMM kernel, and counts every kernel the library launches.

@@ -137,10 +137,6 @@ int gbgemm_create(gbgemm_handle** out, int device) {
   if (cudaMalloc(&h->d_status, 256) != cudaSuccess || cudaMemset(h->d_status, 0, 256) != cudaSuccess) {
     cudaGetLastError();
     if (h->d_status) cudaFree(h->d_status);
-  if (h->d_lu_perm) cudaFree(h->d_lu_perm);
-  for (cudaEvent_t e : h->lu_ev)
-    if (e) cudaEventDestroy(e);
-  if (h->lu_side) cudaStreamDestroy(h->lu_side);
     delete h;
     return GBGEMM_ERR_ALLOC;
   }
@@ -152,8 +148,13 @@ int gbgemm_destroy(gbgemm_handle* h) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   DeviceGuard g(h->device);
   cudaStreamSynchronize(h->stream);
+  if (h->lu_side) cudaStreamSynchronize(h->lu_side);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
+  if (h->d_lu_perm) cudaFree(h->d_lu_perm);
+  for (cudaEvent_t e : h->lu_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->lu_side) cudaStreamDestroy(h->lu_side);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return GBGEMM_OK;
@@ -953,6 +954,15 @@ int gbgemm_get_device_status(gbgemm_handle* h, int* status) {
   if (cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (v != 0 && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return GBGEMM_ERR_CUDA;
   *status = v;
+  return GBGEMM_OK;
+}
+
+int gbgemm_debug_expire_wait(gbgemm_handle* h, uint64_t timeout_ns) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (timeout_ns == 0 || timeout_ns > GBGEMM_DEBUG_MAX_WAIT_NS) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard g(h->device);
+  if (gbg::launch_wait_probe(h->d_status, timeout_ns, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  h->kernel_launches += 1;
   return GBGEMM_OK;
 }
 

@@ -40,6 +40,11 @@ constexpr int kMaxBN = 256;
 constexpr int kEpiWarps = 16;                      // four per TMEM lane quadrant, each a quarter of the columns
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr uint64_t kTimeoutNs = 2000000000ull;
+// The final drain waits (the producer's copies landing, the MMAs finishing
+// before TMEM is freed) take their own, longer bound, whatever limit the
+// caller gave the work waits: the CTA must not exit with its own copies
+// still in flight.
+constexpr uint64_t kDrainTimeoutNs = 4000000000ull;
 // Shared memory of a kernel instance: STAGES ring slots of one A block and
 // MAXBN B rows, barriers, 1024-byte alignment.  With tiles of at most 128
 // columns the same memory holds a six-slot ring (more copies in flight for
@@ -246,7 +251,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       // Let every copy this thread started land before the CTA can exit.
       volatile int never = 0;
       for (int s = 0; s < kStages; ++s)
-        if (issued[s]) (void)mbar_wait(full_bar(s), (uint32_t)issued_phase[s], &never, timeout_ns);
+        if (issued[s]) (void)mbar_wait(full_bar(s), (uint32_t)issued_phase[s], &never, kDrainTimeoutNs);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -320,7 +325,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       // Wait until every MMA issued here has finished before TMEM is released.
       mma_commit(drain_bar);
       volatile int never = 0;
-      if (!mbar_wait(drain_bar, 0u, &never, timeout_ns)) raise_status(status, abort_flag);
+      if (!mbar_wait(drain_bar, 0u, &never, kDrainTimeoutNs)) raise_status(status, abort_flag);
     }
     __syncwarp();
   } else {

@@ -141,6 +141,10 @@ int choose_splitk(int64_t tiles, int64_t k, int num_sms);
 cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s);
 cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s);
 
+// Failure-detection probe: a bounded mbarrier wait that nothing completes;
+// sets *status to GBGEMM_ERR_DEVICE_TIMEOUT after timeout_ns.
+cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t s);
+
 // FP64 error check of C_out against alpha op(A) op(B) + beta C_in over a
 // block (check.cu); synchronises s.
 int run_error_check(cudaStream_t s, char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,

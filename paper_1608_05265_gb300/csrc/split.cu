@@ -80,7 +80,30 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t m, int64_t n
   }
 }
 
+// Failure-detection probe: one thread waits on an mbarrier that nothing
+// arrives on and no copy is bound to, with the library's bounded wait; when
+// the limit runs out it records GBGEMM_ERR_DEVICE_TIMEOUT in *status, as
+// every kernel's waits do, and the CTA returns normally.
+__global__ void __launch_bounds__(32) wait_probe_kernel(int* status, uint64_t timeout_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0u, &abort_flag, timeout_ns))
+    raise_status(status, &abort_flag);
+  __syncwarp();
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(int* status, uint64_t timeout_ns, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(status, timeout_ns);
+  return cudaGetLastError();
+}
 
 int choose_splitk(int64_t tiles, int64_t k, int num_sms) {
   if (split_parts(k) != 1 || tiles <= 0 || tiles * 2 > num_sms) return 1;

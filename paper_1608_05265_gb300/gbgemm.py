@@ -61,7 +61,7 @@ EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_sgemm_strided_batched",
     "gbgemm_sgemv", "gbgemm_sgetrf", "gbgemm_sgetrs",
-    "gbgemm_get_device_status",
+    "gbgemm_get_device_status", "gbgemm_debug_expire_wait",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
     "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
     "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run", "gbgemm_grouped_plan_configs",
@@ -105,6 +105,7 @@ def lib():
             L.gbgemm_sgetrf.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.c_int]
             L.gbgemm_sgetrs.argtypes = [vp, i64, i64, vp, i64, vp, vp, i64]
             L.gbgemm_get_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            L.gbgemm_debug_expire_wait.argtypes = [vp, ctypes.c_uint64]
             L.gbgemm_status_string.argtypes = [ctypes.c_int]
             L.gbgemm_status_string.restype = ctypes.c_char_p
             L.gbgemm_panel_bytes.argtypes = [i64, i64]
@@ -145,7 +146,8 @@ def lib():
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
                          "gbgemm_sgemm_strided_batched", "gbgemm_sgemv", "gbgemm_sgetrf", "gbgemm_sgetrs",
-                         "gbgemm_get_device_status", "gbgemm_split_pack", "gbgemm_profile_begin",
+                         "gbgemm_get_device_status", "gbgemm_debug_expire_wait", "gbgemm_split_pack",
+                         "gbgemm_profile_begin",
                          "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
                          "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
                          "gbgemm_grouped_plan_configs", "gbgemm_grouped_plan_stats",
@@ -269,6 +271,10 @@ class Handle:
         v = ctypes.c_int()
         _check("gbgemm_get_device_status", lib().gbgemm_get_device_status(self._h, ctypes.byref(v)))
         return v.value
+
+    def debug_expire_wait(self, timeout_ns: int):
+        """Queue a bounded wait that nothing completes (failure-detection test)."""
+        _check("gbgemm_debug_expire_wait", lib().gbgemm_debug_expire_wait(self._h, int(timeout_ns)))
 
     def profile_begin(self):
         _check("gbgemm_profile_begin", lib().gbgemm_profile_begin(self._h))

@@ -125,11 +125,23 @@ def normal_rowscaled_matrix(seed: int, stream: int, rows: int, cols: int, ld: in
     Sub-stream ``stream`` gives the values (two draws per entry), sub-stream
     ``stream + 1`` the row exponents.
     """
-    v = normal01(draws(seed, stream, 2 * rows * cols)).reshape(cols, rows)
     e = int_range(draws(seed, stream + 1, rows), elo, ehi)
     scale = np.ldexp(np.ones(rows, dtype=np.float32), e.astype(np.int32)).astype(np.float32)
-    v = (v * scale[None, :]).astype(np.float32)
-    return place_colmajor(v.reshape(-1), rows, cols, ld)
+    if ld < max(1, rows):
+        raise ValueError("ld < rows")
+    out = np.empty((cols, ld), dtype=np.float32)
+    out.view(np.uint32)[:] = SENTINEL_BITS
+    # column blocks of at most 2^24 entries keep the temporaries small; column c
+    # takes draws 2 c rows .. 2 (c + 1) rows - 1 either way
+    step = max(1, (1 << 24) // max(rows, 1))
+    for c0 in range(0, cols if rows > 0 else 0, step):
+        c1 = min(cols, c0 + step)
+        v = normal01(draws(seed, stream, 2 * rows * (c1 - c0), offset=2 * rows * c0)).reshape(c1 - c0, rows)
+        out[c0:c1, :rows] = v * scale[None, :]
+    flat = out.reshape(-1)
+    if flat.size == 0:
+        flat = np.full(1, sentinel_f32(), dtype=np.float32)
+    return flat
 
 
 def small_int_matrix(seed: int, stream: int, rows: int, cols: int, ld: int, lo: int = -4, hi: int = 4) -> np.ndarray:

@@ -102,3 +102,72 @@ def test_linpack_trailing_update(h, mn, nb):
     c64, bnd = O.gemm_f64("N", "N", m, n, nb, -1.0, A, m, B, nb, 1.0, C, m, rows=rows, cols=cols)
     assert O.error_ratio(synth.logical(out, m, n, m)[rows[0]:rows[1], cols[0]:cols[1]], c64, bnd) <= 1.0
     assert freivalds(out, "N", "N", m, n, nb, -1.0, A, m, B, nb, 1.0, C, m, seed=6) <= 1.0
+
+
+_SQUARE_CACHE = {}
+
+
+def _square_inputs(n):
+    """The square sweep's inputs at size n (seed 1, ld = n + 8): the stored
+    shapes are n x n whatever the transposes, so one set serves all four."""
+    if n not in _SQUARE_CACHE:
+        _SQUARE_CACHE[n] = synth.gemm_problem("uniform", 1, "N", "N", n, n, n, pad=8)
+    return _SQUARE_CACHE[n]
+
+
+@pytest.mark.parametrize("n", [2048, 4096])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")])
+@pytest.mark.parametrize("path", [SPLIT, SIMT])
+def test_square_sweep_against_cpu_oracle(h, n, ta, tb, path):
+    """The square sweep's 2048^3 and 4096^3 points on both paths, against the CPU
+    oracle: every element at 2048, sampled 256 x 256 blocks (corners, centre and
+    seeded random ones) plus the Freivalds identity at 4096."""
+    import torch
+    A, lda, B, ldb, C, ldc = _square_inputs(n)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    h.set_path(path)
+    h.sgemm(ta, tb, n, n, n, 1.5, dA, lda, dB, ldb, -0.25, dC, ldc)
+    torch.cuda.synchronize()
+    assert h.last_path() == path and h.get_device_status() == 0
+    out = dC.cpu().numpy()
+    del dA, dB, dC
+    assert synth.padding_is_sentinel(out, n, n, ldc)
+    got = synth.logical(out, n, n, ldc)
+    if n <= 2048:
+        c64, bnd = O.gemm_f64(ta, tb, n, n, n, 1.5, A, lda, B, ldb, -0.25, C, ldc)
+        assert O.error_ratio(got, c64, bnd) <= 1.0
+    else:
+        for rows, cols in sample_blocks(n, n, 256, seed=7, count=2):
+            c64, bnd = O.gemm_f64(ta, tb, n, n, n, 1.5, A, lda, B, ldb, -0.25, C, ldc, rows=rows, cols=cols)
+            assert O.error_ratio(got[rows[0]:rows[1], cols[0]:cols[1]], c64, bnd) <= 1.0
+        assert freivalds(out, ta, tb, n, n, n, 1.5, A, lda, B, ldb, -0.25, C, ldc, seed=8) <= 1.0
+
+
+_LINPACK_C = {}
+
+
+@pytest.mark.parametrize("nb", [128, 256])
+def test_linpack_trailing_update_16384(h, nb):
+    """The Linpack-shaped update at m = n = 16384 (seed 2, entries normal(0,1)
+    times 2^e per stored row, e in [-20, 20]), against the CPU oracle on
+    sampled 256 x 256 blocks and by the Freivalds identity over the whole
+    result."""
+    import torch
+    m = n = 16384
+    if m not in _LINPACK_C:
+        _LINPACK_C[m] = synth.normal_rowscaled_matrix(2, 4, m, n, m)
+    C = _LINPACK_C[m]
+    A = synth.normal_rowscaled_matrix(2, 0, m, nb, m)
+    B = synth.normal_rowscaled_matrix(2, 2, nb, n, nb)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    h.set_path(0)  # AUTO: k = nb >= 128 runs the split path
+    h.sgemm("N", "N", m, n, nb, -1.0, dA, m, dB, nb, 1.0, dC, m)
+    torch.cuda.synchronize()
+    assert h.last_path() == SPLIT and h.get_device_status() == 0
+    out = dC.cpu().numpy()
+    del dA, dB, dC
+    got = synth.logical(out, m, n, m)
+    for rows, cols in sample_blocks(m, n, 256, seed=9, count=3):
+        c64, bnd = O.gemm_f64("N", "N", m, n, nb, -1.0, A, m, B, nb, 1.0, C, m, rows=rows, cols=cols)
+        assert O.error_ratio(got[rows[0]:rows[1], cols[0]:cols[1]], c64, bnd) <= 1.0
+    assert freivalds(out, "N", "N", m, n, nb, -1.0, A, m, B, nb, 1.0, C, m, seed=10) <= 1.0

@@ -93,3 +93,25 @@ def test_predicted_plan_within_bound(h):
     assert h.get_device_status() == 0
     b.check(nthreads=4)
     plan.close()
+
+
+def test_trained_predictor_gains_over_the_default_rule(h):
+    """What the trained network gains over the method without it: on 64
+    held-out shapes (seed 5, never seen in training), every legal
+    configuration is timed by the exhaustive tuner, and the shipped weights'
+    choices must cost less, in geometric mean over the shapes, than the fixed
+    default rule's; they must also be exactly the tuner's best more often."""
+    import os
+    from paper_1608_05265_gb300 import predictor
+    if not os.path.exists(predictor.DEFAULT_WEIGHTS):
+        pytest.fail("trained predictor weights are missing")
+    params, _ = predictor.load_weights()
+    h.predictor_set(params)
+    shapes = predictor.shape_set(5, 64)
+    cost, _ = predictor.label(h, shapes, reps=2)
+    choice, _ = predictor.predict(h, predictor.features(shapes), predictor.legal_bits(cost))
+    assert np.all(cost[np.arange(len(shapes)), choice] > 0)  # only legal configurations are chosen
+    learned = predictor.regret(cost, choice)
+    default = predictor.regret(cost, predictor.default_choice(shapes))
+    assert learned["geomean_ratio"] < default["geomean_ratio"], (learned, default)
+    assert learned["exact"] > default["exact"], (learned, default)

@@ -56,3 +56,45 @@ def test_masked_argmin():
             continue
         cand = [c for c in range(6) if (legal[s] >> c) & 1]
         assert got[s] == cand[int(np.argmin(out[s, cand]))]
+
+
+def hand_network():
+    """A hand-set network with a few nonzero weights (row = output unit)."""
+    p = {name: np.zeros(shape) for name, shape in R.SIZES}
+    p["W1"][0, 0], p["W1"][0, 1], p["b1"][0] = 1.0, -2.0, 0.5   # z1[0] = x0 - 2 x1 + 0.5
+    p["W1"][1, 2], p["b1"][1] = 3.0, -1.0                       # z1[1] = 3 x2 - 1
+    p["W1"][2, 0] = -1.0                                        # z1[2] = -x0 (cut by the ReLU)
+    p["W2"][0, 0], p["W2"][0, 1], p["b2"][0] = 2.0, 1.0, -0.25  # z2[0] = 2 h1[0] + h1[1] - 0.25
+    p["W2"][1, 2], p["b2"][1] = 5.0, 0.75                       # z2[1] = 5 h1[2] + 0.75
+    p["W2"][2, 0] = -1.0                                        # z2[2] = -h1[0] (cut by the ReLU)
+    p["W3"][0, 0], p["W3"][0, 1], p["b3"][0] = 1.0, 2.0, 0.125  # out0 = h2[0] + 2 h2[1] + 1/8
+    p["W3"][1, 0] = -1.0                                        # out1 = -h2[0] (no ReLU on the output)
+    p["W3"][2, 2], p["b3"][2] = 4.0, -0.5                       # out2 = 4 h2[2] - 1/2
+    p["W3"][3, 1] = 1.0                                         # out3 = h2[1]
+    p["b3"][5] = 3.0                                            # out5 = 3
+    return R.pack(p)
+
+
+def test_forward_of_a_hand_set_network():
+    # Worked by hand.  Row 1, x = (1, 1/4, 2, 0 ...): z1 = (1, 5, -1) -> h1 = (1, 5, 0);
+    # z2 = (6.75, 0.75, -1) -> h2 = (6.75, 0.75, 0); out = (8.375, -6.75, -0.5, 0.75, 0, 3).
+    # Row 2, x = (0, 0, 1/2, 0 ...): h1 = (0.5, 0.5, 0); h2 = (1.25, 0.75, 0);
+    # out = (2.875, -1.25, -0.5, 0.75, 0, 3).
+    # A dropped b2 changes out0 and out3, a missing hidden ReLU changes out2,
+    # a ReLU on the output changes out1, a transposed W1 changes every row.
+    theta = hand_network()
+    X = np.zeros((2, 8))
+    X[0, :3] = (1.0, 0.25, 2.0)
+    X[1, 2] = 0.5
+    out, (_, z1, h1, z2, h2) = R.forward(theta, X)
+    assert np.array_equal(out, [[8.375, -6.75, -0.5, 0.75, 0.0, 3.0], [2.875, -1.25, -0.5, 0.75, 0.0, 3.0]])
+    assert np.array_equal(h1[:, :3], [[1.0, 5.0, 0.0], [0.5, 0.5, 0.0]])
+    assert np.array_equal(h2[:, :3], [[6.75, 0.75, 0.0], [1.25, 0.75, 0.0]])
+    # the parameter layout: W1 is 64 x 8 row-major, first in the flat vector
+    assert theta[1] == -2.0 and theta[8 + 2] == 3.0 and theta[64 * 8] == 0.5
+    # loss by hand with y = 0 and the mask keeping out0 and out1 of row 1 only:
+    # (8.375^2 + 6.75^2) / 2
+    M = np.zeros((2, 6))
+    M[0, :2] = 1.0
+    assert R.loss(theta, X, np.zeros((2, 6)), M) == (8.375 ** 2 + 6.75 ** 2) / 2
+    assert list(R.predict(theta, X, np.array([0b111111, 0b111100]))) == [1, 2]

@@ -6,11 +6,17 @@ latency-bound loops, or with device memory reserved by another framework):
 its scratch is a fixed array in the library's device memory instead of a
 handle's workspace.  This file is named so that pytest collects it last.
 
-Checks, through the C ABI: two calls in a row on different problems (the
-second reuses scratch the first left behind) agree with gbgemm_sgemm on the
-split path within the acceptance bound 2 k 2^-24 (|alpha||A||B| + |beta||C|)
-used by every parity test; a problem needing more scratch than the fixed
-maximum is refused with GBGEMM_ERR_SCRATCH_LIMIT before anything runs.
+Checks, through the C ABI, on calls in a row (each reuses the scratch the
+one before left behind):
+  * the result of the allocation-free call is within the acceptance bound
+    |C - C64| <= 2 k 2^-24 (|alpha||A||B| + |beta||C|) of the FP64 oracle,
+    element by element, as is that of gbgemm_sgemm on the split path;
+  * the two results agree with each other within the same bound;
+  * the cases cover the three-part split (k < 512), the two-part split
+    (k >= 512) and operands whose rows span 2^-60 .. 2^60 (the re-pack of
+    badly scaled K-vectors writes into the scratch panels too);
+a problem needing more scratch than the fixed maximum is refused with
+GBGEMM_ERR_SCRATCH_LIMIT before anything runs.
 """
 
 import numpy as np
@@ -22,10 +28,31 @@ from paper_1608_05265_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def _run_both(L, h, stream, ta, tb, m, n, k, alpha, beta, seed):
+def _scaled(seed, ta, tb, m, n, k, pad):
+    """Uniform operands whose K-vectors are scaled by 2^e, e in [-60, 60]:
+    rows of op(A) and columns of op(B)."""
+    A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", seed, ta, tb, m, n, k, pad=pad)
+    ea = synth.int_range(synth.draws(seed, 80, m), -60, 60)
+    eb = synth.int_range(synth.draws(seed, 81, n), -60, 60)
+    ar, ac = synth.op_shape(ta, m, k)
+    br, bc = synth.op_shape(tb, k, n)
+    Al = synth.logical(A, ar, ac, lda).astype(np.float64)
+    Bl = synth.logical(B, br, bc, ldb).astype(np.float64)
+    Al = Al * (np.ldexp(1.0, ea)[:, None] if ta in "Nn" else np.ldexp(1.0, ea)[None, :])
+    Bl = Bl * (np.ldexp(1.0, eb)[None, :] if tb in "Nn" else np.ldexp(1.0, eb)[:, None])
+    A2, B2 = A.copy(), B.copy()
+    synth.logical(A2, ar, ac, lda)[...] = Al.astype(np.float32)
+    synth.logical(B2, br, bc, ldb)[...] = Bl.astype(np.float32)
+    return A2, lda, B2, ldb, C, ldc
+
+
+def _run_both(L, h, stream, ta, tb, m, n, k, alpha, beta, seed, scaled=False):
     import torch
     from paper_1608_05265_gb300 import gbgemm
-    A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", seed, ta, tb, m, n, k, pad=3)
+    if scaled:
+        A, lda, B, ldb, C, ldc = _scaled(seed, ta, tb, m, n, k, pad=3)
+    else:
+        A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", seed, ta, tb, m, n, k, pad=3)
     dA = torch.from_numpy(A).cuda()
     dB = torch.from_numpy(B).cuda()
     c_new = torch.from_numpy(C).cuda()
@@ -42,12 +69,16 @@ def _run_both(L, h, stream, ta, tb, m, n, k, alpha, beta, seed):
     new = c_new.cpu().numpy()
     old = c_old.cpu().numpy()
     assert synth.padding_is_sentinel(new, m, n, ldc)
-    _, bound = O.gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc)
-    diff = np.abs(synth.logical(new, m, n, ldc).astype(np.float64) - synth.logical(old, m, n, ldc))
+    c64, bound = O.gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc)
+    got_new = synth.logical(new, m, n, ldc)
+    got_old = synth.logical(old, m, n, ldc)
+    assert O.error_ratio(got_new, c64, bound) <= 1.0
+    assert O.error_ratio(got_old, c64, bound) <= 1.0
+    diff = np.abs(got_new.astype(np.float64) - got_old)
     assert np.all(diff <= bound)
 
 
-def test_noalloc_matches_existing_entry_point_twice():
+def test_noalloc_matches_oracle_and_existing_entry_point_in_a_row():
     import torch
     from paper_1608_05265_gb300 import build, gbgemm
     build.build()
@@ -55,9 +86,13 @@ def test_noalloc_matches_existing_entry_point_twice():
     h = gbgemm.Handle(0)
     stream = torch.cuda.current_stream()
     h.set_stream(stream)
-    # first call, then a second, larger one that reuses what the first left in the scratch array
+    # three-part split (k < 512), then a larger two-part one that reuses what
+    # the first left in the scratch array, then badly scaled operands (re-pack)
+    # on both splits
     _run_both(L, h, stream.cuda_stream, "N", "T", 300, 520, 384, 1.5, -0.25, 41)
     _run_both(L, h, stream.cuda_stream, "T", "N", 1000, 777, 555, -1.0, 1.0, 42)
+    _run_both(L, h, stream.cuda_stream, "N", "N", 257, 300, 200, 1.0, 0.5, 43, scaled=True)
+    _run_both(L, h, stream.cuda_stream, "T", "T", 390, 260, 640, 2.0, 0.0, 44, scaled=True)
     h.close()
 
 
