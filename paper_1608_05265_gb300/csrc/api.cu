@@ -38,6 +38,8 @@ struct gbgemm_handle {
   int64_t kernel_launches = 0;
   // tuning
   int tuning = 0;
+  size_t grouped_ring_bytes = 0;   // panel ring of grouped plans (0: the default)
+  int packing = GBGEMM_PACKING_AUTO;  // where the split path packs its operands
   gbg::Tuner tuner;
   gbg::Predictor predictor;
 };
@@ -62,8 +64,6 @@ struct DeviceGuard {
     if (changed) cudaSetDevice(prev);
   }
 };
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int ensure_workspace(gbgemm_handle* h, size_t bytes) {
   if (bytes <= h->ws_bytes) return GBGEMM_OK;
@@ -109,9 +109,7 @@ size_t gbgemm_panel_bytes(int64_t rows, int64_t k) {
 
 size_t gbgemm_split_workspace_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  const size_t parts = (size_t)gbg::split_parts(k);
-  return parts * (align_up(gbg::panel_bytes(m, k), 256) + align_up(gbg::panel_bytes(n, k), 256)) +
-         align_up((size_t)m * 4, 256) + align_up((size_t)n * 4, 256);
+  return gbg::split_layout(m, n, k, 1, 1, 256).total;
 }
 
 int gbgemm_create(gbgemm_handle** out, int device) {
@@ -246,55 +244,28 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
     return GBGEMM_OK;
   }
   if (!split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
-  const size_t pa = align_up(gbg::panel_bytes(m, k), 256), pb = align_up(gbg::panel_bytes(n, k), 256);
-  const size_t xa = align_up((size_t)m * 4, 256);
-  // workspace: per problem z, at z * block bytes:
-  //   [panel A | panel B | maxima A | maxima B | (three parts) panel A2 | panel B2]
-  // Split-K (one problem, long k, too few tiles for the SMs): after the
-  // panels, splitk x tiles raw 128 x bn accumulators, summed by a reduction.
-  const size_t block = gbgemm_split_workspace_bytes(m, n, k);
-  if (block > ((size_t)1 << 62) / (size_t)batch) return GBGEMM_ERR_ALLOC;
+  // Workspace (one problem or a strided batch): control words, band counters
+  // and row maxima (zeroed per call), the packed panels, and with split-K
+  // (one problem, long k, too few tiles for the SMs) splitk x tiles raw
+  // 128 x bn accumulators, summed by a reduction.
   const int64_t tiles_mn = ((m + 127) / 128) * ((n + split_bn - 1) / split_bn);
   const int splitk = batch == 1 ? gbg::choose_splitk(tiles_mn, k, h->num_sms) : 1;
-  const size_t partial_bytes = splitk > 1 ? (size_t)splitk * (size_t)tiles_mn * 128 * (size_t)split_bn * 4 : 0;
-  int rc = ensure_workspace(h, block * (size_t)batch + partial_bytes);
+  const gbg::SplitLayout L = gbg::split_layout(m, n, k, batch, splitk, split_bn);
+  if (L.block > ((size_t)1 << 62) / (size_t)batch) return GBGEMM_ERR_ALLOC;
+  int rc = ensure_workspace(h, L.total);
   if (rc != GBGEMM_OK) return rc;
-  uint8_t* ws = static_cast<uint8_t*>(h->ws);
-  void* panelA = ws;
-  void* panelB = ws + pa;
-  uint32_t* amaxA = reinterpret_cast<uint32_t*>(ws + pa + pb);
-  uint32_t* amaxB = reinterpret_cast<uint32_t*>(ws + pa + pb + xa);
-  const size_t xb = align_up((size_t)n * 4, 256);
-  const bool three = gbg::split_parts(k) == 2;
-  void* panelA2 = three ? ws + pa + pb + xa + xb : nullptr;
-  void* panelB2 = three ? ws + pa + pb + xa + xb + pa : nullptr;
-  // Rows of op(A): element (i, p) at A[p + i*lda] when transposed (k contiguous).
-  const int64_t bw = (int64_t)(block / 4);  // maxima stride in words
-  if (gbg::launch_split_pack_batched(m, k, A, lda, ta == 1, amaxA, panelA, panelA2, batch, sa, bw, (int64_t)block,
-                                     h->stream) != cudaSuccess)
-    return GBGEMM_ERR_CUDA;
-  // Columns of op(B): element (j, p) at B[p + j*ldb] when not transposed (k contiguous).
-  if (gbg::launch_split_pack_batched(n, k, B, ldb, tb == 0, amaxB, panelB, panelB2, batch, sb, bw, (int64_t)block,
-                                     h->stream) != cudaSuccess)
-    return GBGEMM_ERR_CUDA;
-  gbg::SplitGemmArgs a;
-  a.panelA = panelA; a.panelB = panelB; a.amaxA = amaxA; a.amaxB = amaxB;
-  a.panelA2 = panelA2; a.panelB2 = panelB2;
-  a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
-  a.status = h->d_status; a.num_sms = h->num_sms;
-  a.bn = split_bn; a.raster = 16;
-  a.batch = batch; a.panel_stride = (int64_t)block; a.amax_stride = bw; a.c_stride = sc;
-  a.splitk = splitk;
-  a.partial = splitk > 1 ? reinterpret_cast<float*>(ws + block) : nullptr;
-  h->kernel_launches += 4;  // two packing and two re-packing kernels
+  gbg::SplitCall c;
+  c.ta = ta; c.tb = tb; c.m = m; c.n = n; c.k = k; c.alpha = alpha; c.beta = beta;
+  c.A = A; c.lda = lda; c.B = B; c.ldb = ldb; c.C = C; c.ldc = ldc;
+  c.batch = batch; c.sa = sa; c.sb = sb; c.sc = sc;
+  c.bn = split_bn; c.raster = 16; c.splitk = splitk;
+  c.ws = h->ws; c.status = h->d_status; c.num_sms = h->num_sms;
+  c.fused = h->packing == GBGEMM_PACKING_FUSED;
+  h->kernel_launches += c.fused ? 1 : 2;  // the memset of the workspace head (and the packing launch)
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  if (gbg::launch_split_gemm(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (gbg::launch_split_call(c, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  h->kernel_launches += 1;
-  if (splitk > 1) {
-    if (gbg::launch_splitk_reduce(a, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
-    h->kernel_launches += 1;
-  }
+  h->kernel_launches += splitk > 1 ? 2 : 1;
   h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;
   return GBGEMM_OK;
@@ -618,14 +589,30 @@ int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, in
   if (t < 0 || (which != 'A' && which != 'B') || rows < 0 || k < 0) return GBGEMM_ERR_INVALID_VALUE;
   if (rows == 0 || k == 0) return GBGEMM_OK;
   if (!X || !amax_bits || !panel || (gbg::split_parts(k) == 2 && !panel2)) return GBGEMM_ERR_INVALID_VALUE;
+  if (!split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
   // Stored rows of X: op(A) rows come from A (m x k or k x m); op(B) columns from B.
   const bool kcontig = (which == 'A') ? (t == 1) : (t == 0);
   const int64_t stored_rows = kcontig ? k : rows;
   if (ldx < (stored_rows > 1 ? stored_rows : 1)) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard g(h->device);
-  return gbg::launch_split_pack(rows, k, X, ldx, kcontig, amax_bits, panel, panel2, h->stream) == cudaSuccess
-             ? GBGEMM_OK
-             : GBGEMM_ERR_CUDA;
+  // The GEMM kernel's packers alone (no tiles), on the K-vectors as rows of
+  // an "A" operand; the panels are cleared first so that the padding rows of
+  // the last (even) block read as zeros.
+  const gbg::SplitLayout L = gbg::split_layout(rows, 0, k, 1, 1, 256);
+  int rc = ensure_workspace(h, L.head);
+  if (rc != GBGEMM_OK) return rc;
+  const size_t pbytes = gbg::panel_bytes(rows, k);
+  if (cudaMemsetAsync(panel, 0, pbytes, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (gbg::split_parts(k) == 2 && cudaMemsetAsync(panel2, 0, pbytes, h->stream) != cudaSuccess)
+    return GBGEMM_ERR_CUDA;
+  gbg::SplitCall c;
+  c.ta = kcontig ? 1 : 0; c.m = rows; c.n = 0; c.k = k;
+  c.A = X; c.lda = ldx;
+  c.ws = h->ws; c.status = h->d_status; c.num_sms = h->num_sms;
+  c.fused = h->packing == GBGEMM_PACKING_FUSED;
+  c.pack_only = true; c.panel_out = panel; c.panel2_out = gbg::split_parts(k) == 2 ? panel2 : nullptr;
+  c.amax_out = amax_bits;
+  return gbg::launch_split_call(c, h->stream) == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
@@ -641,6 +628,8 @@ int create_plan(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, co
   P->num_sms = h->num_sms;
   P->status = h->d_status;
   P->count = count;
+  P->ring_bytes = h->grouped_ring_bytes;
+  P->fused = h->packing == GBGEMM_PACKING_FUSED;
   P->configs = new (std::nothrow) int[count > 0 ? count : 1];
   if (!P->configs) {
     delete P;
@@ -925,6 +914,21 @@ int gbgemm_tuning_load(gbgemm_handle* h, const char* path) {
 int gbgemm_tuning_clear(gbgemm_handle* h) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   h->tuner.cache.clear();
+  return GBGEMM_OK;
+}
+
+int gbgemm_set_grouped_ring_bytes(gbgemm_handle* h, size_t bytes) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (bytes != 0 && (bytes < ((size_t)1 << 20) || bytes > ((size_t)64 << 30))) return GBGEMM_ERR_INVALID_VALUE;
+  h->grouped_ring_bytes = bytes;
+  return GBGEMM_OK;
+}
+
+int gbgemm_set_packing(gbgemm_handle* h, int mode) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (mode != GBGEMM_PACKING_AUTO && mode != GBGEMM_PACKING_SEPARATE && mode != GBGEMM_PACKING_FUSED)
+    return GBGEMM_ERR_INVALID_VALUE;
+  h->packing = mode;
   return GBGEMM_OK;
 }
 

@@ -1,30 +1,46 @@
-// The persistent split-BF16 tcgen05 GEMM kernel, templated on its tile
-// scheduler: SingleSched walks the tiles of one problem in a rasterised
-// order, GroupedSched walks a cost-sorted list of (group, tile row, tile
-// column) items over many problems.  The per-tile job carries everything a
-// role needs, including the tile width BN (64, 128 or 256) as a run-time
+// The persistent split-BF16 tcgen05 GEMM kernel with fused operand packing,
+// templated on its scheduler: SingleSched walks the tiles of one problem (or
+// a strided batch) in a rasterised order, GroupedSched walks the tiles of
+// many problems, problem after problem.  The per-tile job carries everything
+// a role needs, including the tile width BN (64, 128 or 256) as a run-time
 // value: the MMA instruction descriptor, the B copy size and the epilogue
-// width all follow it, and shared memory and TMEM are sized for 256.
+// width all follow it, and shared memory and TMEM are sized for MAXBN.
 //
 // Roles (one CTA per SM, 576 threads):
-//   warp 0, lane 0  producer: per 32-deep k chunk one bulk async copy of the
-//                   128-row A block and one of the BN-row B rows into a
-//                   4-stage ring, signalled on the stage's "full" mbarrier;
-//   warp 1          owns TMEM (512 columns: two 128 x 256 FP32
-//                   accumulators); lane 0 issues the MMAs (hi*hi, hi*lo,
-//                   lo*hi for both 16-deep halves of a chunk), commits each
-//                   stage to its "empty" barrier and each finished tile to an
-//                   "accumulator full" barrier -- the paper's Accumulator
-//                   (Section III-C): clear on the first k block, accumulate,
-//                   send the result after the last;
-//   warps 2-17      epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (the
-//                   tile rows it owns) for a quarter of the tile's columns
-//                   (at least 32; sixteen warps keep enough C loads in
-//                   flight for the HBM-bound shapes with beta != 0),
+//   warp 0, lane 0  producer: takes the next tile from a device-wide counter
+//                   (dynamic scheduling, so any subset of resident CTAs makes
+//                   progress), hands its index to the other roles through a
+//                   four-slot queue in shared memory, waits until the panel
+//                   bands the tile reads are packed, and streams one bulk
+//                   async copy of the 128-row A block and one of the BN B
+//                   rows per 32-deep k chunk into the stage ring ("full"
+//                   mbarriers); with beta != 0 it first asks L2 for the
+//                   tile's C columns, so the epilogue finds them there;
+//   warp 1          owns TMEM (two 128 x MAXBN FP32 accumulators); lane 0
+//                   issues the MMAs (hi*hi, hi*lo, lo*hi for both 16-deep
+//                   halves of a chunk, six products with the three-part
+//                   split), commits each stage back to its "empty" barrier
+//                   and each finished tile to an "accumulator full" barrier
+//                   -- the paper's Accumulator (Section III-C): clear on the
+//                   first k block, accumulate, send the result after the
+//                   last;
+//   warps 2-9       epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (the
+//                   tile rows it owns) for half of the tile's columns,
 //                   applies 2^(e_i + f_j), alpha and beta once and stores
 //                   column-major C with one 128-byte store per warp and
 //                   column (Section III-D: each core owns whole column
-//                   blocks of the result so that stores stay contiguous).
+//                   blocks of the result so that stores stay contiguous);
+//   warps 10-17     packers (BLIS packing, Section III-A): take packing
+//                   tasks (4 x 32 k of one 128-row band of one operand) from
+//                   a second device-wide counter, split them into the hi/lo
+//                   panels and row maxima, and count each finished task on
+//                   the band's counter; the task that completes a band
+//                   re-packs the band's badly scaled rows (if any) and marks
+//                   the band ready.  Tasks come in the order the tiles need
+//                   them, so the first tiles start while later bands are
+//                   still being packed.  For a grouped batch the panels live
+//                   in a ring smaller than L2: a problem is packed only after
+//                   the problems whose ring bytes it reuses have been read.
 // Every wait is bounded: on expiry the kernel records GBGEMM_ERR_DEVICE_TIMEOUT,
 // raises a CTA-wide abort flag, drains its own copies and MMAs, frees TMEM
 // and returns.
@@ -37,23 +53,64 @@ namespace {
 
 constexpr int kStages = 4;                         // ring depth of the general (BN <= 256) kernel
 constexpr int kMaxBN = 256;
-constexpr int kEpiWarps = 16;                      // four per TMEM lane quadrant, each a quarter of the columns
-constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr int kEpiWarp0 = 2;
+// Warps 2-17 are sixteen epilogue warps (four per TMEM lane quadrant, each a
+// quarter of the columns) when the operands were packed beforehand, or
+// eight epilogue warps (each half of the columns) and eight packer warps
+// when the kernel packs them itself.
+__host__ __device__ constexpr int epi_warps(int pstg) { return pstg == 0 ? 16 : 8; }
+constexpr int kPackWarps = 8;
+constexpr int kCpfWarp = kEpiWarp0 + 16;           // asks L2 for the C tiles ahead of the epilogue
+constexpr int kGemmThreads = 32 * (kCpfWarp + 1);
+constexpr int kTileQ = 4;                          // tile-index queue between the roles
+constexpr int kPackChunks = 4;                     // k chunks per packing task (two rounds of two)
 constexpr uint64_t kTimeoutNs = 2000000000ull;
+// Suspend-time hint of the mbarrier waits: a waiting thread sleeps until the
+// phase completes (or this long) instead of spinning, leaving the issue
+// slots to the packers.
+constexpr uint32_t kHintNs = 20000u;
 // The final drain waits (the producer's copies landing, the MMAs finishing
 // before TMEM is freed) take their own, longer bound, whatever limit the
 // caller gave the work waits: the CTA must not exit with its own copies
 // still in flight.
 constexpr uint64_t kDrainTimeoutNs = 4000000000ull;
 // Shared memory of a kernel instance: STAGES ring slots of one A block and
-// MAXBN B rows, barriers, 1024-byte alignment.  With tiles of at most 128
-// columns the same memory holds a six-slot ring (more copies in flight for
-// the latency-bound grouped batches).
-template <int STAGES, int MAXBN>
-constexpr int gemm_smem_bytes() { return STAGES * (kBlockBytes + MAXBN * 128) + 1024 + 256; }
-constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN>();
-constexpr int kNarrowStages = 6;                   // ring depth of the BN <= 128 instance
+// MAXBN B rows, PSTG 16 KiB staging buffers of the packers (one FP32 chunk
+// of 128 rows x 32 k each, one per packing team), barriers and role
+// scratch, 1024-byte alignment.  Every team double-buffers its chunks.  With
+// tiles of at most 128 columns the memory holds four ring slots and four
+// staging buffers (two packing teams: the grouped batches pack the most
+// data), else four ring slots and two staging buffers (one team), which
+// uses all 227 KiB.
+constexpr int kSmemTail = 2048;  // barriers, tile queue, packing slots
+// A staging buffer holds half a band (64 rows) of one 32-deep k chunk, each
+// row (k contiguous) or k column (rows contiguous) as the 16-byte aligned
+// range that covers it: 64 rows x 144 bytes, or 32 columns x 272 bytes.
+constexpr int kStageRowPitch = 36;   // floats: 9 pieces of 16 bytes
+constexpr int kStageColPitch = 68;   // floats: 17 pieces of 16 bytes
+constexpr int kStageBytes = 64 * kStageRowPitch * 4;
+static_assert(32 * kStageColPitch * 4 <= kStageBytes, "staging buffer");
+template <int STAGES, int MAXBN, int PSTG>
+constexpr int gemm_smem_bytes() {
+  return STAGES * (kBlockBytes + MAXBN * 128) + PSTG * kStageBytes + 1024 + kSmemTail;
+}
+constexpr int kPackStages = 2;                     // staging buffers of the BN <= 256 instance: one team
+constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN, kPackStages>();
+constexpr int kNarrowStages = 4;                   // ring depth of the BN <= 128 instance
 constexpr int kNarrowBN = 128;
+constexpr int kNarrowPackStages = 8;               // two teams of four buffers
+constexpr int kNarrowPrepackStages = 6;            // ring depth of the BN <= 128 instance without packers
+static_assert(kGemmSmemBytes <= 232448, "shared memory of the BN 256 instance");
+static_assert(gemm_smem_bytes<kNarrowStages, kNarrowBN, kNarrowPackStages>() <= 232448, "narrow instance");
+
+// Per-launch control words; zeroed before every launch together with the
+// band counters, the consumption counters and the row maxima.
+struct WorkCtl {
+  int tile_next;   // next work item
+  int pack_next;   // next packing task
+  int pad[62];
+};
+static_assert(sizeof(WorkCtl) == kSplitCtlBytes, "control block size");
 
 // Everything one tile needs.
 struct TileJob {
@@ -64,6 +121,9 @@ struct TileJob {
   int nkc;                  // k chunks
   int bn;                   // tile width: 64, 128 or 256
   int parts;                // 1: [hi | lo] panels, 3 products; 2: also compact lo3 panels, 6 products
+  int ready;                // value of a band counter once the band is packed
+  int bandA, bandB0, nbandB;  // band counters to wait for (A band, first B band, B band count)
+  int problem;              // consumption counter to bump once the panels are read (-1: none)
   int64_t a_part, b_part;   // byte offsets from the [hi | mid] panels to the compact lo3 panels
   int64_t m0, n0;           // tile origin in C
   int64_t m, n;             // problem extents
@@ -78,23 +138,63 @@ struct TileJob {
   float* partial;
 };
 
+// One packing task: chunks kc0 .. kc0 + kPackChunks - 1 (those below nkc) of
+// the 128-row band rb of one operand.
+struct PackJob {
+  const float* X;
+  int64_t ld;
+  uint32_t* amax;           // maxima of the operand's K-vectors (row 0)
+  uint8_t* panel;           // the operand's panel (row 0, k chunk 0)
+  uint8_t* panel2;          // its compact lo3 panel (three parts), else NULL
+  int64_t rows, k;          // K-vectors and their length
+  int64_t rows_alloc;       // panel rows per k chunk
+  int64_t rb;
+  int kc0, nkc;
+  int kcontig;
+  int band, band_tasks;     // band counter and the tasks that fill it
+  int problem;              // owning problem (ring waits), -1: none
+  const int* wait_list;     // problems whose panels must be read first
+  int wait_count;
+};
+
 // B rows [r0, r0 + bn) of a panel start inside 128-row block r0/128 at row
 // r0 % 128; the 64-row case uses half a block.
 __device__ __forceinline__ const uint8_t* panel_rows(const uint8_t* panel, int64_t r0) {
   return panel + (size_t)(r0 >> 7) * kBlockBytes + (size_t)(r0 & 127) * 128;
 }
 
+// Packing order of the bands of one problem: each band in the order of the
+// first tile that reads it.  Tiles go in groups of `gm` tile rows (all
+// tile columns of a group before the next group), so the order is the B
+// bands of tile column 0, the A bands of the first group, the other B bands,
+// then the remaining A bands.  Returns the band as (is_a, index).
+__device__ __forceinline__ void band_at(int pos, int ra, int rb, int gm, int nb0, bool& is_a, int& idx) {
+  if (pos < nb0) { is_a = false; idx = pos; return; }
+  if (pos < nb0 + gm) { is_a = true; idx = pos - nb0; return; }
+  if (pos < rb + gm) { is_a = false; idx = pos - gm; return; }
+  is_a = true; idx = pos - rb;
+}
+
 // One problem, or a strided batch of equal problems, tiles of 128 x BN in
-// groups of `raster` tile rows; problem z has its panels at panelA/B + z*ps,
-// its row maxima at amaxA/B + z*as and its result at C + z*cs.
+// groups of `raster` tile rows; problem z reads its operands at A + z*sa and
+// B + z*sb, has its panels at panelA/B + z*ps, its row maxima at amaxA/B +
+// z*as and its result at C + z*cs.  Band counters: problem z's A band a at
+// band_cnt[z*(ra+rb) + a], its B band b at band_cnt[z*(ra+rb) + ra + b].
 struct SingleSched {
+  WorkCtl* ctl;
+  int* band_cnt;
+  const float* A; const float* B;
+  int64_t lda, ldb, sa, sb;
+  int ta, tb;
   const uint8_t* panelA; const uint8_t* panelB;
-  const uint32_t* amaxA; const uint32_t* amaxB;
-  int64_t m, n;
+  uint32_t* amaxA; uint32_t* amaxB;
+  int64_t m, n, k;
   float alpha, beta;
   float* C; int64_t ldc;
   int tiles_m, tiles_n, nkc, raster, bn, parts;
-  int64_t rbA, rbB;
+  int64_t rbA, rbB;          // panel row blocks (padded to even)
+  int ra, rb;                // bands packed (ceil(m/128), ceil(n/128))
+  int ngroups;               // packing tasks per band
   int64_t a_part, b_part;
   int batch;
   int64_t ps, as, cs;
@@ -119,6 +219,12 @@ struct SingleSched {
     j.b_src = panel_rows(panelB + (size_t)z * ps, (int64_t)tn * bn) + (size_t)kc0 * j.b_kstride;
     j.nkc = (nkc - kc0 < slice_chunks) ? nkc - kc0 : slice_chunks;
     j.bn = bn;
+    j.ready = ngroups + 1;
+    j.bandA = z * (ra + rb) + tm;
+    const int b0 = (tn * bn) >> 7, b1 = min(rb - 1, (tn * bn + bn - 1) >> 7);
+    j.bandB0 = z * (ra + rb) + ra + b0;
+    j.nbandB = b1 - b0 + 1;
+    j.problem = -1;
     j.partial = splitk > 1 ? partial + ((size_t)(sl * tiles_m + tm) * tiles_n + tn) * 128 * bn : nullptr;
     j.parts = parts; j.a_part = a_part; j.b_part = b_part;
     j.m0 = (int64_t)tm * 128; j.n0 = (int64_t)tn * bn;
@@ -127,6 +233,39 @@ struct SingleSched {
     j.C = C + (size_t)z * cs; j.ldc = ldc; j.alpha = alpha; j.beta = beta;
     return j;
   }
+  __device__ __forceinline__ int num_pack_tasks() const { return batch * (ra + rb) * ngroups; }
+  __device__ __forceinline__ PackJob pack_job(int i) const {
+    const int per = (ra + rb) * ngroups;
+    const int z = i / per;
+    const int r = i - z * per;
+    const int pos = r / ngroups, g = r - pos * ngroups;
+    const int gm = min(raster, tiles_m);
+    const int nb0 = min(rb, max(1, bn >> 7));
+    bool is_a;
+    int idx;
+    band_at(pos, ra, rb, gm, nb0, is_a, idx);
+    PackJob P;
+    P.X = is_a ? A + (size_t)z * sa : B + (size_t)z * sb;
+    P.ld = is_a ? lda : ldb;
+    P.kcontig = is_a ? (ta == 1) : (tb == 0);
+    P.rows = is_a ? m : n;
+    P.k = k;
+    P.amax = (is_a ? amaxA : amaxB) + (size_t)z * as;
+    P.panel = const_cast<uint8_t*>(is_a ? panelA : panelB) + (size_t)z * ps;
+    P.panel2 = parts == 2 ? P.panel + (is_a ? a_part : b_part) : nullptr;
+    P.rows_alloc = (is_a ? rbA : rbB) * 128;
+    P.rb = idx;
+    P.kc0 = g * kPackChunks;
+    P.nkc = nkc;
+    P.band = z * (ra + rb) + (is_a ? 0 : ra) + idx;
+    P.band_tasks = ngroups;
+    P.problem = -1;
+    P.wait_list = nullptr;
+    P.wait_count = 0;
+    return P;
+  }
+  __device__ __forceinline__ int* done_counters() const { return nullptr; }
+  __device__ __forceinline__ int need_of(int) const { return 0; }
 };
 
 // Device descriptor of one problem of a grouped batch on the split path.
@@ -138,16 +277,41 @@ struct GroupDev {
   int nkc, bn;
   int64_t rowsA, rowsB;     // panel rows per k chunk
   float alpha, beta;
-  int parts, pad_;
+  int parts, ready;         // ready: value of a band counter once the band is packed
   int64_t a_part, b_part;   // byte offsets to the compact lo3 panels (parts == 2)
+  int bandA0, bandB0;       // counters of A band 0 and B band 0
+  int rbB, pad_;            // B bands packed
 };
 
-// Many problems: item t = (group, tile row, tile column), items sorted by
-// decreasing cost so that a static round robin balances the CTAs.
+// One 128-row band of one operand of a grouped problem, as the packers see it.
+struct PackBand {
+  const float* X;
+  int64_t ld;
+  uint32_t* amax;
+  uint8_t* panel;
+  uint8_t* panel2;
+  int64_t rows, k, rows_alloc;
+  int rb, nkc;
+  int kcontig, ngroups;
+  int first_task, problem;
+  int wait_begin, wait_count;  // the problem's ring waits: wait_list[wait_begin ..)
+  int cnt, pad_;               // the band's counter
+};
+
+// Many problems: item t = (group, tile row, tile column), the items of one
+// problem together, problems in packing order (decreasing cost per tile, so
+// that the cheap tiles come last and fill the gaps).
 struct GroupedSched {
+  WorkCtl* ctl;
+  int* band_cnt;
+  int* done;                // tiles of each problem whose panels have been read
   const int4* items;
   const GroupDev* groups;
-  int n_items;
+  const PackBand* bands;
+  const int* task_band;
+  const int* wait_list;
+  const int* need;          // tiles of each problem (its consumption counter's final value)
+  int n_items, n_tasks;
   __device__ __forceinline__ int num_items() const { return n_items; }
   __device__ __forceinline__ TileJob job(int t) const {
     const int4 it = items[t];
@@ -158,6 +322,12 @@ struct GroupedSched {
     j.a_kstride = (size_t)g.rowsA * 128;
     j.b_kstride = (size_t)g.rowsB * 128;
     j.nkc = g.nkc; j.bn = g.bn;
+    j.ready = g.ready;
+    j.bandA = g.bandA0 + it.y;
+    const int b0 = (it.z * g.bn) >> 7, b1 = min(g.rbB - 1, (it.z * g.bn + g.bn - 1) >> 7);
+    j.bandB0 = g.bandB0 + b0;
+    j.nbandB = b1 - b0 + 1;
+    j.problem = it.x;
     j.parts = g.parts; j.a_part = g.a_part; j.b_part = g.b_part;
     j.m0 = (int64_t)it.y * 128; j.n0 = (int64_t)it.z * g.bn;
     j.m = g.m; j.n = g.n;
@@ -166,11 +336,259 @@ struct GroupedSched {
     j.partial = nullptr;
     return j;
   }
+  __device__ __forceinline__ int num_pack_tasks() const { return n_tasks; }
+  __device__ __forceinline__ PackJob pack_job(int i) const {
+    const int b = task_band[i];
+    const PackBand B = bands[b];
+    PackJob P;
+    P.X = B.X; P.ld = B.ld; P.amax = B.amax; P.panel = B.panel; P.panel2 = B.panel2;
+    P.rows = B.rows; P.k = B.k; P.rows_alloc = B.rows_alloc; P.rb = B.rb;
+    P.kc0 = (i - B.first_task) * kPackChunks;
+    P.nkc = B.nkc;
+    P.kcontig = B.kcontig;
+    P.band = B.cnt;
+    P.band_tasks = B.ngroups;
+    P.problem = B.problem;
+    P.wait_list = wait_list + B.wait_begin;
+    P.wait_count = B.wait_count;
+    return P;
+  }
+  __device__ __forceinline__ int* done_counters() const { return done; }
+  __device__ __forceinline__ int need_of(int q) const { return need[q]; }
 };
 
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
+// Packing teams: the eight packer warps form NT teams of TS = 256 / NT
+// threads, each with its own named barrier and NB = PSTG / NT staging
+// buffers.  A team streams the half chunks (64 rows x 32 k) of its tasks
+// through its buffers: while one is split and stored, the next ones (of
+// this task or of the task the team takes next) are in flight, and the next
+// task's descriptor is fetched during the current one.
+//
+// Staging copies are 16-byte cp.async.cg (through L2 only, whatever the
+// alignment of the leading dimension): each row (k contiguous) or k column
+// (rows contiguous) is copied as the 16-byte aligned range around it, the
+// bytes past its last element cut off by the copy size (and zero-filled), so
+// nothing outside the row or column ahead of it is read; only where that
+// range would start before X itself (X not 16-byte aligned) does the first
+// piece go element by element.  The split reads each value at its offset
+// (0..3 floats) inside the staged range.
+//
+// Item (rr, cc) of a half chunk: row rr (0..63) and 8-wide k piece cc
+// (0..3); item idx = tid + TS * it.  KCONTIG (element (r,p) at X[r*ld + p]):
+// four consecutive items per row.  !KCONTIG (X[r + p*ld]): 32 consecutive
+// rows per warp, one piece per warp.
+template <bool KCONTIG, int TS>
+__device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
+  const int idx = tid + TS * it;
+  if (KCONTIG) {
+    rr = idx >> 2;
+    cc = idx & 3;
+  } else {
+    const int w = idx >> 5;
+    cc = w & 3;
+    rr = (w >> 2) * 32 + (idx & 31);
+  }
+}
+
+// One 16-byte piece of a staged range: bytes [ps, ps + 16) of the source,
+// of which [.., end) are wanted; xb is X's address.
+__device__ __forceinline__ void stage_piece(uint32_t dst, uintptr_t ps, uintptr_t end, uintptr_t xb) {
+  const int64_t left = (int64_t)end - (int64_t)ps;
+  const uint32_t nb = left <= 0 ? 0u : (left >= 16 ? 16u : (uint32_t)left);
+  if (ps >= xb || nb == 0u) {
+    cp_async16(dst, reinterpret_cast<const void*>(nb ? ps : xb), nb);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {  // the range starts before X: element by element
+      const uintptr_t q = ps + 4 * e;
+      const bool ok = q >= xb && q + 4 <= end;
+      cp_async4(dst + 4 * e, reinterpret_cast<const void*>(ok ? q : xb), ok ? 4u : 0u);
+    }
+  }
+}
+
+// Stage half `h` (rows 64h .. 64h + 63 of the band) of k chunk kc into the
+// staging buffer at shared address stg: KCONTIG [row][36 floats], else
+// [k][68 floats].  Zeros outside the operand.
+template <bool KCONTIG, int TS>
+__device__ __forceinline__ void stage_half(const PackJob& P, int64_t kc, int h, uint32_t stg, int tid) {
+  const int64_t r0 = P.rb * 128 + 64 * h, p0 = kc * 32;
+  const uintptr_t xb = reinterpret_cast<uintptr_t>(P.X);
+  if (KCONTIG) {
+    const int64_t kv = P.k - p0 < 32 ? P.k - p0 : 32;  // k values of the chunk (> 0)
+    for (int id = tid; id < 64 * 9; id += TS) {
+      const int row = id / 9, piece = id - row * 9;
+      const int64_t r = r0 + row;
+      const uintptr_t addr = xb + (uintptr_t)(r * P.ld + p0) * 4;
+      const uintptr_t a = addr & ~(uintptr_t)15;
+      const uintptr_t end = (r < P.rows) ? addr + (uintptr_t)kv * 4 : 0;
+      stage_piece(stg + (uint32_t)(row * kStageRowPitch * 4 + piece * 16), a + 16 * piece, end, xb);
+    }
+  } else {
+    const int64_t rv = P.rows - r0 < 64 ? P.rows - r0 : 64;  // rows of the half (may be <= 0)
+    for (int id = tid; id < 32 * 17; id += TS) {
+      const int kk = id / 17, piece = id - kk * 17;
+      const int64_t p = p0 + kk;
+      const uintptr_t addr = xb + (uintptr_t)(r0 + p * P.ld) * 4;
+      const uintptr_t a = addr & ~(uintptr_t)15;
+      const uintptr_t end = (p < P.k && rv > 0) ? addr + (uintptr_t)rv * 4 : 0;
+      stage_piece(stg + (uint32_t)(kk * kStageColPitch * 4 + piece * 16), a + 16 * piece, end, xb);
+    }
+  }
+}
+
+// Split and store half h of k chunk kc of a task from the staging buffer at
+// sf (store_split8 / store_split8_3), folding the rows' maxima into mxr.
+template <bool KCONTIG, int TS>
+__device__ __forceinline__ void convert_half(const PackJob& P, int64_t kc, int h, const float* sf, int tid,
+                                             uint32_t (&mxr)[2][256 / TS]) {
+  constexpr int IT = 256 / TS;
+  const int64_t r0 = P.rb * 128 + 64 * h, p0 = kc * 32;
+  const int64_t xw = (int64_t)(reinterpret_cast<uintptr_t>(P.X) >> 2);  // X in floats
+  uint8_t* blk = P.panel + ((size_t)kc * P.rows_alloc + P.rb * 128) * 128;
+  uint8_t* blk2 = P.panel2 ? P.panel2 + ((size_t)(kc >> 1) * P.rows_alloc + P.rb * 128) * 128 : nullptr;
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    int rr, cc;
+    item_of<KCONTIG, TS>(tid, it, rr, cc);
+    float x[8];
+    if (KCONTIG) {
+      const int sh = (int)((xw + (r0 + rr) * P.ld + p0) & 3);
+      const float* src = sf + rr * kStageRowPitch + sh + cc * 8;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = src[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int kk = cc * 8 + q;
+        const int sh = (int)((xw + r0 + (p0 + kk) * P.ld) & 3);
+        x[q] = sf[kk * kStageColPitch + sh + rr];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) mxr[h][it] = max(mxr[h][it], __float_as_uint(x[q]) & 0x7FFFFFFFu);
+    const int row = 64 * h + rr;
+    if (P.rb * 128 + row < P.rows_alloc) {
+      if (blk2) store_split8_3(blk, blk2, (int)(kc & 1), row, cc, x);
+      else store_split8(blk, row, cc, x);
+    }
+  }
+}
+
+__device__ __forceinline__ int task_chunks(const PackJob& P) {
+  return (P.nkc - P.kc0 < kPackChunks) ? P.nkc - P.kc0 : kPackChunks;
+}
+
+template <int TS>
+__device__ __forceinline__ void stage_any(const PackJob& P, int64_t kc, int h, uint32_t stg, int tid) {
+  if (P.kcontig) stage_half<true, TS>(P, kc, h, stg, tid);
+  else stage_half<false, TS>(P, kc, h, stg, tid);
+  cp_async_commit();
+}
+
+// ---------------------------------------------------------------------------
+// Packing ahead of the GEMM: one CTA of 256 threads per packing task of the
+// scheduler, the operand read straight into registers (all loads of two
+// chunks in flight before any is split), several CTAs per SM.  Counts the
+// task on its band's counter; the task that completes a band re-packs the
+// band's badly scaled rows.  Used where the GEMM kernel runs without packer
+// warps: the two launches are ordered on the stream.
+// ---------------------------------------------------------------------------
+template <bool KCONTIG>
+__device__ __forceinline__ void load8(const PackJob& P, int64_t r, int64_t p, bool vec, float (&x)[8]) {
+  if (KCONTIG) {
+    if (r < P.rows && vec && p + 8 <= P.k) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(P.X + r * P.ld + p));
+      const float4 b = __ldg(reinterpret_cast<const float4*>(P.X + r * P.ld + p + 4));
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = (r < P.rows && p + q < P.k) ? __ldg(P.X + r * P.ld + p + q) : 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = (r < P.rows && p + q < P.k) ? __ldg(P.X + r + (p + q) * P.ld) : 0.f;
+  }
+}
+
+template <bool KCONTIG>
+__device__ __forceinline__ void pack_task_regs(const PackJob& P, uint32_t* smax) {
+  const int tid = threadIdx.x;
+  const int64_t r0 = P.rb * 128;
+  const bool vec = ((P.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.X) & 15) == 0);
+  const int nch = task_chunks(P);
+  if (tid < 128) smax[tid] = 0u;
+  uint32_t mxr[2] = {0u, 0u};
+  for (int c0 = 0; c0 < nch; c0 += 2) {
+    float x[2][2][8];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        int rr, cc;
+        item_of<KCONTIG, 256>(tid, it, rr, cc);
+        if (c0 + c < nch) load8<KCONTIG>(P, r0 + rr, (int64_t)(P.kc0 + c0 + c) * 32 + cc * 8, vec, x[c][it]);
+      }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c0 + c >= nch) break;
+      const int64_t kc = P.kc0 + c0 + c;
+      uint8_t* blk = P.panel + ((size_t)kc * P.rows_alloc + r0) * 128;
+      uint8_t* blk2 = P.panel2 ? P.panel2 + ((size_t)(kc >> 1) * P.rows_alloc + r0) * 128 : nullptr;
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        int rr, cc;
+        item_of<KCONTIG, 256>(tid, it, rr, cc);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) mxr[it] = max(mxr[it], __float_as_uint(x[c][it][q]) & 0x7FFFFFFFu);
+        if (r0 + rr < P.rows_alloc) {
+          if (blk2) store_split8_3(blk, blk2, (int)(kc & 1), rr, cc, x[c][it]);
+          else store_split8(blk, rr, cc, x[c][it]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    int rr, cc;
+    item_of<KCONTIG, 256>(tid, it, rr, cc);
+    if (mxr[it] != 0u) atomicMax(&smax[rr], mxr[it]);
+  }
+  __syncthreads();
+  if (tid < 128 && r0 + tid < P.rows && smax[tid] != 0u) atomicMax(&P.amax[r0 + tid], smax[tid]);
+}
+
+template <class Sched>
+__global__ void __launch_bounds__(256) pack_tasks_kernel(const Sched S) {
+  __shared__ uint32_t smax[128];
+  __shared__ int finisher;
+  const PackJob P = S.pack_job((int)blockIdx.x);
+  if (P.kcontig) pack_task_regs<true>(P, smax);
+  else pack_task_regs<false>(P, smax);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int old = atomicAdd(S.band_cnt + P.band, 1);
+    __threadfence();  // the other tasks' maxima are visible from here on
+    finisher = (old == P.band_tasks - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (finisher) {
+    __threadfence();
+    rescale_block<256>(P.rows, P.k, P.X, P.ld, P.kcontig != 0, P.amax, P.panel, P.panel2, P.rows_alloc, P.nkc, P.rb,
+                       reinterpret_cast<int*>(smax), threadIdx.x, TeamBar{0, 256});
+  }
+}
+
+// One CTA per SM.  Registers are handed out to whole groups of four warps,
+// so the 19 warps are charged as 20: 96 registers per thread.
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, int PSTG = kPackStages>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
+  constexpr int kEpiWarps = epi_warps(PSTG);
+  constexpr int kPackWarp0 = kEpiWarp0 + kEpiWarps;
+  constexpr bool kFused = PSTG > 0;
   constexpr uint32_t A_BYTES = kBlockBytes;        // 128 rows x 128 B
   constexpr uint32_t B_STAGE = MAXBN * 128;        // room for MAXBN rows x 128 B
   constexpr uint32_t kTmemCols = 2 * MAXBN;        // two accumulator buffers
@@ -183,14 +601,21 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   uint8_t* const base_ptr = smem_raw + (base - raw_addr);
   const uint32_t sA = base;                                   // kStages x A_BYTES
   const uint32_t sB = base + kStages * A_BYTES;               // kStages x B_STAGE
-  const uint32_t bar0 = sB + kStages * B_STAGE;               // barriers
+  const uint32_t sP = sB + kStages * B_STAGE;                 // PSTG packer staging buffers
+  const uint32_t bar0 = sP + PSTG * kStageBytes;              // barriers
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
   auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
   auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(base_ptr + (bar0 - base) + 8 * (2 * kStages + 5));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  auto tqf_bar = [&](int s) { return bar0 + 8u * (2 * kStages + 5 + s); };
+  auto tqe_bar = [&](int s) { return bar0 + 8u * (2 * kStages + 5 + kTileQ + s); };
+  uint8_t* const tail = base_ptr + (bar0 - base) + 8 * (2 * kStages + 5 + 2 * kTileQ);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tail + 4);
+  volatile int* tile_q = reinterpret_cast<volatile int*>(tail + 16);          // kTileQ ints
+  volatile int* pack_slot = reinterpret_cast<volatile int*>(tail + 64);    // 4 ints per packing team
+  uint32_t* team_smax = reinterpret_cast<uint32_t*>(tail + 128);            // 128 words per packing team
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_items = S.num_items();
@@ -199,6 +624,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
     for (int s = 0; s < kStages; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(accf_bar(b), 1); mbar_init(acce_bar(b), kEpiWarps); }
     mbar_init(drain_bar, 1);
+    for (int s = 0; s < kTileQ; ++s) { mbar_init(tqf_bar(s), 1); mbar_init(tqe_bar(s), 2 + kEpiWarps); }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -218,19 +644,42 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
+      int tq = 0;
+      uint32_t tqph = 0;
       int issued_phase[kStages];
       bool issued[kStages];
       for (int s = 0; s < kStages; ++s) { issued[s] = false; issued_phase[s] = 0; }
       bool ok = true;
-      for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x) {
+      while (ok) {
+        if (!mbar_wait_hint(tqe_bar(tq), tqph ^ 1u, abort_flag, timeout_ns, kHintNs)) {
+          raise_status(status, abort_flag);
+          break;
+        }
+        int t = atomicAdd(&S.ctl->tile_next, 1);
+        if (t >= num_items || *abort_flag) t = -1;
+        tile_q[tq] = t;
+        mbar_arrive(tqf_bar(tq));
+        if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
+        if (t < 0) break;
         const TileJob J = S.job(t);
+        if (kFused) {
+          // the panel bands this tile reads must be packed
+          bool ready = wait_counter(S.band_cnt + J.bandA, J.ready, abort_flag, timeout_ns);
+          for (int b = 0; b < J.nbandB && ready; ++b)
+            ready = wait_counter(S.band_cnt + J.bandB0 + b, J.ready, abort_flag, timeout_ns);
+          if (!ready) {
+            raise_status(status, abort_flag);
+            break;
+          }
+          fence_proxy_async_global();
+        }
         const uint32_t b_bytes = (uint32_t)J.bn * 128u;
         // one ring slot per k chunk, and with three parts one more per pair
         // of chunks (the compact [lo3 | lo3] block, loaded with the even chunk)
         for (int kc = 0; kc < J.nkc && ok; ++kc) {
           const int nparts = (J.parts == 2 && (kc & 1) == 0) ? 2 : 1;
           for (int part = 0; part < nparts; ++part) {
-            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, timeout_ns)) {
+            if (!mbar_wait_hint(empty_bar(stage), phase ^ 1u, abort_flag, timeout_ns, kHintNs)) {
               raise_status(status, abort_flag);
               ok = false;
               break;
@@ -261,11 +710,22 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       uint32_t phase = 0;
       int abuf = 0;
       uint32_t aphase = 0;
+      int tq = 0;
+      uint32_t tqph = 0;
+      int* const done = S.done_counters();
       bool ok = true;
-      for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x) {
+      while (ok) {
+        if (!mbar_wait_hint(tqf_bar(tq), tqph, abort_flag, timeout_ns, kHintNs)) {
+          raise_status(status, abort_flag);
+          break;
+        }
+        const int t = tile_q[tq];
+        mbar_arrive(tqe_bar(tq));
+        if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
+        if (t < 0) break;
         const TileJob J = S.job(t);
         const uint32_t idesc = make_idesc_bf16(128, J.bn);
-        if (!mbar_wait(acce_bar(abuf), aphase ^ 1u, abort_flag, timeout_ns)) {
+        if (!mbar_wait_hint(acce_bar(abuf), aphase ^ 1u, abort_flag, timeout_ns, kHintNs)) {
           raise_status(status, abort_flag);
           break;
         }
@@ -277,7 +737,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           // an even chunk also brings the pair's [lo3 | lo3] slot
           const int s0 = stage;
           const uint32_t ph0 = phase;
-          if (!mbar_wait(full_bar(s0), ph0, abort_flag, timeout_ns)) {
+          if (!mbar_wait_hint(full_bar(s0), ph0, abort_flag, timeout_ns, kHintNs)) {
             raise_status(status, abort_flag);
             ok = false;
             break;
@@ -285,7 +745,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           if (J.parts == 2 && (kc & 1) == 0) {
             if (++stage == kStages) { stage = 0; phase ^= 1u; }
             s1 = stage;
-            if (!mbar_wait(full_bar(s1), phase, abort_flag, timeout_ns)) {
+            if (!mbar_wait_hint(full_bar(s1), phase, abort_flag, timeout_ns, kHintNs)) {
               raise_status(status, abort_flag);
               ok = false;
               break;
@@ -321,6 +781,13 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         if (!ok) break;
         mma_commit(accf_bar(abuf));      // the tile's accumulator is complete
         if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+        // Every copy of this tile has landed (each full barrier was waited
+        // on): its panel bytes may now be reused.
+        if (kFused && done && J.problem >= 0) {
+          fence_proxy_async_global();
+          __threadfence();
+          atomicAdd(done + J.problem, 1);
+        }
       }
       // Wait until every MMA issued here has finished before TMEM is released.
       mma_commit(drain_bar);
@@ -328,16 +795,33 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       if (!mbar_wait(drain_bar, 0u, &never, kDrainTimeoutNs)) raise_status(status, abort_flag);
     }
     __syncwarp();
-  } else {
+  } else if (warp < kPackWarp0) {
     // ---------------- epilogue ----------------
     const int q = warp & 3;
-    const int part = (warp - 2) >> 2;  // column part: 0 .. kEpiWarps / 4 - 1
+    const int part = (warp - kEpiWarp0) >> 2;  // column half: 0 or 1
     int abuf = 0;
     uint32_t aphase = 0;
-    for (int t = blockIdx.x; t < num_items; t += gridDim.x) {
+    int tq = 0;
+    uint32_t tqph = 0;
+    for (;;) {
+      int ok = 1, t = -1;
+      if (lane == 0) {
+        ok = mbar_wait_hint(tqf_bar(tq), tqph, abort_flag, timeout_ns, kHintNs) ? 1 : 0;
+        if (ok) {
+          t = tile_q[tq];
+          mbar_arrive(tqe_bar(tq));
+        }
+      }
+      ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+      t = __shfl_sync(0xFFFFFFFFu, t, 0);
+      if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
+      if (!ok) {
+        if (lane == 0) raise_status(status, abort_flag);
+        break;
+      }
+      if (t < 0) break;
       const TileJob J = S.job(t);
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait_hint(accf_bar(abuf), aphase, abort_flag, timeout_ns, 2000u) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait_hint(accf_bar(abuf), aphase, abort_flag, timeout_ns, kHintNs) ? 1 : 0;
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
         if (lane == 0) raise_status(status, abort_flag);
@@ -346,7 +830,8 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       tc_fence_after();
       const int64_t i = J.m0 + q * 32 + lane;
       const bool row_ok = i < J.m;
-      const int ea = row_ok ? scale_exp_from_bits(J.amaxA[i]) : 0;
+      // maxima were built by other CTAs' atomics: read them through L2
+      const int ea = row_ok ? scale_exp_from_bits(__ldcg(J.amaxA + i)) : 0;
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kMaxBN);
       float* const crow = J.C + i;
       const int cols = (J.bn / (kEpiWarps / 4)) > 32 ? J.bn / (kEpiWarps / 4) : 32;
@@ -373,7 +858,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           for (int jj = 0; jj < 32; ++jj) cv[jj] = (row_ok && jj < jmax) ? __ldcs(cp + jj * J.ldc) : 0.f;
         }
         const int64_t jl = J.n0 + c0 + lane;
-        const int eb_l = (jl < J.n) ? scale_exp_from_bits(J.amaxB[jl]) : 0;
+        const int eb_l = (jl < J.n) ? scale_exp_from_bits(__ldcg(J.amaxB + jl)) : 0;
         uint32_t r[32];
         tmem_ld32(taddr + (uint32_t)c0, r);
         // Every lane runs every shuffle; only the stores are predicated.
@@ -392,6 +877,175 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       if (lane == 0) mbar_arrive(acce_bar(abuf));
       if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
     }
+  } else if (warp == kCpfWarp) {
+    // ---------------- C prefetch ----------------
+    // With beta != 0 the epilogue reads the tile's C: ask L2 for it as soon
+    // as the tile is handed out, one to three tiles ahead of the epilogue.
+    int tq = 0;
+    uint32_t tqph = 0;
+    for (;;) {
+      int ok = 1, t = -1;
+      if (lane == 0) {
+        ok = mbar_wait_hint(tqf_bar(tq), tqph, abort_flag, timeout_ns, kHintNs) ? 1 : 0;
+        if (ok) {
+          t = tile_q[tq];
+          mbar_arrive(tqe_bar(tq));
+        }
+      }
+      ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+      t = __shfl_sync(0xFFFFFFFFu, t, 0);
+      if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
+      if (!ok || t < 0) break;
+      const TileJob J = S.job(t);
+      if (J.beta == 0.f || J.partial) continue;
+      const int64_t rows = (J.m - J.m0 < 128) ? J.m - J.m0 : 128;
+      const int64_t ncols = (J.n - J.n0 < J.bn) ? J.n - J.n0 : J.bn;
+      const float* c0 = J.C + J.m0 + J.n0 * J.ldc;
+      for (int64_t j = lane; j < ncols; j += 32) {
+        const char* col = reinterpret_cast<const char*>(c0 + j * J.ldc);
+        for (int64_t off = 0; off < rows * 4; off += 128) prefetch_l2(col + off);
+        prefetch_l2(col + rows * 4 - 4);
+      }
+    }
+  } else if (kFused) {
+    // ---------------- packers ----------------
+    constexpr int NT = PSTG >= 8 ? 2 : 1;  // teams
+    constexpr int NB = PSTG / NT > 0 ? PSTG / NT : 1;  // staging buffers per team
+    constexpr int TS = 256 / NT;           // threads per team
+    constexpr int IT = 256 / TS;           // items per thread and half chunk
+    const int pt = threadIdx.x - kPackWarp0 * 32;
+    const int team = pt / TS, tid = pt % TS;
+    const TeamBar bar{1 + team, TS};
+    volatile int* slot = pack_slot + 4 * team;
+    uint32_t* smax = team_smax + 128 * team;
+    const uint32_t stg0 = sP + (uint32_t)(team * NB) * kStageBytes;
+    const uint8_t* const stg_ptr0 = base_ptr + (stg0 - base);
+    const int n_tasks = S.num_pack_tasks();
+    int* const done = S.done_counters();
+    int verified = -1;  // the last problem whose ring waits this team has seen through
+    int nxt = 0;
+    if (tid == 0) {
+      slot[0] = atomicAdd(&S.ctl->pack_next, 1);
+      nxt = atomicAdd(&S.ctl->pack_next, 1);
+    }
+    bar();
+    const int first = slot[0];
+    PackJob P, N;
+    int nhP = 0, issP = 0, nhN = 0, issN = 0;  // half chunks of a task, and those issued
+    bool haveN = false;
+    int sidx = 0, sissue = 0;  // half-chunk stream: next to split, next to issue (buffer = index % NB)
+    // keep every buffer busy: the current task's half chunks, then the next task's
+    auto refill = [&]() {
+      while (sissue - sidx < NB) {
+        const uint32_t dst = stg0 + (uint32_t)(sissue % NB) * kStageBytes;
+        if (issP < nhP) {
+          stage_any<TS>(P, P.kc0 + (issP >> 1), issP & 1, dst, tid);
+          ++issP;
+        } else if (haveN && issN < nhN) {
+          stage_any<TS>(N, N.kc0 + (issN >> 1), issN & 1, dst, tid);
+          ++issN;
+        } else {
+          break;
+        }
+        ++sissue;
+      }
+    };
+    bool ok = first < n_tasks;
+    if (ok) {
+      P = S.pack_job(first);
+      nhP = 2 * task_chunks(P);
+      refill();
+    }
+    while (ok) {
+      // the next task: its index was taken while the previous one ran
+      if (tid == 0) slot[1] = (*abort_flag) ? n_tasks : nxt;
+      bar();
+      const int ni = slot[1];
+      haveN = ni < n_tasks;
+      issN = 0;
+      if (haveN) {
+        N = S.pack_job(ni);
+        nhN = 2 * task_chunks(N);
+        if (tid == 0) nxt = atomicAdd(&S.ctl->pack_next, 1);
+      }
+      refill();
+      if (P.wait_count > 0 && P.problem != verified) {
+        // the ring bytes of this problem: every earlier problem that wrote
+        // them last must have been read by the GEMM
+        bool wok = true;
+        for (int w = tid; w < P.wait_count && wok; w += TS) {
+          const int qp = P.wait_list[w];
+          wok = wait_counter(done + qp, S.need_of(qp), abort_flag, timeout_ns);
+        }
+        if (bar.any(!wok)) {
+          if (tid == 0) raise_status(status, abort_flag);
+          break;
+        }
+        __threadfence();
+        verified = P.problem;
+      }
+      uint32_t mxr[2][IT];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int it = 0; it < IT; ++it) mxr[h][it] = 0u;
+      for (int c = 0; c < nhP; ++c) {
+        cp_async_wait(sissue - sidx - 1);
+        bar();  // the half chunk has landed for every thread of the team
+        const float* sf = reinterpret_cast<const float*>(stg_ptr0 + (sidx % NB) * kStageBytes);
+        if (P.kcontig) convert_half<true, TS>(P, P.kc0 + (c >> 1), c & 1, sf, tid, mxr);
+        else convert_half<false, TS>(P, P.kc0 + (c >> 1), c & 1, sf, tid, mxr);
+        ++sidx;
+        bar();  // the buffer may be refilled
+        refill();
+      }
+      // the rows' maxima of the task
+      const int64_t r0 = P.rb * 128;
+      for (int r = tid; r < 128; r += TS) smax[r] = 0u;
+      bar();
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          int rr, cc;
+          if (P.kcontig) item_of<true, TS>(tid, it, rr, cc);
+          else item_of<false, TS>(tid, it, rr, cc);
+          if (mxr[h][it] != 0u) atomicMax(&smax[64 * h + rr], mxr[h][it]);
+        }
+      bar();
+      for (int r = tid; r < 128; r += TS)
+        if (r0 + r < P.rows && smax[r] != 0u) atomicMax(&P.amax[r0 + r], smax[r]);
+      // publish the task on its band's counter
+      fence_proxy_async_global();
+      bar();
+      if (tid == 0) {
+        __threadfence();
+        const int old = atomicAdd(S.band_cnt + P.band, 1);
+        __threadfence();  // the other tasks' maxima are visible from here on
+        slot[2] = (old == P.band_tasks - 1) ? 1 : 0;
+      }
+      bar();
+      if (slot[2]) {
+        // this task completed the band: every task's maxima are in, so the
+        // badly scaled rows can be re-packed (usually none), then the band
+        // is marked ready
+        __threadfence();
+        rescale_block<TS>(P.rows, P.k, P.X, P.ld, P.kcontig != 0, P.amax, P.panel, P.panel2, P.rows_alloc, P.nkc,
+                          P.rb, reinterpret_cast<int*>(smax), tid, bar);
+        fence_proxy_async_global();
+        bar();
+        if (tid == 0) {
+          __threadfence();
+          atomicAdd(S.band_cnt + P.band, 1);
+        }
+      }
+      if (!haveN) break;
+      P = N;
+      nhP = nhN;
+      issP = issN;
+      haveN = false;
+    }
+    cp_async_wait(0);  // no copy of this team is left in flight
   }
 
   tc_fence_before();
@@ -404,15 +1058,15 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
 
 // The shared-memory opt-in is a per-device function attribute: set it once
 // for every device a kernel instance is launched on.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, int PSTG = kPackStages>
 cudaError_t ensure_gemm_smem_attr() {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             gemm_smem_bytes<STAGES, MAXBN>());
+    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN, PSTG>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem_bytes<STAGES, MAXBN, PSTG>());
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }

@@ -4,9 +4,11 @@
 // across problems: every problem is cut into tiles, the tiles of all
 // problems form one work list per kernel, and persistent CTAs drain it.
 //
-// Graph (one launch): [zero row maxima] -> grouped pack -> grouped re-pack
-// of badly scaled vectors -> grouped tcgen05 GEMM over all split-path
-// problems -> one grouped SIMT kernel per SIMT tile shape.
+// Graph (one launch): zero the counters and row maxima, then one persistent
+// tcgen05 kernel whose packer warps split the operands of the split-path
+// problems into a panel ring that stays in L2 while its tile roles multiply
+// them; the SIMT-configured problems run on side branches, one grouped SIMT
+// kernel per tile shape and variant.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -18,47 +20,6 @@
 
 namespace gbg {
 namespace {
-
-// One operand of one split-path problem, as seen by the packing kernels.
-struct PackTask {
-  const float* X;
-  int64_t ld;
-  uint32_t* amax;
-  uint8_t* panel;
-  uint8_t* panel2;         // compact lo3 panel of a three-part split, else NULL
-  int64_t rows, k;
-  int64_t rb_count, nkc;   // 128-row blocks per k chunk, k chunks
-  int64_t rows_alloc;      // panel rows per k chunk (rows rounded up to 8)
-  int64_t block_begin;     // first pack-kernel block of this task
-  int64_t rowblock_begin;  // first rescale-kernel block of this task
-  int kcontig;
-  int pad_;
-};
-
-// block_task[b]: the task of pack-kernel block b (and, for the re-pack
-// kernel, of row block b), built on the host at plan creation.  A pack
-// block splits kPackChunks consecutive k chunks of one 128-row block, with
-// all their loads in flight at once.
-constexpr int kPackChunks = 2;
-__global__ void __launch_bounds__(256) grouped_pack_kernel(const PackTask* __restrict__ tasks,
-                                                           const int* __restrict__ block_task) {
-  __shared__ uint32_t smax[128];
-  const PackTask T = tasks[block_task[blockIdx.x]];
-  const int64_t local = (int64_t)blockIdx.x - T.block_begin;
-  const int64_t rb = local % T.rb_count, kc0 = (local / T.rb_count) * kPackChunks;
-  if (T.kcontig)
-    pack_block<true, kPackChunks>(T.rows, T.k, T.X, T.ld, T.amax, T.panel, T.panel2, T.rows_alloc, rb, kc0, smax, T.nkc);
-  else
-    pack_block<false, kPackChunks>(T.rows, T.k, T.X, T.ld, T.amax, T.panel, T.panel2, T.rows_alloc, rb, kc0, smax, T.nkc);
-}
-
-__global__ void __launch_bounds__(256) grouped_rescale_kernel(const PackTask* __restrict__ tasks,
-                                                              const int* __restrict__ rowblock_task) {
-  __shared__ int se[128];
-  const PackTask T = tasks[rowblock_task[blockIdx.x]];
-  const int64_t rb = (int64_t)blockIdx.x - T.rowblock_begin;
-  rescale_block(T.rows, T.k, T.X, T.ld, T.kcontig != 0, T.amax, T.panel, T.panel2, T.rows_alloc, T.nkc, rb, se);
-}
 
 // Items: x = problem index into `probs`, y = tile row, z = tile column.
 // One launch per tile shape and (transpose, vector-load) variant, so each
@@ -135,12 +96,12 @@ int validate_problem(const gbgemm_problem& q) {
 
 bool config_legal(const gbgemm_problem& q, int cfg) {
   if (cfg < 0 || cfg >= GBGEMM_NUM_CONFIGS) return false;
-  if (cfg >= GBGEMM_CFG_SPLIT_BN64) return q.k >= kSplitMinK && q.alpha != 0.0f;
+  if (cfg >= GBGEMM_CFG_SPLIT_BN64) return q.k >= kSplitShortK && q.alpha != 0.0f;
   return true;
 }
 
 int default_config(const gbgemm_problem& q) {
-  if (q.k >= kSplitMinK && q.alpha != 0.0f) return q.n <= 64 ? GBGEMM_CFG_SPLIT_BN64 : GBGEMM_CFG_SPLIT_BN128;
+  if (q.k >= kSplitShortK && q.alpha != 0.0f) return q.n <= 64 ? GBGEMM_CFG_SPLIT_BN64 : GBGEMM_CFG_SPLIT_BN128;
   // SIMT: the tile shape with the least padded area (ties to the larger tile)
   auto area = [&](int64_t bm, int64_t bn) { return ((q.m + bm - 1) / bm) * bm * (((q.n + bn - 1) / bn) * bn); };
   const int64_t a_big = area(128, 128), a_wide = area(128, 64), a_small = area(64, 64);
@@ -158,6 +119,33 @@ void simt_tile_shape(int cfg, int& bm, int& bn) {
   }
 }
 
+void ring_layout(const std::vector<size_t>& sizes, size_t ring, size_t granule, std::vector<size_t>& off,
+                 std::vector<int>& wait_begin, std::vector<int>& wait_count, std::vector<int>& wait_list) {
+  const size_t n = sizes.size();
+  off.assign(n, 0);
+  wait_begin.assign(n, 0);
+  wait_count.assign(n, 0);
+  wait_list.clear();
+  std::vector<int> last_writer(ring / granule + 1, -1);
+  std::vector<int> seen(n, -1);
+  size_t o = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (o + sizes[i] > ring) o = 0;
+    off[i] = o;
+    wait_begin[i] = (int)wait_list.size();
+    for (size_t gr = o / granule; gr < (o + sizes[i]) / granule; ++gr) {
+      const int w = last_writer[gr];
+      if (w >= 0 && seen[w] != (int)i) {
+        seen[w] = (int)i;
+        wait_list.push_back(w);
+      }
+      last_writer[gr] = (int)i;
+    }
+    wait_count[i] = (int)wait_list.size() - wait_begin[i];
+    o += sizes[i];
+  }
+}
+
 GroupedPlan::~GroupedPlan() {
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -166,17 +154,17 @@ GroupedPlan::~GroupedPlan() {
 
 int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t count, const int* configs,
                        cudaStream_t capture_stream) {
-  // ---- classify and lay out device memory ----
-  std::vector<PackTask> tasks;
-  std::vector<GroupDev> gdev;
-  std::vector<int64_t> split_of;           // problem index of each split group
+  // ---- classify ----
+  struct SplitProb {
+    int64_t g;             // index into probs
+    int bn, nkc, parts, ra, rb, tiles;
+    int64_t rowsA, rowsB;
+    size_t offA, offB, offA2, offB2, size;  // ring layout
+    double cost;           // per tile: k chunks x width x products
+  };
+  std::vector<SplitProb> sp;
   std::vector<Problem> sprobs;             // SIMT problems
   std::vector<int> simt_cfg;
-  struct Region { size_t off, bytes; };
-  size_t off = 0;
-  auto take = [&](size_t bytes) { Region r{off, bytes}; off = align256(off + bytes); return r; };
-  std::vector<Region> panelA_r, panelB_r, panelA2_r, panelB2_r;
-  int64_t amax_words = 0;
   P->flops_split = P->flops_simt = 0.0;
   for (int64_t g = 0; g < count; ++g) {
     const gbgemm_problem& q = probs[g];
@@ -186,26 +174,19 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     if (!use_ab && q.beta == 1.0f) continue;
     const int ta = trans_code_g(q.transa), tb = trans_code_g(q.transb);
     if (use_ab && cfg >= GBGEMM_CFG_SPLIT_BN64) {
-      // Compact panels: rows rounded up to 8 per k chunk.  A tile copy may
-      // run past the last row into the next chunk (or, for the last chunk,
-      // into 32 KiB of slack): those rows feed only outputs that are never
-      // stored.
-      const int bn = config_bn(cfg);
-      const int64_t rowsA = (q.m + 7) / 8 * 8, rowsB = (q.n + 7) / 8 * 8;
-      const int64_t nkc = panel_k_chunks(q.k);
-      const int parts = split_parts(q.k);
-      panelA_r.push_back(take((size_t)rowsA * nkc * 128 + 32768));
-      panelB_r.push_back(take((size_t)rowsB * nkc * 128 + 32768));
-      // three parts: compact [lo3 | lo3] panels, one block per pair of k chunks
-      panelA2_r.push_back(parts == 2 ? take((size_t)rowsA * ((nkc + 1) / 2) * 128 + 32768) : Region{0, 0});
-      panelB2_r.push_back(parts == 2 ? take((size_t)rowsB * ((nkc + 1) / 2) * 128 + 32768) : Region{0, 0});
-      split_of.push_back(g);
-      GroupDev d{};
-      d.m = q.m; d.n = q.n; d.nkc = (int)nkc; d.bn = bn; d.rowsA = rowsA; d.rowsB = rowsB;
-      d.parts = parts;
-      d.alpha = q.alpha; d.beta = q.beta; d.C = q.C; d.ldc = q.ldc;
-      gdev.push_back(d);
-      amax_words += q.m + q.n;
+      SplitProb x{};
+      x.g = g;
+      x.bn = config_bn(cfg);
+      x.nkc = (int)panel_k_chunks(q.k);
+      x.parts = split_parts(q.k);
+      x.ra = (int)((q.m + 127) / 128);
+      x.rb = (int)((q.n + 127) / 128);
+      x.tiles = x.ra * (int)((q.n + x.bn - 1) / x.bn);
+      // compact panels: rows rounded up to 8 per k chunk
+      x.rowsA = (q.m + 7) / 8 * 8;
+      x.rowsB = (q.n + 7) / 8 * 8;
+      x.cost = (double)x.nkc * x.bn * (x.parts == 2 ? 2.0 : 1.0);
+      sp.push_back(x);
       P->flops_split += 2.0 * q.m * q.n * q.k;
     } else {
       Problem p{ta, tb, q.m, q.n, use_ab ? q.k : 0, use_ab ? q.alpha : 0.0f, q.beta, q.A, q.lda, q.B, q.ldb, q.C, q.ldc};
@@ -214,18 +195,111 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
       if (use_ab) P->flops_simt += 2.0 * q.m * q.n * q.k;
     }
   }
-  const Region amax_r = take((size_t)amax_words * 4 + 4);
-  // work lists
-  std::vector<int4> split_items;
-  for (size_t s = 0; s < gdev.size(); ++s) {
-    const int64_t tm = (gdev[s].m + 127) / 128, tn = (gdev[s].n + gdev[s].bn - 1) / gdev[s].bn;
-    for (int64_t i = 0; i < tm; ++i)
-      for (int64_t j = 0; j < tn; ++j) split_items.push_back(make_int4((int)s, (int)i, (int)j, 0));
+  // Packing and tile order: problem after problem, costlier tiles first, so
+  // that the cheap tiles come last and even out the CTAs' finishing times.
+  std::stable_sort(sp.begin(), sp.end(), [](const SplitProb& a, const SplitProb& b) { return a.cost > b.cost; });
+
+  // ---- the panel ring ----
+  // Each problem's panels ([hi | lo] or [hi | mid] of op(A) and op(B), and
+  // with three parts the compact lo3 panels) take one contiguous region of a
+  // ring of ring_bytes, whole granules of kGranule bytes, allocated in
+  // packing order and wrapping to the start when the next region does not
+  // fit.  A problem may be packed once every problem that last wrote one of
+  // its granules has been read by the GEMM (its wait list).  When the whole
+  // batch fits, nothing waits.  A tile copy may run up to 32 KiB past its
+  // panel's end: into the next region, or into slack after the ring; those
+  // rows only feed outputs that are never stored.
+  constexpr size_t kGranule = 4096;
+  auto gran = [&](size_t x) { return (x + kGranule - 1) / kGranule * kGranule; };
+  size_t total = 0, largest = 0;
+  for (SplitProb& x : sp) {
+    const size_t a = gran((size_t)x.rowsA * x.nkc * 128), b = gran((size_t)x.rowsB * x.nkc * 128);
+    const int pairs = (x.nkc + 1) / 2;
+    const size_t a2 = x.parts == 2 ? gran((size_t)x.rowsA * pairs * 128) : 0;
+    const size_t b2 = x.parts == 2 ? gran((size_t)x.rowsB * pairs * 128) : 0;
+    x.offA = 0; x.offB = a; x.offA2 = a + b; x.offB2 = a + b + a2;
+    x.size = a + b + a2 + b2;
+    total += x.size;
+    largest = std::max(largest, x.size);
   }
-  // Longest-processing-time order: costlier tiles first (k chunks x tile width).
-  std::stable_sort(split_items.begin(), split_items.end(), [&](const int4& a, const int4& b) {
-    return (int64_t)gdev[a.x].nkc * gdev[a.x].bn > (int64_t)gdev[b.x].nkc * gdev[b.x].bn;
-  });
+  size_t ring = P->ring_bytes > 0 ? gran(P->ring_bytes) : kGroupedRingBytes;
+  ring = std::max(ring, largest);
+  // packed ahead of the GEMM, every panel needs its own bytes
+  if (total <= ring || !P->fused) ring = total;
+  std::vector<size_t> sizes(sp.size());
+  for (size_t i = 0; i < sp.size(); ++i) sizes[i] = sp[i].size;
+  std::vector<int> wait_list, wait_begin, wait_count;
+  std::vector<size_t> ring_off;
+  ring_layout(sizes, ring, kGranule, ring_off, wait_begin, wait_count, wait_list);
+
+  // ---- bands, packing tasks, tiles ----
+  std::vector<PackBand> bands;
+  std::vector<int> task_band;
+  std::vector<int4> split_items;
+  std::vector<GroupDev> gdev(sp.size());
+  std::vector<int> need(sp.size());
+  int64_t amax_words = 0, n_cnt = 0;
+  for (size_t i = 0; i < sp.size(); ++i) {
+    amax_words += probs[sp[i].g].m + probs[sp[i].g].n;
+    n_cnt += sp[i].ra + sp[i].rb;
+  }
+  if (n_cnt > 0x3FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
+  struct Region { size_t off, bytes; };
+  size_t off = 0;
+  auto take = [&](size_t bytes) { Region r{off, bytes}; off = align256(off + bytes); return r; };
+  const Region ctl_r = take(kSplitCtlBytes);
+  const Region cnt_r = take((size_t)n_cnt * 4);
+  const Region done_r = take(sp.size() * 4);
+  const Region amax_r = take((size_t)amax_words * 4 + 4);
+  const size_t head_bytes = off;
+  int64_t cnt_base = 0, aw = 0;
+  for (size_t i = 0; i < sp.size(); ++i) {
+    const SplitProb& x = sp[i];
+    const gbgemm_problem& q = probs[x.g];
+    GroupDev& d = gdev[i];
+    d.m = q.m; d.n = q.n; d.nkc = x.nkc; d.bn = x.bn; d.rowsA = x.rowsA; d.rowsB = x.rowsB;
+    d.parts = x.parts;
+    d.ready = (x.nkc + kPackChunks - 1) / kPackChunks + 1;
+    d.alpha = q.alpha; d.beta = q.beta; d.C = q.C; d.ldc = q.ldc;
+    d.bandA0 = (int)cnt_base;
+    d.bandB0 = (int)cnt_base + x.ra;
+    d.rbB = x.rb;
+    need[i] = x.tiles;
+    // bands in the order of the first tile that reads them (tiles go column
+    // of tiles by column of tiles): op(B)'s bands of tile column 0, every
+    // band of op(A), the remaining bands of op(B)
+    const int nb0 = std::min(x.rb, std::max(1, x.bn >> 7));
+    const int ngroups = (x.nkc + kPackChunks - 1) / kPackChunks;
+    const int ta = trans_code_g(q.transa), tb = trans_code_g(q.transb);
+    auto add_band = [&](bool is_a, int j) {
+      PackBand b{};
+      b.X = is_a ? q.A : q.B;
+      b.ld = is_a ? q.lda : q.ldb;
+      b.rows = is_a ? q.m : q.n;
+      b.k = q.k;
+      b.rows_alloc = is_a ? x.rowsA : x.rowsB;
+      b.rb = j;
+      b.nkc = x.nkc;
+      b.kcontig = is_a ? (ta == 1) : (tb == 0);
+      b.ngroups = ngroups;
+      b.first_task = (int)task_band.size();
+      b.problem = (int)i;
+      b.wait_begin = wait_begin[i];
+      b.wait_count = wait_count[i];
+      b.cnt = (int)cnt_base + (is_a ? 0 : x.ra) + j;
+      for (int t = 0; t < ngroups; ++t) task_band.push_back((int)bands.size());
+      bands.push_back(b);
+    };
+    for (int j = 0; j < nb0; ++j) add_band(false, j);
+    for (int j = 0; j < x.ra; ++j) add_band(true, j);
+    for (int j = nb0; j < x.rb; ++j) add_band(false, j);
+    const int tn = (int)((q.n + x.bn - 1) / x.bn);
+    for (int c = 0; c < tn; ++c)
+      for (int r = 0; r < x.ra; ++r) split_items.push_back(make_int4((int)i, r, c, 0));
+    cnt_base += x.ra + x.rb;
+    aw += q.m + q.n;
+  }
+  if (task_band.size() > 0x7FFFFFFF || split_items.size() > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
   std::vector<int4> simt_items[3 * 8];  // index: config * 8 + variant
   for (size_t s = 0; s < sprobs.size(); ++s) {
     int bm, bn;
@@ -242,20 +316,14 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     std::stable_sort(v.begin(), v.end(), [&](const int4& a, const int4& b) { return sprobs[a.x].k > sprobs[b.x].k; });
   const Region gdev_r = take(gdev.size() * sizeof(GroupDev) + 16);
   const Region sitems_r = take(split_items.size() * sizeof(int4) + 16);
+  const Region bands_r = take(bands.size() * sizeof(PackBand) + 16);
+  const Region tband_r = take(task_band.size() * 4 + 16);
+  const Region wait_r = take(wait_list.size() * 4 + 16);
+  const Region need_r = take(need.size() * 4 + 16);
   const Region sprob_r = take(sprobs.size() * sizeof(Problem) + 16);
   Region simt_items_r[24];
   for (int c = 0; c < 24; ++c) simt_items_r[c] = take(simt_items[c].size() * sizeof(int4) + 16);
-  const Region tasks_r = take(2 * gdev.size() * sizeof(PackTask) + 16);
-  // block -> task maps of the packing kernels (sized below, once the tasks are known)
-  int64_t n_blocks = 0, n_rowblocks = 0;
-  for (size_t s = 0; s < gdev.size(); ++s) {
-    const gbgemm_problem& q = probs[split_of[s]];
-    n_blocks += ((q.m + 127) / 128 + (q.n + 127) / 128) * ((gdev[s].nkc + kPackChunks - 1) / kPackChunks);
-    n_rowblocks += (q.m + 127) / 128 + (q.n + 127) / 128;
-  }
-  if (n_blocks > 0x7FFFFFFF || n_rowblocks > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
-  const Region bmap_r = take((size_t)n_blocks * 4 + 16);
-  const Region rmap_r = take((size_t)n_rowblocks * 4 + 16);
+  const Region ring_r = take(sp.empty() ? 16 : ring + 32768);
 
   if (off > 0 && cudaMalloc(&P->dmem, off) != cudaSuccess) {
     cudaGetLastError();
@@ -263,72 +331,69 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     return GBGEMM_ERR_ALLOC;
   }
   P->dbytes = off;
+  P->ring_used = sp.empty() ? 0 : ring;
   uint8_t* base = static_cast<uint8_t*>(P->dmem);
-  // fill pointers
-  int64_t aw = 0;
+  // device addresses of the panels and maxima
   uint32_t* amax_base = reinterpret_cast<uint32_t*>(base + amax_r.off);
-  int64_t blocks = 0, rowblocks = 0;
-  for (size_t s = 0; s < gdev.size(); ++s) {
-    const gbgemm_problem& q = probs[split_of[s]];
-    GroupDev& d = gdev[s];
-    d.panelA = base + panelA_r[s].off;
-    d.panelB = base + panelB_r[s].off;
-    uint8_t* pA2 = d.parts == 2 ? base + panelA2_r[s].off : nullptr;
-    uint8_t* pB2 = d.parts == 2 ? base + panelB2_r[s].off : nullptr;
-    d.a_part = d.parts == 2 ? (int64_t)(pA2 - d.panelA) : 0;
-    d.b_part = d.parts == 2 ? (int64_t)(pB2 - d.panelB) : 0;
+  aw = 0;
+  std::vector<uint8_t*> pa(sp.size()), pb(sp.size()), pa2(sp.size()), pb2(sp.size());
+  for (size_t i = 0; i < sp.size(); ++i) {
+    const SplitProb& x = sp[i];
+    const gbgemm_problem& q = probs[x.g];
+    uint8_t* r0 = base + ring_r.off + ring_off[i];
+    pa[i] = r0 + x.offA;
+    pb[i] = r0 + x.offB;
+    pa2[i] = x.parts == 2 ? r0 + x.offA2 : nullptr;
+    pb2[i] = x.parts == 2 ? r0 + x.offB2 : nullptr;
+    GroupDev& d = gdev[i];
+    d.panelA = pa[i];
+    d.panelB = pb[i];
+    d.a_part = x.parts == 2 ? (int64_t)(pa2[i] - pa[i]) : 0;
+    d.b_part = x.parts == 2 ? (int64_t)(pb2[i] - pb[i]) : 0;
     d.amaxA = amax_base + aw;
     d.amaxB = amax_base + aw + q.m;
     aw += q.m + q.n;
-    const int ta = trans_code_g(q.transa), tb = trans_code_g(q.transb);
-    const int64_t rbA = (q.m + 127) / 128, rbB = (q.n + 127) / 128;
-    PackTask ta_{q.A, q.lda, const_cast<uint32_t*>(d.amaxA), const_cast<uint8_t*>(d.panelA), pA2, q.m, q.k,
-                 rbA, d.nkc, d.rowsA, blocks, rowblocks, ta == 1, 0};
-    blocks += rbA * ((d.nkc + kPackChunks - 1) / kPackChunks);
-    rowblocks += rbA;
-    PackTask tb_{q.B, q.ldb, const_cast<uint32_t*>(d.amaxB), const_cast<uint8_t*>(d.panelB), pB2, q.n, q.k,
-                 rbB, d.nkc, d.rowsB, blocks, rowblocks, tb == 0, 0};
-    blocks += rbB * ((d.nkc + kPackChunks - 1) / kPackChunks);
-    rowblocks += rbB;
-    tasks.push_back(ta_);
-    tasks.push_back(tb_);
   }
-  std::vector<int> bmap((size_t)blocks), rmap((size_t)rowblocks);
-  for (size_t t = 0; t < tasks.size(); ++t) {
-    const int64_t nb = tasks[t].rb_count * ((tasks[t].nkc + kPackChunks - 1) / kPackChunks);
-    for (int64_t b = 0; b < nb; ++b) bmap[(size_t)(tasks[t].block_begin + b)] = (int)t;
-    for (int64_t b = 0; b < tasks[t].rb_count; ++b) rmap[(size_t)(tasks[t].rowblock_begin + b)] = (int)t;
+  for (PackBand& b : bands) {
+    const int i = b.problem;
+    const bool is_a = b.cnt < gdev[i].bandB0;
+    b.amax = const_cast<uint32_t*>(is_a ? gdev[i].amaxA : gdev[i].amaxB);
+    b.panel = is_a ? pa[i] : pb[i];
+    b.panel2 = is_a ? pa2[i] : pb2[i];
   }
   auto h2d = [&](const Region& r, const void* src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(base + r.off, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   bool ok = h2d(gdev_r, gdev.data(), gdev.size() * sizeof(GroupDev)) &&
             h2d(sitems_r, split_items.data(), split_items.size() * sizeof(int4)) &&
-            h2d(sprob_r, sprobs.data(), sprobs.size() * sizeof(Problem)) &&
-            h2d(tasks_r, tasks.data(), tasks.size() * sizeof(PackTask)) &&
-            h2d(bmap_r, bmap.data(), bmap.size() * 4) && h2d(rmap_r, rmap.data(), rmap.size() * 4);
+            h2d(bands_r, bands.data(), bands.size() * sizeof(PackBand)) &&
+            h2d(tband_r, task_band.data(), task_band.size() * 4) && h2d(wait_r, wait_list.data(), wait_list.size() * 4) &&
+            h2d(need_r, need.data(), need.size() * 4) && h2d(sprob_r, sprobs.data(), sprobs.size() * sizeof(Problem));
   for (int c = 0; c < 24; ++c) ok = ok && h2d(simt_items_r[c], simt_items[c].data(), simt_items[c].size() * sizeof(int4));
   if (!ok) return GBGEMM_ERR_CUDA;
-  P->n_split = (int64_t)gdev.size();
+  P->n_split = (int64_t)sp.size();
   P->n_simt = (int64_t)sprobs.size();
   P->split_tiles = (int64_t)split_items.size();
   P->kernels_per_run = 0;
 
   // ---- capture the graph ----
-  if (blocks > 0x7FFFFFFF || rowblocks > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
   // Tiles of at most 128 columns everywhere: the six-slot ring instance.
   bool narrow = true;
   for (const GroupDev& gd : gdev) narrow = narrow && gd.bn <= kNarrowBN;
   if (!gdev.empty()) {
-    const cudaError_t ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowStages, kNarrowBN>()
-                                  : ensure_gemm_smem_attr<GroupedSched>();
+    cudaError_t ea;
+    if (P->fused)
+      ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowStages, kNarrowBN, kNarrowPackStages>()
+                  : ensure_gemm_smem_attr<GroupedSched>();
+    else
+      ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowPrepackStages, kNarrowBN, 0>()
+                  : ensure_gemm_smem_attr<GroupedSched, kStages, kMaxBN, 0>();
     if (ea != cudaSuccess) return GBGEMM_ERR_CUDA;
   }
   // Graph: the SIMT launches run on side branches, concurrently with the
-  // split chain (packing, re-packing, tcgen05 GEMM) on the main branch; the
-  // branches join at the end.  (Holding the GEMM back until the SIMT
-  // branches finish, so that they overlap the memory-bound packing, measured
-  // 1% slower.)
+  // split kernel on the main branch; the branches join at the end.  The
+  // split kernel hands out its tiles and packing tasks dynamically, so it
+  // needs no SM to itself while the branches run.
   constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, joins[kSide] = {};
@@ -372,29 +437,44 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   }
   P->kernels_per_run += simt_launches;
   if (!gdev.empty() && e == cudaSuccess) {
-    const PackTask* dt = reinterpret_cast<const PackTask*>(base + tasks_r.off);
-    e = cudaMemsetAsync(amax_base, 0, (size_t)amax_words * 4, capture_stream);
-    if (e == cudaSuccess) {
-      const int* dbmap = reinterpret_cast<const int*>(base + bmap_r.off);
-      const int* drmap = reinterpret_cast<const int*>(base + rmap_r.off);
-      grouped_pack_kernel<<<(unsigned)blocks, 256, 0, capture_stream>>>(dt, dbmap);
-      grouped_rescale_kernel<<<(unsigned)rowblocks, 256, 0, capture_stream>>>(dt, drmap);
-      P->kernels_per_run += 2;
-    }
-  }
-  if (!gdev.empty() && e == cudaSuccess) {
+    e = cudaMemsetAsync(base, 0, head_bytes, capture_stream);
     GroupedSched S;
+    S.ctl = reinterpret_cast<WorkCtl*>(base + ctl_r.off);
+    S.band_cnt = reinterpret_cast<int*>(base + cnt_r.off);
+    S.done = reinterpret_cast<int*>(base + done_r.off);
     S.items = reinterpret_cast<const int4*>(base + sitems_r.off);
     S.groups = reinterpret_cast<const GroupDev*>(base + gdev_r.off);
+    S.bands = reinterpret_cast<const PackBand*>(base + bands_r.off);
+    S.task_band = reinterpret_cast<const int*>(base + tband_r.off);
+    S.wait_list = reinterpret_cast<const int*>(base + wait_r.off);
+    S.need = reinterpret_cast<const int*>(base + need_r.off);
     S.n_items = (int)split_items.size();
-    const int grid = (int)std::min<int64_t>((int64_t)split_items.size(), P->num_sms);
-    if (narrow)
-      split_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN>
-          <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowStages, kNarrowBN>(), capture_stream>>>(S, P->status,
-                                                                                               kTimeoutNs);
-    else
-      split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status, kTimeoutNs);
-    P->kernels_per_run += 1;
+    S.n_tasks = (int)task_band.size();
+    if (e == cudaSuccess && P->fused) {
+      const int grid = (int)std::min<int64_t>(
+          std::max<int64_t>((int64_t)split_items.size(), (int64_t)task_band.size()), P->num_sms);
+      if (narrow)
+        split_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN, kNarrowPackStages>
+            <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowStages, kNarrowBN, kNarrowPackStages>(), capture_stream>>>(
+                S, P->status, kTimeoutNs);
+      else
+        split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status,
+                                                                                              kTimeoutNs);
+      P->kernels_per_run += 2;  // the memset and the kernel
+    } else if (e == cudaSuccess) {
+      // every packing task as its own CTA, then the GEMM without packer warps
+      pack_tasks_kernel<GroupedSched><<<(unsigned)task_band.size(), 256, 0, capture_stream>>>(S);
+      const int grid = (int)std::min<int64_t>((int64_t)split_items.size(), P->num_sms);
+      if (narrow)
+        split_gemm_kernel<GroupedSched, kNarrowPrepackStages, kNarrowBN, 0>
+            <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowPrepackStages, kNarrowBN, 0>(), capture_stream>>>(
+                S, P->status, kTimeoutNs);
+      else
+        split_gemm_kernel<GroupedSched, kStages, kMaxBN, 0>
+            <<<grid, kGemmThreads, gemm_smem_bytes<kStages, kMaxBN, 0>(), capture_stream>>>(S, P->status,
+                                                                                           kTimeoutNs);
+      P->kernels_per_run += 3;  // the memset, the packing and the GEMM
+    }
   }
   for (int i = 0; i < kSide && e == cudaSuccess; ++i) {
     e = cudaEventRecord(joins[i], side[i]);
@@ -419,3 +499,30 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
 }
 
 }  // namespace gbg
+
+extern "C" int gbgemm_grouped_ring_layout(const uint64_t* sizes, int64_t count, uint64_t ring_bytes,
+                                          uint64_t granule, uint64_t* offsets, int32_t* wait_begin,
+                                          int32_t* wait_count, int32_t* wait_list, int64_t wait_capacity,
+                                          int64_t* wait_total) {
+  if (count < 0 || (count > 0 && (!sizes || !offsets || !wait_begin || !wait_count)) || !wait_total ||
+      granule == 0 || wait_capacity < 0 || (wait_capacity > 0 && !wait_list))
+    return GBGEMM_ERR_INVALID_VALUE;
+  std::vector<size_t> sz((size_t)count);
+  for (int64_t i = 0; i < count; ++i) {
+    if (sizes[i] == 0 || sizes[i] % granule != 0 || sizes[i] > ring_bytes) return GBGEMM_ERR_INVALID_VALUE;
+    sz[(size_t)i] = (size_t)sizes[i];
+  }
+  if (ring_bytes % granule != 0) return GBGEMM_ERR_INVALID_VALUE;
+  std::vector<size_t> off;
+  std::vector<int> wb, wc, wl;
+  gbg::ring_layout(sz, (size_t)ring_bytes, (size_t)granule, off, wb, wc, wl);
+  for (int64_t i = 0; i < count; ++i) {
+    offsets[i] = off[(size_t)i];
+    wait_begin[i] = wb[(size_t)i];
+    wait_count[i] = wc[(size_t)i];
+  }
+  *wait_total = (int64_t)wl.size();
+  if ((int64_t)wl.size() > wait_capacity) return GBGEMM_ERR_INVALID_VALUE;
+  for (size_t i = 0; i < wl.size(); ++i) wait_list[i] = wl[i];
+  return GBGEMM_OK;
+}

@@ -82,7 +82,9 @@ cudaError_t launch_lu_trsv_sweep(bool upper, int n, const float* LU, int64_t lda
 constexpr int kPanelRows = 128;     // rows per panel block
 constexpr int kPanelK = 32;         // k per panel block (hi and lo: 64 BF16 = 128 bytes per row)
 constexpr int kBlockBytes = kPanelRows * 128;  // 16 KiB
+constexpr int kSplitCtlBytes = 256; // per-launch control words of the fused split GEMM
 constexpr int kSplitMinK = 128;     // AUTO uses the split path from this k upwards
+constexpr int kSplitShortK = 16;    // the split path holds the bound from this k (grouped configurations)
 constexpr int kSplitTwoPartK = 512; // from this k two BF16 parts (3 products) meet the bound; below, three parts (6 products)
 
 // Number of panel parts of the split path for a given k: 1 ([hi | lo]) or 2 ([hi | mid] and compact lo3).
@@ -94,42 +96,54 @@ inline size_t panel_bytes(int64_t rows, int64_t k) {
   return (size_t)panel_row_blocks(rows) * (size_t)panel_k_chunks(k) * (size_t)kBlockBytes;
 }
 
-// Split one operand: one pass packs the unscaled hi/lo panel and records
-// every K-vector's max |x|, a second pass re-packs the badly scaled vectors
-// (max outside [2^-48, 2^48)).  `kcontig` selects the view: element (r, p) =
-// X[r*ld + p] (kcontig) or X[r + p*ld] (!kcontig).  amax_bits must hold
-// `rows` words; it is zeroed here.
-// With three parts (k < kSplitTwoPartK) panel2 (allocated with the size of
-// `panel`) receives the compact lo3 panel: block (kc / 2, rb) holds lo3 of k
-// chunk kc in logical chunks 4 (kc % 2) .. 4 (kc % 2) + 3; otherwise panel2 is
-// ignored (may be NULL).
-cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
-                              uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s);
-// The same for a strided batch (batch <= 65535): problem z reads X + z*xs and
-// writes amax_bits + z*as (as >= rows) and panel(2) + z*ps.
-cudaError_t launch_split_pack_batched(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
-                                      uint32_t* amax_bits, void* panel, void* panel2, int64_t batch, int64_t xs,
-                                      int64_t as, int64_t ps, cudaStream_t s);
+// Workspace of one split-path call (or strided batch), in bytes from its
+// start: [control words | band counters | row maxima | per problem: panel A,
+// panel B (and with three parts the compact lo3 panels A2, B2) | split-K
+// partials].  The head (control words, band counters, maxima) is zeroed
+// before every launch.
+struct SplitLayout {
+  size_t bands;           // band counters
+  size_t band_off, amax_off, head;
+  int64_t amax_stride;    // words between problems' maxima (m + n; op(B)'s follow op(A)'s)
+  size_t pa, pb, block;   // panel bytes of op(A), op(B), and per problem
+  size_t panel_off, partial_off, total;
+};
+SplitLayout split_layout(int64_t m, int64_t n, int64_t k, int64_t batch, int splitk, int bn);
+
+// One split-path call: packing fused into the persistent tcgen05 GEMM.
+struct SplitCall {
+  int ta = 0, tb = 0;
+  int64_t m = 0, n = 0, k = 0;
+  float alpha = 1.f, beta = 0.f;
+  const float* A = nullptr; int64_t lda = 1;
+  const float* B = nullptr; int64_t ldb = 1;
+  float* C = nullptr; int64_t ldc = 1;
+  int64_t batch = 1, sa = 0, sb = 0, sc = 0;  // strided batch: problem z at A + z*sa, B + z*sb, C + z*sc
+  int bn = 256;          // tile width: 64, 128 or 256
+  int raster = 16;       // tile rows per group of the tile order
+  int splitk = 1;        // k slices (batch 1, k >= kSplitTwoPartK)
+  void* ws = nullptr;    // split_layout(...).total bytes
+  int* status = nullptr;
+  int num_sms = 0;
+  // packing inside the GEMM kernel (its packer warps) or by a separate
+  // launch ahead of it
+  bool fused = true;
+  // panel inspection: pack op(A)'s rows only, into these caller buffers
+  bool pack_only = false;
+  void* panel_out = nullptr;
+  void* panel2_out = nullptr;
+  uint32_t* amax_out = nullptr;
+};
+// Zero the workspace head, run the fused kernel (and the split-K reduction).
+cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s);
 
 struct SplitGemmArgs {
-  const void* panelA; const void* panelB;     // [hi | lo] (or [hi | mid]) panels
-  const void* panelA2; const void* panelB2;   // compact lo3 panels when split_parts(k) == 2
   const uint32_t* amaxA; const uint32_t* amaxB;
   int64_t m, n, k;
   float alpha, beta;
   float* C; int64_t ldc;
-  int* status;
   int num_sms;
-  int bn;          // 256, 128 or 64
-  int raster;      // tile-row group size of the tile order
-  // strided batch (batch 0 or 1: one problem): problem z's panels at
-  // panelA/B(2) + z*panel_stride bytes, maxima at amaxA/B + z*amax_stride
-  // words, result at C + z*c_stride elements
-  int64_t batch = 1;
-  int64_t panel_stride = 0, amax_stride = 0, c_stride = 0;
-  // split-K (batch 1, split_parts(k) == 1): splitk > 1 slices of k, their raw
-  // accumulators in `partial` (splitk x tiles x 128 x bn floats), finished by
-  // launch_splitk_reduce
+  int bn;
   int splitk = 1;
   float* partial = nullptr;
 };
@@ -138,7 +152,6 @@ struct SplitGemmArgs {
 // (1 when the tiles already fill half of the SMs, or k is short).
 int choose_splitk(int64_t tiles, int64_t k, int num_sms);
 // C := alpha 2^(e_i + f_j) sum_s partial_s + beta C, slices summed in order.
-cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s);
 cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s);
 
 // Failure-detection probe: a bounded mbarrier wait that nothing completes;

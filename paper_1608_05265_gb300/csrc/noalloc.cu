@@ -41,8 +41,6 @@ int trans_code_na(char t) {
   }
 }
 
-size_t round256(size_t x) { return (x + 255) / 256 * 256; }
-
 // Per-device set-up: the device address of the scratch array, the SM count
 // and whether the split kernels run here.  Called with `dev` current.
 int setup_device(int dev, void** scratch, int* num_sms, bool* split_ok) {
@@ -72,9 +70,7 @@ int setup_device(int dev, void** scratch, int* num_sms, bool* split_ok) {
 
 // Scratch bytes one call needs: the status slot plus gbgemm_split_workspace_bytes(m, n, k).
 size_t noalloc_scratch_bytes(int64_t m, int64_t n, int64_t k) {
-  const size_t parts = (size_t)gbg::split_parts(k);
-  return kStatusBytes + parts * (round256(gbg::panel_bytes(m, k)) + round256(gbg::panel_bytes(n, k))) +
-         round256((size_t)m * 4) + round256((size_t)n * 4);
+  return kStatusBytes + gbg::split_layout(m, n, k, 1, 1, 256).total;
 }
 
 }  // namespace
@@ -119,33 +115,20 @@ int gbgemm_sgemm_split_noalloc(void* cuda_stream, char transa, char transb, int6
   if (rc != GBGEMM_OK) return rc;
   if (!split_ok) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
 
-  // Carve the array: [status | panel A | panel B | row maxima A | row maxima B
-  // | (three-part split) panel A2 | panel B2].
-  // Panels are rewritten in full by the packing kernels and the row maxima
-  // are zeroed by launch_split_pack, so stale contents of earlier calls do
-  // not leak into this one.
+  // Carve the array: [status | the call's workspace: control words, band
+  // counters and row maxima (zeroed by launch_split_call before the kernel
+  // runs), then the panels, which the kernel's packers rewrite in full before
+  // any tile reads them], so stale contents of earlier calls do not leak
+  // into this one.
   unsigned char* base = static_cast<unsigned char*>(scratch);
-  const size_t pa = round256(gbg::panel_bytes(m, k)), pb = round256(gbg::panel_bytes(n, k));
-  const size_t xa = round256((size_t)m * 4);
   int* dstatus = status ? status : reinterpret_cast<int*>(base);
-  void* panelA = base + kStatusBytes;
-  void* panelB = base + kStatusBytes + pa;
-  uint32_t* amaxA = reinterpret_cast<uint32_t*>(base + kStatusBytes + pa + pb);
-  uint32_t* amaxB = reinterpret_cast<uint32_t*>(base + kStatusBytes + pa + pb + xa);
-  const size_t xb = round256((size_t)n * 4);
-  const bool three = gbg::split_parts(k) == 2;
-  void* panelA2 = three ? base + kStatusBytes + pa + pb + xa + xb : nullptr;
-  void* panelB2 = three ? base + kStatusBytes + pa + pb + xa + xb + pa : nullptr;
   if (!status && cudaMemsetAsync(dstatus, 0, sizeof(int), s) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  if (gbg::launch_split_pack(m, k, A, lda, ta == 1, amaxA, panelA, panelA2, s) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  if (gbg::launch_split_pack(n, k, B, ldb, tb == 0, amaxB, panelB, panelB2, s) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  gbg::SplitGemmArgs a;
-  a.panelA = panelA; a.panelB = panelB; a.amaxA = amaxA; a.amaxB = amaxB;
-  a.panelA2 = panelA2; a.panelB2 = panelB2;
-  a.m = m; a.n = n; a.k = k; a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
-  a.status = dstatus; a.num_sms = num_sms;
-  a.bn = 256; a.raster = 16;
-  return gbg::launch_split_gemm(a, s) == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
+  gbg::SplitCall c;
+  c.ta = ta; c.tb = tb; c.m = m; c.n = n; c.k = k; c.alpha = alpha; c.beta = beta;
+  c.A = A; c.lda = lda; c.B = B; c.ldb = ldb; c.C = C; c.ldc = ldc;
+  c.bn = 256; c.raster = 16; c.splitk = 1;
+  c.ws = base + kStatusBytes; c.status = dstatus; c.num_sms = num_sms;
+  return gbg::launch_split_call(c, s) == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
 }
 
 }  // extern "C"

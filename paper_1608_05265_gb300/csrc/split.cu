@@ -32,30 +32,6 @@
 namespace gbg {
 namespace {
 
-// blockIdx.z selects the problem of a strided batch: its operand at
-// X + z*xs, its row maxima at amax + z*as, its panels at panel(2) + z*ps.
-template <bool KCONTIG>
-__global__ void __launch_bounds__(256) pack_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
-                                                   uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
-                                                   uint8_t* __restrict__ panel2, int64_t rows_alloc, int64_t xs,
-                                                   int64_t as, int64_t ps) {
-  __shared__ uint32_t smax[128];
-  const int64_t z = blockIdx.z;
-  pack_block<KCONTIG>(rows, k, X + z * xs, ld, amax + z * as, panel + z * ps, panel2 ? panel2 + z * ps : nullptr,
-                      rows_alloc, blockIdx.x, blockIdx.y, smax);
-}
-
-__global__ void __launch_bounds__(256) rescale_kernel(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
-                                                      bool kcontig, const uint32_t* __restrict__ amax,
-                                                      uint8_t* __restrict__ panel, uint8_t* __restrict__ panel2,
-                                                      int64_t rows_alloc, int64_t nkc, int64_t xs, int64_t as,
-                                                      int64_t ps) {
-  __shared__ int se[128];
-  const int64_t z = blockIdx.z;
-  rescale_block(rows, k, X + z * xs, ld, kcontig, amax + z * as, panel + z * ps, panel2 ? panel2 + z * ps : nullptr,
-                rows_alloc, nkc, blockIdx.x, se);
-}
-
 // Split-K reduction: thread per C element (i, j), the slices' raw
 // accumulators summed in slice order (deterministic), then the epilogue of
 // split_gemm_kernel: x 2^(e_i + f_j), alpha, and beta C with one rounding of
@@ -118,76 +94,124 @@ int choose_splitk(int64_t tiles, int64_t k, int num_sms) {
   return s >= 2 ? (int)s : 1;
 }
 
-cudaError_t launch_split_pack(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
-                              uint32_t* amax_bits, void* panel, void* panel2, cudaStream_t s) {
-  return launch_split_pack_batched(rows, k, X, ld, kcontig, amax_bits, panel, panel2, 1, 0, 0, 0, s);
+SplitLayout split_layout(int64_t m, int64_t n, int64_t k, int64_t batch, int splitk, int bn) {
+  SplitLayout L{};
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const int64_t ra = (m + 127) / 128, rb = (n + 127) / 128;
+  L.bands = (size_t)(ra + rb) * (size_t)batch;
+  L.band_off = kSplitCtlBytes;
+  L.amax_off = L.band_off + up(L.bands * 4);
+  L.amax_stride = m + n;
+  L.head = L.amax_off + up((size_t)batch * (size_t)(m + n) * 4);
+  L.pa = up(panel_bytes(m, k));
+  L.pb = up(panel_bytes(n, k));
+  L.block = (size_t)split_parts(k) * (L.pa + L.pb);
+  L.panel_off = L.head;
+  L.partial_off = L.panel_off + L.block * (size_t)batch;
+  const size_t tiles = (size_t)((m + 127) / 128) * (size_t)((n + bn - 1) / bn);
+  L.total = L.partial_off + (splitk > 1 ? (size_t)splitk * tiles * 128 * (size_t)bn * 4 : 0);
+  return L;
 }
 
-cudaError_t launch_split_pack_batched(int64_t rows, int64_t k, const float* X, int64_t ld, bool kcontig,
-                                      uint32_t* amax_bits, void* panel, void* panel2, int64_t batch, int64_t xs,
-                                      int64_t as, int64_t ps, cudaStream_t s) {
-  if (rows <= 0 || k <= 0 || batch <= 0) return cudaSuccess;
-  if (batch > 65535) return cudaErrorInvalidConfiguration;
-  if (batch > 1 && as < rows) return cudaErrorInvalidValue;
-  // every problem's row maxima start at zero (they sit between its panels)
-  cudaError_t e = batch == 1 ? cudaMemsetAsync(amax_bits, 0, (size_t)rows * sizeof(uint32_t), s)
-                             : cudaMemset2DAsync(amax_bits, (size_t)as * sizeof(uint32_t), 0,
-                                                 (size_t)rows * sizeof(uint32_t), (size_t)batch, s);
-  if (e != cudaSuccess) return e;
-  const int64_t rbc = panel_row_blocks(rows);
-  const int64_t nkc = panel_k_chunks(k);
-  dim3 g((unsigned)rbc, (unsigned)nkc, (unsigned)batch);
-  if (g.y > 65535u) return cudaErrorInvalidConfiguration;
-  uint8_t* pn = static_cast<uint8_t*>(panel);
-  uint8_t* pn2 = split_parts(k) == 2 ? static_cast<uint8_t*>(panel2) : nullptr;
-  if (split_parts(k) == 2 && !pn2) return cudaErrorInvalidValue;
-  if (kcontig) pack_kernel<true><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128, xs, as, ps);
-  else pack_kernel<false><<<g, 256, 0, s>>>(rows, k, X, ld, amax_bits, pn, pn2, rbc * 128, xs, as, ps);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  rescale_kernel<<<dim3((unsigned)rbc, 1, (unsigned)batch), 256, 0, s>>>(rows, k, X, ld, kcontig, amax_bits, pn, pn2,
-                                                                         rbc * 128, nkc, xs, as, ps);
-  return cudaGetLastError();
-}
+namespace {
 
-cudaError_t launch_split_gemm(const SplitGemmArgs& a, cudaStream_t s) {
-  if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
-  if (a.bn != 64 && a.bn != 128 && a.bn != 256) return cudaErrorInvalidValue;
-  const int64_t tm = (a.m + 127) / 128, tn = (a.n + a.bn - 1) / a.bn;
-  const int64_t batch = a.batch > 0 ? a.batch : 1;
-  if (tm * tn * batch > (int64_t)0x7FFFFFFF || panel_k_chunks(a.k) > (int64_t)0x7FFFFFFF) return cudaErrorInvalidValue;
+// The scheduler of one call (or strided batch) over the workspace `ws`.
+// pack_only: no tiles, only the packing of op(A)'s rows (panel inspection).
+SingleSched make_single_sched(const SplitCall& c, const SplitLayout& L) {
+  uint8_t* ws = static_cast<uint8_t*>(c.ws);
   SingleSched S;
-  S.panelA = static_cast<const uint8_t*>(a.panelA);
-  S.panelB = static_cast<const uint8_t*>(a.panelB);
-  S.amaxA = a.amaxA; S.amaxB = a.amaxB;
-  S.m = a.m; S.n = a.n;
-  S.alpha = a.alpha; S.beta = a.beta;
-  S.C = a.C; S.ldc = a.ldc;
-  S.tiles_m = (int)tm; S.tiles_n = (int)tn;
-  S.nkc = (int)panel_k_chunks(a.k);
-  S.raster = a.raster > 0 ? a.raster : 16;
-  S.bn = a.bn;
-  S.rbA = panel_row_blocks(a.m);
-  S.rbB = panel_row_blocks(a.n);
-  S.parts = split_parts(a.k);
-  if (S.parts == 2 && (!a.panelA2 || !a.panelB2)) return cudaErrorInvalidValue;
-  S.a_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelA2) - S.panelA) : 0;
-  S.b_part = S.parts == 2 ? (size_t)(static_cast<const uint8_t*>(a.panelB2) - S.panelB) : 0;
-  S.batch = (int)batch;
-  S.ps = a.panel_stride; S.as = a.amax_stride; S.cs = a.c_stride;
-  S.splitk = a.splitk > 1 ? a.splitk : 1;
-  if (S.splitk > 1 && (batch != 1 || S.parts != 1 || !a.partial)) return cudaErrorInvalidValue;
+  S.ctl = reinterpret_cast<WorkCtl*>(ws);
+  S.band_cnt = reinterpret_cast<int*>(ws + L.band_off);
+  S.A = c.A; S.B = c.B; S.lda = c.lda; S.ldb = c.ldb; S.sa = c.sa; S.sb = c.sb;
+  S.ta = c.ta; S.tb = c.tb;
+  S.panelA = ws + L.panel_off;
+  S.panelB = ws + L.panel_off + L.pa;
+  S.amaxA = reinterpret_cast<uint32_t*>(ws + L.amax_off);
+  S.amaxB = S.amaxA + c.m;
+  S.m = c.m; S.n = c.n; S.k = c.k;
+  S.alpha = c.alpha; S.beta = c.beta;
+  S.C = c.C; S.ldc = c.ldc;
+  S.tiles_m = (int)((c.m + 127) / 128);
+  S.tiles_n = (int)((c.n + c.bn - 1) / c.bn);
+  S.nkc = (int)panel_k_chunks(c.k);
+  S.raster = c.raster > 0 ? c.raster : 16;
+  S.bn = c.bn;
+  S.parts = split_parts(c.k);
+  S.rbA = panel_row_blocks(c.m);
+  S.rbB = panel_row_blocks(c.n);
+  S.ra = (int)((c.m + 127) / 128);
+  S.rb = (int)((c.n + 127) / 128);
+  S.ngroups = (S.nkc + kPackChunks - 1) / kPackChunks;
+  // per problem [A | B | A2 | B2]: A2 - A = B2 - B = pa + pb
+  S.a_part = S.parts == 2 ? (int64_t)(L.pa + L.pb) : 0;
+  S.b_part = S.a_part;
+  S.batch = (int)c.batch;
+  S.ps = (int64_t)L.block;
+  S.as = L.amax_stride;
+  S.cs = c.sc;
+  S.splitk = c.splitk > 1 ? c.splitk : 1;
   S.slice_chunks = (S.nkc + S.splitk - 1) / S.splitk;
+  S.partial = c.splitk > 1 ? reinterpret_cast<float*>(ws + L.partial_off) : nullptr;
+  return S;
+}
+
+}  // namespace
+
+cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
+  if (c.m <= 0 || c.k <= 0 || c.batch <= 0) return cudaSuccess;
+  if (c.n < 0 || (c.n == 0 && !c.pack_only)) return cudaSuccess;
+  if (c.bn != 64 && c.bn != 128 && c.bn != 256) return cudaErrorInvalidValue;
+  if (c.batch > 65535 || !c.ws) return cudaErrorInvalidValue;
+  const int splitk = c.splitk > 1 ? c.splitk : 1;
+  if (splitk > 1 && (c.batch != 1 || split_parts(c.k) != 1)) return cudaErrorInvalidValue;
+  const int64_t tm = (c.m + 127) / 128, tn = (c.n + c.bn - 1) / c.bn;
+  const int64_t nkc = panel_k_chunks(c.k);
+  const int64_t tasks = c.batch * (tm + (c.n + 127) / 128) * ((nkc + kPackChunks - 1) / kPackChunks);
+  if (tm * tn * c.batch * splitk > (int64_t)0x7FFFFFFF || tasks > (int64_t)0x7FFFFFFF) return cudaErrorInvalidValue;
+  const SplitLayout L = split_layout(c.m, c.n, c.k, c.batch, splitk, c.bn);
+  SingleSched S = make_single_sched(c, L);
+  if (c.pack_only) {
+    S.tiles_n = 0;  // no tiles: the packers only
+    if (c.panel_out) {
+      S.panelA = static_cast<const uint8_t*>(c.panel_out);
+      S.a_part = c.panel2_out ? static_cast<const uint8_t*>(c.panel2_out) - S.panelA : 0;
+    }
+    if (c.amax_out) S.amaxA = c.amax_out;
+  }
   // no empty slice (an empty slice would store a stale accumulator)
   if ((int64_t)(S.splitk - 1) * S.slice_chunks >= S.nkc) return cudaErrorInvalidValue;
-  S.partial = a.partial;
-  cudaError_t e = ensure_gemm_smem_attr<SingleSched>();
+  cudaError_t e = cudaMemsetAsync(c.ws, 0, L.head, s);
   if (e != cudaSuccess) return e;
-  const int64_t tiles = tm * tn * batch * S.splitk;
-  const int64_t sms = a.num_sms > 0 ? a.num_sms : 148;
-  const int grid = (int)(tiles < sms ? tiles : sms);
-  split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, a.status, kTimeoutNs);
-  return cudaGetLastError();
+  if (c.pack_only && c.amax_out) {
+    e = cudaMemsetAsync(c.amax_out, 0, (size_t)c.m * 4, s);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t items = tm * tn * c.batch * splitk;
+  const int64_t sms = c.num_sms > 0 ? c.num_sms : 148;
+  if (c.fused) {
+    e = ensure_gemm_smem_attr<SingleSched>();
+    if (e != cudaSuccess) return e;
+    const int64_t want = items > tasks ? items : tasks;
+    const int grid = (int)(want < sms ? (want > 0 ? want : 1) : sms);
+    split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, c.status, kTimeoutNs);
+  } else {
+    // packing tasks first, each its own CTA, then the GEMM without packer warps
+    if (tasks > 0) pack_tasks_kernel<SingleSched><<<(unsigned)tasks, 256, 0, s>>>(S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || items == 0) return e;
+    e = ensure_gemm_smem_attr<SingleSched, kStages, kMaxBN, 0>();
+    if (e != cudaSuccess) return e;
+    const int grid = (int)(items < sms ? items : sms);
+    split_gemm_kernel<SingleSched, kStages, kMaxBN, 0>
+        <<<grid, kGemmThreads, gemm_smem_bytes<kStages, kMaxBN, 0>(), s>>>(S, c.status, kTimeoutNs);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess || splitk == 1 || c.pack_only) return e;
+  SplitGemmArgs a;
+  a.m = c.m; a.n = c.n; a.k = c.k; a.alpha = c.alpha; a.beta = c.beta; a.C = c.C; a.ldc = c.ldc;
+  a.amaxA = S.amaxA; a.amaxB = S.amaxB; a.num_sms = c.num_sms; a.bn = c.bn; a.splitk = splitk;
+  a.partial = S.partial;
+  return launch_splitk_reduce(a, s);
 }
 
 cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s) {

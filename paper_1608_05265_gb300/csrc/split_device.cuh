@@ -1,7 +1,8 @@
 // Device helpers of the split-BF16 path, shared by the single-problem
-// kernels (split.cu) and the grouped kernels (grouped.cu): scaling and
-// hi/lo splitting, panel-chunk stores, and the PTX wrappers for mbarriers,
-// bulk asynchronous copies and tcgen05 (MMA, commit, TMEM loads).
+// launches (split.cu) and the grouped plans (grouped.cu): scaling and hi/lo
+// splitting, panel-chunk stores, the re-pack of badly scaled rows, and the
+// PTX wrappers for mbarriers, asynchronous copies, fences and tcgen05 (MMA,
+// commit, TMEM loads).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -46,7 +47,7 @@ __device__ __forceinline__ void split_bf16(float xs, uint32_t& h, uint32_t& l) {
 }
 
 // ---------------------------------------------------------------------------
-// K1: split and pack.  One pass writes the hi/lo panel of the UNSCALED
+// Split and pack.  One pass writes the hi/lo panel of the UNSCALED
 // operand and the max |x| of every K-vector (bit patterns; NaN > Inf >
 // finite as unsigned).  Well-scaled vectors (the large majority) are then
 // final.  A second, usually empty pass re-packs the badly scaled ones with
@@ -59,16 +60,44 @@ __device__ __forceinline__ void split_bf16(float xs, uint32_t& h, uint32_t& l) {
 // chunk positions XOR (r mod 8).
 // ---------------------------------------------------------------------------
 
+// Two floats rounded to BF16 (RN-even) in one instruction: `a` into the
+// low half, `b` into the high half.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float a, float b) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t d) { return __uint_as_float(d << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t d) { return __uint_as_float(d & 0xFFFF0000u); }
+
+// True when none of the 8 values is Inf or NaN (the packed splits below
+// apply; otherwise the element-wise ones, which give lo = 0 for them).
+__device__ __forceinline__ bool all_finite8(const float (&x)[8]) {
+  uint32_t e = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) e = max(e, __float_as_uint(x[q]) & 0x7F800000u);
+  return e != 0x7F800000u;
+}
+
 // Split 8 values (already scaled) and store the hi and lo chunks of row rr.
 __device__ __forceinline__ void store_split8(uint8_t* blk, int rr, int cc, const float (&x)[8]) {
   uint32_t hw[4], lw[4];
+  if (all_finite8(x)) {
+    // x - hi is exact in FP32, so the packed form equals the element-wise one
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint32_t h0, l0, h1, l1;
-    split_bf16(x[2 * q], h0, l0);
-    split_bf16(x[2 * q + 1], h1, l1);
-    hw[q] = h0 | (h1 << 16);
-    lw[q] = l0 | (l1 << 16);
+    for (int q = 0; q < 4; ++q) {
+      hw[q] = cvt_bf16x2(x[2 * q], x[2 * q + 1]);
+      lw[q] = cvt_bf16x2(x[2 * q] - bf16_lo(hw[q]), x[2 * q + 1] - bf16_hi(hw[q]));
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t h0, l0, h1, l1;
+      split_bf16(x[2 * q], h0, l0);
+      split_bf16(x[2 * q + 1], h1, l1);
+      hw[q] = h0 | (h1 << 16);
+      lw[q] = l0 | (l1 << 16);
+    }
   }
   const int sw = rr & 7;
   *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -80,23 +109,33 @@ __device__ __forceinline__ void store_split8(uint8_t* blk, int rr, int cc, const
 __device__ __forceinline__ void store_split8_3(uint8_t* blk, uint8_t* blk2, int half, int rr, int cc,
                                                const float (&x)[8]) {
   uint32_t hw[4], mw[4], lw[4];
+  if (all_finite8(x)) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint32_t hb[2], mb[2], lb[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float v = x[2 * q + u];
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      hb[u] = (uint32_t)__bfloat16_as_ushort(h);
-      if (!isfinite(v)) { mb[u] = 0u; lb[u] = 0u; continue; }
-      const float r1 = v - __bfloat162float(h);
-      const __nv_bfloat16 mdl = __float2bfloat16_rn(r1);
-      mb[u] = (uint32_t)__bfloat16_as_ushort(mdl);
-      lb[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(mdl)));
+    for (int q = 0; q < 4; ++q) {
+      hw[q] = cvt_bf16x2(x[2 * q], x[2 * q + 1]);
+      const float r0 = x[2 * q] - bf16_lo(hw[q]), r1 = x[2 * q + 1] - bf16_hi(hw[q]);
+      mw[q] = cvt_bf16x2(r0, r1);
+      lw[q] = cvt_bf16x2(r0 - bf16_lo(mw[q]), r1 - bf16_hi(mw[q]));
     }
-    hw[q] = hb[0] | (hb[1] << 16);
-    mw[q] = mb[0] | (mb[1] << 16);
-    lw[q] = lb[0] | (lb[1] << 16);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t hb[2], mb[2], lb[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float v = x[2 * q + u];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hb[u] = (uint32_t)__bfloat16_as_ushort(h);
+        if (!isfinite(v)) { mb[u] = 0u; lb[u] = 0u; continue; }
+        const float r1 = v - __bfloat162float(h);
+        const __nv_bfloat16 mdl = __float2bfloat16_rn(r1);
+        mb[u] = (uint32_t)__bfloat16_as_ushort(mdl);
+        lb[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(mdl)));
+      }
+      hw[q] = hb[0] | (hb[1] << 16);
+      mw[q] = mb[0] | (mb[1] << 16);
+      lw[q] = lb[0] | (lb[1] << 16);
+    }
   }
   const int sw = rr & 7;
   *reinterpret_cast<uint4*>(blk + rr * 128 + ((cc ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -104,42 +143,6 @@ __device__ __forceinline__ void store_split8_3(uint8_t* blk, uint8_t* blk2, int 
   // lo3 of an even k chunk in logical chunks 0-3 of the compact block, of an
   // odd one in 4-7
   *reinterpret_cast<uint4*>(blk2 + rr * 128 + (((cc + 4 * half) ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-}
-
-// Item mapping inside a 256-thread CTA, two items per thread.
-// KCONTIG (element (r,p) at X[r*ld + p]): four lanes per row, eight rows per
-//   warp, so a warp reads eight 128-byte row segments.
-// !KCONTIG (element (r,p) at X[r + p*ld]): 32 consecutive rows per warp and
-//   one chunk per warp, so every load instruction reads 128 contiguous bytes.
-template <bool KCONTIG>
-__device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
-  if (KCONTIG) {
-    const int idx = tid + 256 * it;
-    rr = idx >> 2;
-    cc = idx & 3;
-  } else {
-    const int w = tid >> 5;
-    cc = w & 3;
-    rr = ((w >> 2) + 2 * it) * 32 + (tid & 31);
-  }
-}
-
-template <bool KCONTIG>
-__device__ __forceinline__ void load8(const float* __restrict__ X, int64_t ld, int64_t r, int64_t p, int64_t rows,
-                                      int64_t k, bool vec, float (&x)[8]) {
-  if (KCONTIG) {
-    if (r < rows && vec && p + 8 <= k) {
-      const float4 a = *reinterpret_cast<const float4*>(X + r * ld + p);
-      const float4 b = *reinterpret_cast<const float4*>(X + r * ld + p + 4);
-      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = (r < rows && p + q < k) ? X[r * ld + p + q] : 0.f;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (r < rows && p + q < k) ? X[r + (p + q) * ld] : 0.f;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -217,6 +220,58 @@ __device__ __noinline__ bool mbar_wait_hint(uint32_t bar, uint32_t parity, volat
   }
 }
 
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Orders this thread's generic-proxy accesses of global memory against
+// async-proxy ones (bulk copies) on either side of it.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Wait until *p >= target (acquire).  Gives up (returns false) once
+// `timeout_ns` has passed or another role raised the abort flag.
+__device__ __noinline__ bool wait_counter(const int* p, int target, volatile int* abort_flag, uint64_t timeout_ns) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    __nanosleep(100);
+    if (ld_acquire(p) >= target) return true;
+    if ((it & 7u) == 0u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > timeout_ns) return false;
+    }
+  }
+}
+
+// Ask L2 for the 128-byte line holding `p`.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Asynchronous copies into shared memory that hold no registers while in
+// flight: 16 bytes (16-byte aligned source) or 4 bytes; bytes past
+// `src_bytes` are filled with zeros (src_bytes 0: nothing is read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most `pending` of this thread's committed groups are still in flight.
+__device__ __forceinline__ void cp_async_wait(int pending) {
+  switch (pending) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
+}
+
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
@@ -286,90 +341,56 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = r / gm;
 }
 
-// Pack rows 128*rb .. +127 of k chunk kc of one operand (256 threads).  The
-// panel holds `rows_alloc` rows (a multiple of 8) per k chunk: row r of
+// Panels hold `rows_alloc` rows (a multiple of 8) per k chunk: row r of
 // chunk kc is the 128 bytes at (kc*rows_alloc + r)*128.  Rows from `rows`
 // up to rows_alloc are written as zeros, rows past rows_alloc not at all.
-// smax: 128 words of shared memory.
-// With panel2 != NULL the three-part split is written ([hi | mid] into
+// With a second panel the three-part split is written ([hi | mid] into the
 // panel, lo3 into the compact panel2: block kc / 2, half kc % 2).
-template <bool KCONTIG, int G = 1>
-__device__ __forceinline__ void pack_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
-                                           uint32_t* __restrict__ amax, uint8_t* __restrict__ panel,
-                                           uint8_t* __restrict__ panel2, int64_t rows_alloc, int64_t rb, int64_t kc0,
-                                           uint32_t* smax, int64_t nkc = 1 << 30) {
-  // G consecutive k chunks kc0 .. kc0 + G - 1 (those below nkc) of one 128-row block
-  const int64_t r0 = rb * 128;
-  const int tid = threadIdx.x;
-  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-  if (tid < 128) smax[tid] = 0u;
-  float x[G][2][8];
-#pragma unroll
-  for (int c = 0; c < G; ++c) {  // all loads first: 16 G (or 4 G vector) loads in flight per thread
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      int rr, cc;
-      item_of<KCONTIG>(tid, it, rr, cc);
-      if (kc0 + c < nkc) load8<KCONTIG>(X, ld, r0 + rr, (kc0 + c) * 32 + cc * 8, rows, k, vec, x[c][it]);
-    }
+
+// Named barrier `id` of `n` threads: one packing team inside the GEMM CTA.
+struct TeamBar {
+  int id, n;
+  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+  __device__ __forceinline__ bool any(bool p) const {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\t"
+        "setp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.or.pred b, %2, %3, a;\n\t"
+        "selp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0u;
   }
-  __syncthreads();
-  uint32_t mxr[2] = {0u, 0u};
-#pragma unroll
-  for (int c = 0; c < G; ++c) {
-    if (kc0 + c >= nkc) break;
-    const size_t boff = ((size_t)(kc0 + c) * rows_alloc + r0) * 128;
-    const size_t boff2 = ((size_t)((kc0 + c) >> 1) * rows_alloc + r0) * 128;  // compact [lo3 | lo3] block
-    uint8_t* blk = panel + boff;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      int rr, cc;
-      item_of<KCONTIG>(tid, it, rr, cc);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) mxr[it] = max(mxr[it], __float_as_uint(x[c][it][q]) & 0x7FFFFFFFu);
-      if (r0 + rr < rows_alloc) {
-        if (panel2) store_split8_3(blk, panel2 + boff2, (int)((kc0 + c) & 1), rr, cc, x[c][it]);
-        else store_split8(blk, rr, cc, x[c][it]);
-      }
-    }
-  }
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    int rr, cc;
-    item_of<KCONTIG>(tid, it, rr, cc);
-    uint32_t mx = mxr[it];
-    if (KCONTIG) {
-      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
-      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
-      if (cc == 0 && mx != 0u) atomicMax(&smax[rr], mx);
-    } else if (mx != 0u) {
-      atomicMax(&smax[rr], mx);
-    }
-  }
-  __syncthreads();
-  if (tid < 128 && r0 + tid < rows && smax[tid] != 0u) atomicMax(&amax[r0 + tid], smax[tid]);
-}
+};
 
 // Re-pack the badly scaled K-vectors of one 128-row block over all k chunks
-// with x' = x * 2^-e.  A block without such rows returns at once.
+// with x' = x * 2^-e, by a team of TS threads.  A block without such rows
+// returns at once.  The maxima are read through L2 (they were built by
+// atomics of other CTAs).  se: 128 ints of shared memory.
+template <int TS>
 __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                               bool kcontig, const uint32_t* __restrict__ amax,
                                               uint8_t* __restrict__ panel, uint8_t* __restrict__ panel2,
-                                              int64_t rows_alloc, int64_t nkc, int64_t rb, int* se) {
+                                              int64_t rows_alloc, int64_t nkc, int64_t rb, int* se, int tid,
+                                              TeamBar bar) {
   const int64_t r0 = rb * 128;
-  const int tid = threadIdx.x;
-  int e = 0;
-  if (tid < 128 && r0 + tid < rows) e = scale_exp_from_bits(amax[r0 + tid]);
-  if (tid < 128) se[tid] = e;
-  if (!__syncthreads_or(e != 0)) return;
+  bool any = false;
+  for (int r = tid; r < 128; r += TS) {
+    const int e = (r0 + r < rows) ? scale_exp_from_bits(__ldcg(&amax[r0 + r])) : 0;
+    se[r] = e;
+    any = any || e != 0;
+  }
+  if (!bar.any(any)) return;
   for (int64_t kc = 0; kc < nkc; ++kc) {
     const size_t boff = ((size_t)kc * rows_alloc + r0) * 128;
     const size_t boff2 = ((size_t)(kc >> 1) * rows_alloc + r0) * 128;
     uint8_t* blk = panel + boff;
-    for (int it = 0; it < 2; ++it) {
-      const int idx = tid + 256 * it, rr = idx >> 2, cc = idx & 3;
+    for (int idx = tid; idx < 512; idx += TS) {
+      const int rr = idx >> 2, cc = idx & 3;
       const int er = se[rr];
-      if (er == 0) continue;
+      if (er == 0 || r0 + rr >= rows_alloc) continue;
       const int64_t r = r0 + rr, p = kc * 32 + cc * 8;
       float x[8];
 #pragma unroll

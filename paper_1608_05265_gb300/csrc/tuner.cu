@@ -109,8 +109,8 @@ int Tuner::measure(const gbgemm_problem& q0, int reps, TuneResult* out) {
   const size_t a_bytes = (size_t)q0.lda * std::max<int64_t>(acols, 1) * 4 + 16;
   const size_t b_bytes = (size_t)q0.ldb * std::max<int64_t>(bcols, 1) * 4 + 16;
   const size_t c_bytes = (size_t)q0.ldc * std::max<int64_t>(q0.n, 1) * 4 + 16;
-  const size_t pa = (gbg::panel_bytes(q0.m, q0.k) + 255) / 256 * 256, pb = (gbg::panel_bytes(q0.n, q0.k) + 255) / 256 * 256;
-  const size_t ws = (size_t)split_parts(q0.k) * (pa + pb) + (size_t)(q0.m + q0.n) * 4 + 512;
+  size_t ws = 0;  // the largest split workspace of the three tile widths
+  for (int bn : {64, 128, 256}) ws = std::max(ws, split_layout(q0.m, q0.n, q0.k, 1, 1, bn).total);
   auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
   int rc = ensure(r256(a_bytes) + r256(b_bytes) + r256(c_bytes) + ws);
   if (rc != GBGEMM_OK) return rc;
@@ -132,26 +132,13 @@ int Tuner::measure(const gbgemm_problem& q0, int reps, TuneResult* out) {
     if (!config_legal(q, c)) continue;
     auto run = [&]() -> cudaError_t {
       if (c < GBGEMM_CFG_SPLIT_BN64) return launch_simt(p, c, stream_);
-      // scratch: [panel A | panel B | maxima | (three parts) panel A2 | panel B2]
-      uint8_t* p2 = wsp + pa + pb + (((size_t)(q.m + q.n) * 4 + 511) / 256 * 256);
-      const bool three = split_parts(q.k) == 2;
-      cudaError_t e = launch_split_pack(q.m, q.k, A, q.lda, ta == 1, reinterpret_cast<uint32_t*>(wsp + pa + pb),
-                                        wsp, three ? p2 : nullptr, stream_);
-      if (e == cudaSuccess)
-        e = launch_split_pack(q.n, q.k, B, q.ldb, tb == 0, reinterpret_cast<uint32_t*>(wsp + pa + pb) + q.m, wsp + pa,
-                              three ? p2 + pa : nullptr, stream_);
-      if (e != cudaSuccess) return e;
-      SplitGemmArgs a;
-      a.panelA = wsp; a.panelB = wsp + pa;
-      a.panelA2 = three ? p2 : nullptr;
-      a.panelB2 = three ? p2 + pa : nullptr;
-      a.amaxA = reinterpret_cast<const uint32_t*>(wsp + pa + pb);
-      a.amaxB = reinterpret_cast<const uint32_t*>(wsp + pa + pb) + q.m;
-      a.m = q.m; a.n = q.n; a.k = q.k; a.alpha = 1.0f; a.beta = 0.0f; a.C = C; a.ldc = q.ldc;
-      a.status = status_; a.num_sms = num_sms_;
-      a.bn = c == GBGEMM_CFG_SPLIT_BN64 ? 64 : c == GBGEMM_CFG_SPLIT_BN128 ? 128 : 256;
-      a.raster = 16;
-      return launch_split_gemm(a, stream_);
+      SplitCall sc;
+      sc.ta = ta; sc.tb = tb; sc.m = q.m; sc.n = q.n; sc.k = q.k; sc.alpha = 1.0f; sc.beta = 0.0f;
+      sc.A = A; sc.lda = q.lda; sc.B = B; sc.ldb = q.ldb; sc.C = C; sc.ldc = q.ldc;
+      sc.bn = c == GBGEMM_CFG_SPLIT_BN64 ? 64 : c == GBGEMM_CFG_SPLIT_BN128 ? 128 : 256;
+      sc.raster = 16;
+      sc.ws = wsp; sc.status = status_; sc.num_sms = num_sms_;
+      return launch_split_call(sc, stream_);
     };
     if (run() != cudaSuccess) return GBGEMM_ERR_CUDA;  // warm-up
     std::vector<float> t;

@@ -119,7 +119,7 @@ def default_choice(shapes) -> np.ndarray:
     """The library's fixed heuristic (GBGEMM_CONFIG_DEFAULT) for each shape."""
     out = []
     for (ta, tb, m, n, k, *_rest) in shapes:
-        if k >= 128:
+        if k >= 16:
             out.append(gbgemm.CFG_SPLIT_BN64 if n <= 64 else gbgemm.CFG_SPLIT_BN128)
         else:
             out.append(gbgemm.CFG_SIMT_128x128)

@@ -11,6 +11,9 @@ beyond a one-line summary.  Names:
   split8192   sgemm 8192^3 NN, ld 8200, split path (the headline shape)
   grouped     the 4096-problem uneven batch (m, n, k log-uniform in
               [16, 1024], seed 3), one plan with the default configurations
+  linpack8192 / linpack16384
+              the Linpack-shaped update C(m x m) -= A(m x 128) B(128 x m),
+              normal entries, split path
   lu4608      sgetrf + sgetrs, N 4608 (the paper's HPL size), default block
 """
 
@@ -55,6 +58,19 @@ def _grouped(h, reps):
     plan.close()
 
 
+def _linpack(h, reps, m, nb=128):
+    import torch
+    from paper_1608_05265_gb300 import gbgemm
+    g = torch.Generator(device="cuda").manual_seed(20 + nb)
+    A = torch.randn(m * nb, device="cuda", generator=g)
+    B = torch.randn(nb * m, device="cuda", generator=g)
+    C = torch.randn(m * m, device="cuda", generator=g)
+    h.set_path(gbgemm.PATH_AUTO)
+    for _ in range(reps):
+        h.sgemm("N", "N", m, m, nb, -1.0, A, m, B, nb, 1.0, C, m)
+    torch.cuda.synchronize()
+
+
 def _lu(h, reps):
     import torch
     n = 4608
@@ -74,7 +90,8 @@ def _lu(h, reps):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=["split4096", "simt4096", "split8192", "grouped", "lu4608"])
+    ap.add_argument("name", choices=["split4096", "simt4096", "split8192", "grouped", "lu4608", "linpack8192",
+                                     "linpack16384"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
     import torch
@@ -86,6 +103,8 @@ def main(argv=None) -> int:
         _split_or_simt(h, args.name[:-4], args.reps, int(args.name[-4:]))
     elif args.name == "grouped":
         _grouped(h, args.reps)
+    elif args.name.startswith("linpack"):
+        _linpack(h, args.reps, int(args.name[len("linpack"):]))
     else:
         _lu(h, args.reps)
     status = h.get_device_status()

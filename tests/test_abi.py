@@ -150,7 +150,10 @@ def test_panel_and_workspace_sizes(L):
     assert gbgemm.panel_bytes(8192, 8192) == 64 * 256 * 16384
     assert gbgemm.panel_bytes(0, 5) == 0
     ws = gbgemm.split_workspace_bytes(8192, 8192, 8192)
-    assert ws == 2 * 64 * 256 * 16384 + 2 * 8192 * 4
+    # control words (256 B), 64 + 64 band counters (512 B), row maxima, panels
+    assert ws == 256 + 512 + 2 * 8192 * 4 + 2 * 64 * 256 * 16384
+    # three parts below k = 512: a compact lo3 panel per operand as well
+    assert gbgemm.split_workspace_bytes(300, 200, 100) == 256 + 256 + 2048 + 2 * (4 + 2) * 4 * 16384
 
 
 def test_no_cpu_fallback_without_gpu(L):

@@ -78,7 +78,7 @@ def run_plan(h, batch, **kw):
 
 
 def test_grouped_default_configs(h):
-    specs = random_specs(31, 160, 16, 600, alphas=(1.0, -1.5, 0.5), betas=(0.0, 1.0, -0.25))
+    specs = random_specs(31, 160, 4, 600, alphas=(1.0, -1.5, 0.5), betas=(0.0, 1.0, -0.25))
     b = Batch(specs, 31)
     plan = run_plan(h, b)
     cfg = plan.configs()
@@ -93,7 +93,7 @@ def test_grouped_every_config(h):
     b = Batch(specs, 32)
     configs = []
     for g, (ta, tb, m, n, k, alpha, beta) in enumerate(specs):
-        legal = [0, 1, 2] + ([3, 4, 5] if k >= 128 else [])
+        legal = [0, 1, 2] + ([3, 4, 5] if k >= 16 else [])
         configs.append(legal[g % len(legal)])
     plan = run_plan(h, b, configs=configs)
     assert plan.configs() == configs
@@ -154,11 +154,36 @@ def test_grouped_bad_plans(h):
                               p.C, p.ldc)
     rc, bad = gbgemm.create_plan_status(h, probs)
     assert rc == gbgemm.ERR_BAD_PLAN and bad == 2
-    # a split configuration for a problem with k < 128 is illegal
-    small = [("N", "N", 40, 40, 64, 1.0, 0.0)]
+    # a split configuration for a problem with k < 16 is illegal
+    small = [("N", "N", 40, 40, 12, 1.0, 0.0)]
     b2 = Batch(small, 36)
     rc, bad = gbgemm.create_plan_status(h, b2.probs, configs=[gbgemm.CFG_SPLIT_BN128])
     assert rc == gbgemm.ERR_BAD_PLAN and bad == 0
+
+
+@pytest.mark.parametrize("ring", [0, 1 << 20])
+def test_grouped_fused_packing_ring(h, ring):
+    """Packing inside the GEMM kernel with its panel ring: the default ring,
+    and a 1 MiB ring that forces many wraps (problems packed only once the
+    problems whose ring bytes they reuse have been read)."""
+    import torch
+    from paper_1608_05265_gb300 import gbgemm
+    specs = random_specs(37, 300, 16, 700, alphas=(1.0, -1.5), betas=(0.0, 0.5))
+    b = Batch(specs, 37)
+    h.set_packing(gbgemm.PACKING_FUSED)
+    h.set_grouped_ring_bytes(ring)
+    try:
+        plan = run_plan(h, b)
+        b.check(nthreads=4)
+        b.reset_c()
+        plan.run(torch.cuda.current_stream())  # a replay reuses the ring from the start
+        torch.cuda.synchronize()
+        assert h.get_device_status() == 0
+        b.check(nthreads=4)
+        plan.close()
+    finally:
+        h.set_packing(gbgemm.PACKING_AUTO)
+        h.set_grouped_ring_bytes(0)
 
 
 def test_grouped_uneven_batch_4096(h):
@@ -170,7 +195,7 @@ def test_grouped_uneven_batch_4096(h):
     b = Batch(specs, 3)
     plan = run_plan(h, b)
     st = plan.stats()
-    assert st["n_split"] > 1000 and st["n_simt"] > 1000
+    assert st["n_split"] == 4096 and st["n_simt"] == 0  # every k >= 16: the split path
     b.check()
     plan.close()
 

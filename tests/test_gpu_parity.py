@@ -68,6 +68,22 @@ def test_split_grid_guaranteed_k(h):
         check_full(h, SPLIT, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, nthreads=4)
 
 
+def test_split_grid_short_k(h):
+    # 16 <= k < 128: the three-part split (six products) drops mid*lo3 + lo3*mid
+    # + lo3*lo3 (at most about 2^-23 |a||b| per term) and its FP32 accumulation
+    # rounds at most once per 16-deep MMA (6 ceil(k / 16) roundings of at most
+    # sum |a||b| 2^-24 each): together below the bound 2 k 2^-24 sum |a||b| from
+    # k = 16 on.  (At k = 1 the dropped terms alone can reach the bound.)
+    case = 0
+    for m, n, k in itertools.product([1, 17, 129, 300], [1, 64, 200, 257], [16, 17, 31, 33, 64, 100, 127]):
+        ta, tb = TRANS[case % 4]
+        alpha, beta = AB[case % 5]
+        pad = [0, 1, 8][case % 3]
+        case += 1
+        A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 400 + case, ta, tb, m, n, k, pad=pad)
+        check_full(h, SPLIT, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, nthreads=4)
+
+
 @pytest.mark.parametrize("path", [SIMT, SPLIT])
 @pytest.mark.parametrize("ta,tb", TRANS)
 @pytest.mark.parametrize("m,n,k,pad", [(1000, 777, 555, 8), (513, 1030, 1024, 0), (129, 2000, 300, 3)])
@@ -239,11 +255,16 @@ def unpack_compact_lo3(panel2: np.ndarray, rows: int, k: int):
     return both.transpose(1, 2, 0, 3).reshape(RB * 128, KC * 32)
 
 
+@pytest.mark.parametrize("packing", [1, 2], ids=["separate", "fused"])
 @pytest.mark.parametrize("which,trans", [("A", "N"), ("A", "T"), ("B", "N"), ("B", "T")])
 @pytest.mark.parametrize("rows,k", [(1, 1), (130, 37), (300, 300), (257, 1000), (200, 600), (70, 160), (90, 480)])
-def test_split_pack_bit_exact(h, which, trans, rows, k):
+def test_split_pack_bit_exact(h, which, trans, rows, k, packing):
+    """The panels and row maxima of both packers (the separate packing launch
+    and the GEMM kernel's packer warps) equal the oracle's split bit for bit,
+    rows scaled by 2^-60 .. 2^60 so that the re-pack of badly scaled rows runs."""
     import torch
     from paper_1608_05265_gb300 import gbgemm
+    h.set_packing(packing)
     kcontig = (which == "A") == (trans == "T")
     sr, sc = (k, rows) if kcontig else (rows, k)   # stored shape of X
     ld = sr + 3
@@ -270,6 +291,22 @@ def test_split_pack_bit_exact(h, which, trans, rows, k):
     vec = L.T if kcontig else L
     want = np.abs(vec).max(axis=1).astype(np.float32).view(np.uint32)
     assert np.array_equal(am, want)
+    h.set_packing(0)
+
+
+@pytest.mark.parametrize("packing", [1, 2], ids=["separate", "fused"])
+@pytest.mark.parametrize("ta,tb", TRANS)
+@pytest.mark.parametrize("m,n,k,pad", [(1000, 777, 555, 3), (129, 2000, 300, 1), (300, 260, 64, 0), (257, 513, 129, 5)])
+def test_both_packings_against_oracle(h, packing, ta, tb, m, n, k, pad):
+    """Both places the split path packs its operands give results within the
+    bound, two-part and three-part splits, odd leading dimensions (unaligned
+    rows and columns)."""
+    h.set_packing(packing)
+    A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 17, ta, tb, m, n, k, pad=pad)
+    try:
+        check_full(h, SPLIT, ta, tb, m, n, k, 1.5, A, lda, B, ldb, -0.25, C, ldc, nthreads=4)
+    finally:
+        h.set_packing(0)
 
 
 @pytest.mark.parametrize("path", [SIMT, SPLIT])
@@ -288,3 +325,16 @@ def test_auto_path_choice(h):
         A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 16, "N", "N", m, n, k)
         check_full(h, gbgemm.PATH_AUTO, "N", "N", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc)
         assert h.last_path() == want
+
+
+def test_packings_give_identical_bits(h):
+    """The two packers write the same panels and the GEMM does the same
+    arithmetic, so the results agree bit for bit (single call and batch)."""
+    from paper_1608_05265_gb300 import gbgemm
+    outs = []
+    for packing in (gbgemm.PACKING_SEPARATE, gbgemm.PACKING_FUSED):
+        h.set_packing(packing)
+        A, lda, B, ldb, C, ldc = synth.gemm_problem("normal_rowscaled", 19, "T", "N", 700, 650, 900, pad=1)
+        outs.append(run_sgemm(h, SPLIT, "T", "N", 700, 650, 900, -1.0, A, lda, B, ldb, 1.0, C, ldc))
+    h.set_packing(gbgemm.PACKING_AUTO)
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
