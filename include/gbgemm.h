@@ -100,22 +100,6 @@ int gbgemm_set_stream(gbgemm_handle* h, void* cuda_stream);
  * the error bound is then not guaranteed.  Bad code: GBGEMM_ERR_INVALID_VALUE. */
 int gbgemm_set_path(gbgemm_handle* h, int path);
 
-/* Where the split path packs its operands into BF16 panels (BLIS packing,
- * Section III-A): GBGEMM_PACKING_SEPARATE, a launch of its own ahead of the
- * GEMM kernel (many thread blocks per SM); GBGEMM_PACKING_FUSED, packer warps
- * inside the persistent GEMM kernel, which start the tiles whose panels are
- * ready while later ones are still being packed (grouped plans then keep
- * their panels in a ring sized for L2, see gbgemm_set_grouped_ring_bytes);
- * GBGEMM_PACKING_AUTO (the default), the faster of the two as measured on
- * GB300.  Applies to later calls and to plans created later.  Results are
- * the same bit for bit either way.  Bad mode: GBGEMM_ERR_INVALID_VALUE. */
-typedef enum {
-  GBGEMM_PACKING_AUTO = 0,
-  GBGEMM_PACKING_SEPARATE = 1,
-  GBGEMM_PACKING_FUSED = 2
-} gbgemm_packing;
-int gbgemm_set_packing(gbgemm_handle* h, int mode);
-
 /* Path taken by the handle's most recent gbgemm_sgemm (0 when it returned
  * early without launching the product kernels). */
 int gbgemm_last_path(gbgemm_handle* h, int* path);
@@ -149,8 +133,9 @@ int gbgemm_sgemm(gbgemm_handle* h, char transa, char transb, int64_t m, int64_t 
  * of fixed-size problems fed by BLIS (Section III-A, III-C); the paper itself
  * has no batched call.  stride_a or stride_b 0 shares one operand among all
  * problems; the results must not overlap (stride_c >= ldc (n - 1) + m when
- * batch > 1).  One packing launch per operand and one persistent GEMM launch
- * serve the whole batch (split path), or one SIMT launch.  The workspace
+ * batch > 1).  One packing launch (both operands of every problem) and one
+ * persistent GEMM launch serve the whole batch (split path), or one SIMT
+ * launch.  The workspace
  * holds about batch x gbgemm_split_workspace_bytes(m, n, k) bytes on the
  * split path.
  * Argument errors, in this order: transa -1, transb -2, m -3, n -4, k -5,
@@ -361,27 +346,6 @@ int gbgemm_grouped_plan_stats(const gbgemm_grouped_plan* plan, int64_t* n_split,
                               double* flops_simt, int* kernels_per_run, size_t* device_bytes);
 /* Free the plan (synchronises the device first). */
 int gbgemm_grouped_plan_destroy(gbgemm_grouped_plan* plan);
-/* Size of the panel ring of plans created later with this handle: the
- * split-path problems' hi/lo panels are packed into a ring of this many
- * bytes, reused problem after problem, so that they are read back from L2
- * instead of HBM.  0 selects the default (64 MiB); otherwise 1 MiB .. 64 GiB
- * (a ring is never smaller than the largest problem's panels, nor larger
- * than all of them).  GBGEMM_ERR_INVALID_VALUE outside that range. */
-int gbgemm_set_grouped_ring_bytes(gbgemm_handle* h, size_t bytes);
-/* The ring layout a plan uses (host only, for inspection and tests): count
- * regions of sizes[i] bytes (each a nonzero multiple of `granule`, none
- * larger than ring_bytes, itself a multiple of `granule`) are placed one
- * after another in order, wrapping to offset 0 when the next one does not
- * fit.  offsets[i] = region i's offset; wait_list[wait_begin[i] ..
- * wait_begin[i] + wait_count[i]) = the distinct earlier regions that last
- * wrote one of region i's granules, which the GEMM must have finished
- * reading before region i is packed.  *wait_total = entries needed; when it
- * exceeds wait_capacity the call returns GBGEMM_ERR_INVALID_VALUE (as for
- * any bad argument) after filling offsets, wait_begin and wait_count. */
-int gbgemm_grouped_ring_layout(const uint64_t* sizes, int64_t count, uint64_t ring_bytes, uint64_t granule,
-                               uint64_t* offsets, int32_t* wait_begin, int32_t* wait_count, int32_t* wait_list,
-                               int64_t wait_capacity, int64_t* wait_total);
-
 /* ---------------------------------------------------------------------- */
 /* Autotuner.  The paper fixes its micro-kernel sizes at compile time
  * (Sections III-C, III-D); here every legal configuration (gbgemm_config) of

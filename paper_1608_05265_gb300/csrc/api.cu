@@ -38,8 +38,6 @@ struct gbgemm_handle {
   int64_t kernel_launches = 0;
   // tuning
   int tuning = 0;
-  size_t grouped_ring_bytes = 0;   // panel ring of grouped plans (0: the default)
-  int packing = GBGEMM_PACKING_AUTO;  // where the split path packs its operands
   gbg::Tuner tuner;
   gbg::Predictor predictor;
 };
@@ -260,8 +258,7 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   c.batch = batch; c.sa = sa; c.sb = sb; c.sc = sc;
   c.bn = split_bn; c.raster = 16; c.splitk = splitk;
   c.ws = h->ws; c.status = h->d_status; c.num_sms = h->num_sms;
-  c.fused = h->packing == GBGEMM_PACKING_FUSED;
-  h->kernel_launches += c.fused ? 1 : 2;  // the memset of the workspace head (and the packing launch)
+  h->kernel_launches += 2;  // the memset of the workspace head and the packing launch
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (gbg::launch_split_call(c, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
@@ -595,9 +592,9 @@ int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, in
   const int64_t stored_rows = kcontig ? k : rows;
   if (ldx < (stored_rows > 1 ? stored_rows : 1)) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard g(h->device);
-  // The GEMM kernel's packers alone (no tiles), on the K-vectors as rows of
-  // an "A" operand; the panels are cleared first so that the padding rows of
-  // the last (even) block read as zeros.
+  // The packing launch alone (no tiles), on the K-vectors as rows of an "A"
+  // operand; the panels are cleared first so that the padding rows of the
+  // last (even) block read as zeros.
   const gbg::SplitLayout L = gbg::split_layout(rows, 0, k, 1, 1, 256);
   int rc = ensure_workspace(h, L.head);
   if (rc != GBGEMM_OK) return rc;
@@ -609,7 +606,6 @@ int gbgemm_split_pack(gbgemm_handle* h, char which, char trans, int64_t rows, in
   c.ta = kcontig ? 1 : 0; c.m = rows; c.n = 0; c.k = k;
   c.A = X; c.lda = ldx;
   c.ws = h->ws; c.status = h->d_status; c.num_sms = h->num_sms;
-  c.fused = h->packing == GBGEMM_PACKING_FUSED;
   c.pack_only = true; c.panel_out = panel; c.panel2_out = gbg::split_parts(k) == 2 ? panel2 : nullptr;
   c.amax_out = amax_bits;
   return gbg::launch_split_call(c, h->stream) == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
@@ -628,8 +624,6 @@ int create_plan(gbgemm_handle* h, const gbgemm_problem* probs, int64_t count, co
   P->num_sms = h->num_sms;
   P->status = h->d_status;
   P->count = count;
-  P->ring_bytes = h->grouped_ring_bytes;
-  P->fused = h->packing == GBGEMM_PACKING_FUSED;
   P->configs = new (std::nothrow) int[count > 0 ? count : 1];
   if (!P->configs) {
     delete P;
@@ -914,21 +908,6 @@ int gbgemm_tuning_load(gbgemm_handle* h, const char* path) {
 int gbgemm_tuning_clear(gbgemm_handle* h) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   h->tuner.cache.clear();
-  return GBGEMM_OK;
-}
-
-int gbgemm_set_grouped_ring_bytes(gbgemm_handle* h, size_t bytes) {
-  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
-  if (bytes != 0 && (bytes < ((size_t)1 << 20) || bytes > ((size_t)64 << 30))) return GBGEMM_ERR_INVALID_VALUE;
-  h->grouped_ring_bytes = bytes;
-  return GBGEMM_OK;
-}
-
-int gbgemm_set_packing(gbgemm_handle* h, int mode) {
-  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
-  if (mode != GBGEMM_PACKING_AUTO && mode != GBGEMM_PACKING_SEPARATE && mode != GBGEMM_PACKING_FUSED)
-    return GBGEMM_ERR_INVALID_VALUE;
-  h->packing = mode;
   return GBGEMM_OK;
 }
 

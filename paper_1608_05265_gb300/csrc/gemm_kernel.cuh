@@ -1,21 +1,26 @@
-// The persistent split-BF16 tcgen05 GEMM kernel with fused operand packing,
-// templated on its scheduler: SingleSched walks the tiles of one problem (or
-// a strided batch) in a rasterised order, GroupedSched walks the tiles of
-// many problems, problem after problem.  The per-tile job carries everything
-// a role needs, including the tile width BN (64, 128 or 256) as a run-time
-// value: the MMA instruction descriptor, the B copy size and the epilogue
-// width all follow it, and shared memory and TMEM are sized for MAXBN.
+// The persistent split-BF16 tcgen05 GEMM kernel and the packing kernel
+// that runs ahead of it, templated on the scheduler: SingleSched walks the
+// tiles of one problem (or a strided batch) in a rasterised order,
+// GroupedSched walks the tiles of many problems, problem after problem.  The
+// per-tile job carries everything a role needs, including the tile width BN
+// (64, 128 or 256) as a run-time value: the MMA instruction descriptor, the
+// B copy size and the epilogue width all follow it, and shared memory and
+// TMEM are sized for MAXBN.
 //
-// Roles (one CTA per SM, 576 threads):
+// Packing (BLIS packing, Section III-A): one CTA of 256 threads per packing
+// task (4 x 32 k of one 128-row band of one operand), several per SM, the
+// operand read straight into registers; each task counts itself on its
+// band's counter, and the task that completes a band re-packs the band's
+// badly scaled rows.  The GEMM launch follows on the same stream.
+//
+// GEMM roles (one CTA per SM, 608 threads):
 //   warp 0, lane 0  producer: takes the next tile from a device-wide counter
-//                   (dynamic scheduling, so any subset of resident CTAs makes
-//                   progress), hands its index to the other roles through a
-//                   four-slot queue in shared memory, waits until the panel
-//                   bands the tile reads are packed, and streams one bulk
-//                   async copy of the 128-row A block and one of the BN B
-//                   rows per 32-deep k chunk into the stage ring ("full"
-//                   mbarriers); with beta != 0 it first asks L2 for the
-//                   tile's C columns, so the epilogue finds them there;
+//                   (dynamic scheduling, so the CTAs that run finish the
+//                   work however many are resident), hands its index to the
+//                   other roles through a four-slot queue in shared memory,
+//                   and streams one bulk async copy of the 128-row A block
+//                   and one of the BN B rows per 32-deep k chunk into the
+//                   stage ring ("full" mbarriers);
 //   warp 1          owns TMEM (two 128 x MAXBN FP32 accumulators); lane 0
 //                   issues the MMAs (hi*hi, hi*lo, lo*hi for both 16-deep
 //                   halves of a chunk, six products with the three-part
@@ -24,26 +29,19 @@
 //                   -- the paper's Accumulator (Section III-C): clear on the
 //                   first k block, accumulate, send the result after the
 //                   last;
-//   warps 2-9       epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (the
-//                   tile rows it owns) for half of the tile's columns,
+//   warps 2-17      epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (the
+//                   tile rows it owns) for a quarter of the tile's columns,
 //                   applies 2^(e_i + f_j), alpha and beta once and stores
 //                   column-major C with one 128-byte store per warp and
 //                   column (Section III-D: each core owns whole column
 //                   blocks of the result so that stores stay contiguous);
-//   warps 10-17     packers (BLIS packing, Section III-A): take packing
-//                   tasks (4 x 32 k of one 128-row band of one operand) from
-//                   a second device-wide counter, split them into the hi/lo
-//                   panels and row maxima, and count each finished task on
-//                   the band's counter; the task that completes a band
-//                   re-packs the band's badly scaled rows (if any) and marks
-//                   the band ready.  Tasks come in the order the tiles need
-//                   them, so the first tiles start while later bands are
-//                   still being packed.  For a grouped batch the panels live
-//                   in a ring smaller than L2: a problem is packed only after
-//                   the problems whose ring bytes it reuses have been read.
+//   warp 18         with beta != 0, asks L2 for each tile's C columns as soon
+//                   as the tile is handed out, so that the epilogue's reads
+//                   of C find them there.
 // Every wait is bounded: on expiry the kernel records GBGEMM_ERR_DEVICE_TIMEOUT,
 // raises a CTA-wide abort flag, drains its own copies and MMAs, frees TMEM
-// and returns.
+// and returns.  Waiting threads sleep (mbarrier try_wait with a suspend
+// hint) instead of spinning.
 #pragma once
 
 #include "split_device.cuh"
@@ -53,21 +51,16 @@ namespace {
 
 constexpr int kStages = 4;                         // ring depth of the general (BN <= 256) kernel
 constexpr int kMaxBN = 256;
-constexpr int kEpiWarp0 = 2;
-// Warps 2-17 are sixteen epilogue warps (four per TMEM lane quadrant, each a
-// quarter of the columns) when the operands were packed beforehand, or
-// eight epilogue warps (each half of the columns) and eight packer warps
-// when the kernel packs them itself.
-__host__ __device__ constexpr int epi_warps(int pstg) { return pstg == 0 ? 16 : 8; }
-constexpr int kPackWarps = 8;
-constexpr int kCpfWarp = kEpiWarp0 + 16;           // asks L2 for the C tiles ahead of the epilogue
-constexpr int kGemmThreads = 32 * (kCpfWarp + 1);
+constexpr int kNarrowStages = 6;                   // ring depth of the BN <= 128 instance
+constexpr int kNarrowBN = 128;
+constexpr int kEpiWarps = 16;
+constexpr int kCpfWarp = 2 + kEpiWarps;            // the C prefetch warp
+constexpr int kGemmThreads = 32 * (kCpfWarp + 1);  // 19 warps, charged as 20: 96 registers per thread
 constexpr int kTileQ = 4;                          // tile-index queue between the roles
-constexpr int kPackChunks = 4;                     // k chunks per packing task (two rounds of two)
+constexpr int kPackChunks = 4;                     // k chunks per packing task
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // Suspend-time hint of the mbarrier waits: a waiting thread sleeps until the
-// phase completes (or this long) instead of spinning, leaving the issue
-// slots to the packers.
+// phase completes (or this long) instead of spinning.
 constexpr uint32_t kHintNs = 20000u;
 // The final drain waits (the producer's copies landing, the MMAs finishing
 // before TMEM is freed) take their own, longer bound, whatever limit the
@@ -75,40 +68,17 @@ constexpr uint32_t kHintNs = 20000u;
 // still in flight.
 constexpr uint64_t kDrainTimeoutNs = 4000000000ull;
 // Shared memory of a kernel instance: STAGES ring slots of one A block and
-// MAXBN B rows, PSTG 16 KiB staging buffers of the packers (one FP32 chunk
-// of 128 rows x 32 k each, one per packing team), barriers and role
-// scratch, 1024-byte alignment.  Every team double-buffers its chunks.  With
-// tiles of at most 128 columns the memory holds four ring slots and four
-// staging buffers (two packing teams: the grouped batches pack the most
-// data), else four ring slots and two staging buffers (one team), which
-// uses all 227 KiB.
-constexpr int kSmemTail = 2048;  // barriers, tile queue, packing slots
-// A staging buffer holds half a band (64 rows) of one 32-deep k chunk, each
-// row (k contiguous) or k column (rows contiguous) as the 16-byte aligned
-// range that covers it: 64 rows x 144 bytes, or 32 columns x 272 bytes.
-constexpr int kStageRowPitch = 36;   // floats: 9 pieces of 16 bytes
-constexpr int kStageColPitch = 68;   // floats: 17 pieces of 16 bytes
-constexpr int kStageBytes = 64 * kStageRowPitch * 4;
-static_assert(32 * kStageColPitch * 4 <= kStageBytes, "staging buffer");
-template <int STAGES, int MAXBN, int PSTG>
-constexpr int gemm_smem_bytes() {
-  return STAGES * (kBlockBytes + MAXBN * 128) + PSTG * kStageBytes + 1024 + kSmemTail;
-}
-constexpr int kPackStages = 2;                     // staging buffers of the BN <= 256 instance: one team
-constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN, kPackStages>();
-constexpr int kNarrowStages = 4;                   // ring depth of the BN <= 128 instance
-constexpr int kNarrowBN = 128;
-constexpr int kNarrowPackStages = 8;               // two teams of four buffers
-constexpr int kNarrowPrepackStages = 6;            // ring depth of the BN <= 128 instance without packers
-static_assert(kGemmSmemBytes <= 232448, "shared memory of the BN 256 instance");
-static_assert(gemm_smem_bytes<kNarrowStages, kNarrowBN, kNarrowPackStages>() <= 232448, "narrow instance");
+// MAXBN B rows, barriers and the tile queue, 1024-byte alignment.  With tiles
+// of at most 128 columns the same memory holds a six-slot ring.
+template <int STAGES, int MAXBN>
+constexpr int gemm_smem_bytes() { return STAGES * (kBlockBytes + MAXBN * 128) + 1024 + 256; }
+constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN>();
 
 // Per-launch control words; zeroed before every launch together with the
-// band counters, the consumption counters and the row maxima.
+// band counters and the row maxima.
 struct WorkCtl {
   int tile_next;   // next work item
-  int pack_next;   // next packing task
-  int pad[62];
+  int pad[63];
 };
 static_assert(sizeof(WorkCtl) == kSplitCtlBytes, "control block size");
 
@@ -121,9 +91,6 @@ struct TileJob {
   int nkc;                  // k chunks
   int bn;                   // tile width: 64, 128 or 256
   int parts;                // 1: [hi | lo] panels, 3 products; 2: also compact lo3 panels, 6 products
-  int ready;                // value of a band counter once the band is packed
-  int bandA, bandB0, nbandB;  // band counters to wait for (A band, first B band, B band count)
-  int problem;              // consumption counter to bump once the panels are read (-1: none)
   int64_t a_part, b_part;   // byte offsets from the [hi | mid] panels to the compact lo3 panels
   int64_t m0, n0;           // tile origin in C
   int64_t m, n;             // problem extents
@@ -152,9 +119,6 @@ struct PackJob {
   int kc0, nkc;
   int kcontig;
   int band, band_tasks;     // band counter and the tasks that fill it
-  int problem;              // owning problem (ring waits), -1: none
-  const int* wait_list;     // problems whose panels must be read first
-  int wait_count;
 };
 
 // B rows [r0, r0 + bn) of a panel start inside 128-row block r0/128 at row
@@ -219,12 +183,6 @@ struct SingleSched {
     j.b_src = panel_rows(panelB + (size_t)z * ps, (int64_t)tn * bn) + (size_t)kc0 * j.b_kstride;
     j.nkc = (nkc - kc0 < slice_chunks) ? nkc - kc0 : slice_chunks;
     j.bn = bn;
-    j.ready = ngroups + 1;
-    j.bandA = z * (ra + rb) + tm;
-    const int b0 = (tn * bn) >> 7, b1 = min(rb - 1, (tn * bn + bn - 1) >> 7);
-    j.bandB0 = z * (ra + rb) + ra + b0;
-    j.nbandB = b1 - b0 + 1;
-    j.problem = -1;
     j.partial = splitk > 1 ? partial + ((size_t)(sl * tiles_m + tm) * tiles_n + tn) * 128 * bn : nullptr;
     j.parts = parts; j.a_part = a_part; j.b_part = b_part;
     j.m0 = (int64_t)tm * 128; j.n0 = (int64_t)tn * bn;
@@ -259,13 +217,8 @@ struct SingleSched {
     P.nkc = nkc;
     P.band = z * (ra + rb) + (is_a ? 0 : ra) + idx;
     P.band_tasks = ngroups;
-    P.problem = -1;
-    P.wait_list = nullptr;
-    P.wait_count = 0;
     return P;
   }
-  __device__ __forceinline__ int* done_counters() const { return nullptr; }
-  __device__ __forceinline__ int need_of(int) const { return 0; }
 };
 
 // Device descriptor of one problem of a grouped batch on the split path.
@@ -277,10 +230,8 @@ struct GroupDev {
   int nkc, bn;
   int64_t rowsA, rowsB;     // panel rows per k chunk
   float alpha, beta;
-  int parts, ready;         // ready: value of a band counter once the band is packed
+  int parts, pad_;
   int64_t a_part, b_part;   // byte offsets to the compact lo3 panels (parts == 2)
-  int bandA0, bandB0;       // counters of A band 0 and B band 0
-  int rbB, pad_;            // B bands packed
 };
 
 // One 128-row band of one operand of a grouped problem, as the packers see it.
@@ -293,24 +244,19 @@ struct PackBand {
   int64_t rows, k, rows_alloc;
   int rb, nkc;
   int kcontig, ngroups;
-  int first_task, problem;
-  int wait_begin, wait_count;  // the problem's ring waits: wait_list[wait_begin ..)
-  int cnt, pad_;               // the band's counter
+  int first_task, cnt;      // the band's first packing task and its counter
 };
 
 // Many problems: item t = (group, tile row, tile column), the items of one
-// problem together, problems in packing order (decreasing cost per tile, so
-// that the cheap tiles come last and fill the gaps).
+// problem together, problems in decreasing cost per tile, so that the cheap
+// tiles come last and fill the gaps.
 struct GroupedSched {
   WorkCtl* ctl;
   int* band_cnt;
-  int* done;                // tiles of each problem whose panels have been read
   const int4* items;
   const GroupDev* groups;
   const PackBand* bands;
   const int* task_band;
-  const int* wait_list;
-  const int* need;          // tiles of each problem (its consumption counter's final value)
   int n_items, n_tasks;
   __device__ __forceinline__ int num_items() const { return n_items; }
   __device__ __forceinline__ TileJob job(int t) const {
@@ -322,12 +268,6 @@ struct GroupedSched {
     j.a_kstride = (size_t)g.rowsA * 128;
     j.b_kstride = (size_t)g.rowsB * 128;
     j.nkc = g.nkc; j.bn = g.bn;
-    j.ready = g.ready;
-    j.bandA = g.bandA0 + it.y;
-    const int b0 = (it.z * g.bn) >> 7, b1 = min(g.rbB - 1, (it.z * g.bn + g.bn - 1) >> 7);
-    j.bandB0 = g.bandB0 + b0;
-    j.nbandB = b1 - b0 + 1;
-    j.problem = it.x;
     j.parts = g.parts; j.a_part = g.a_part; j.b_part = g.b_part;
     j.m0 = (int64_t)it.y * 128; j.n0 = (int64_t)it.z * g.bn;
     j.m = g.m; j.n = g.n;
@@ -348,38 +288,19 @@ struct GroupedSched {
     P.kcontig = B.kcontig;
     P.band = B.cnt;
     P.band_tasks = B.ngroups;
-    P.problem = B.problem;
-    P.wait_list = wait_list + B.wait_begin;
-    P.wait_count = B.wait_count;
     return P;
   }
-  __device__ __forceinline__ int* done_counters() const { return done; }
-  __device__ __forceinline__ int need_of(int q) const { return need[q]; }
 };
 
-// Packing teams: the eight packer warps form NT teams of TS = 256 / NT
-// threads, each with its own named barrier and NB = PSTG / NT staging
-// buffers.  A team streams the half chunks (64 rows x 32 k) of its tasks
-// through its buffers: while one is split and stored, the next ones (of
-// this task or of the task the team takes next) are in flight, and the next
-// task's descriptor is fetched during the current one.
-//
-// Staging copies are 16-byte cp.async.cg (through L2 only, whatever the
-// alignment of the leading dimension): each row (k contiguous) or k column
-// (rows contiguous) is copied as the 16-byte aligned range around it, the
-// bytes past its last element cut off by the copy size (and zero-filled), so
-// nothing outside the row or column ahead of it is read; only where that
-// range would start before X itself (X not 16-byte aligned) does the first
-// piece go element by element.  The split reads each value at its offset
-// (0..3 floats) inside the staged range.
-//
-// Item (rr, cc) of a half chunk: row rr (0..63) and 8-wide k piece cc
-// (0..3); item idx = tid + TS * it.  KCONTIG (element (r,p) at X[r*ld + p]):
-// four consecutive items per row.  !KCONTIG (X[r + p*ld]): 32 consecutive
-// rows per warp, one piece per warp.
-template <bool KCONTIG, int TS>
+// Item (rr, cc) of a chunk in a packing CTA: row rr (0..127) of the band and
+// 8-wide k piece cc (0..3); item idx = tid + 256 * it, two per thread.
+// KCONTIG (element (r,p) at X[r*ld + p]): four consecutive items per row, so
+// a warp reads eight 128-byte row pieces.  !KCONTIG (X[r + p*ld]): 32
+// consecutive rows per warp and one piece per warp, so every load
+// instruction reads 128 contiguous bytes.
+template <bool KCONTIG>
 __device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
-  const int idx = tid + TS * it;
+  const int idx = tid + 256 * it;
   if (KCONTIG) {
     rr = idx >> 2;
     cc = idx & 3;
@@ -390,100 +311,8 @@ __device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
   }
 }
 
-// One 16-byte piece of a staged range: bytes [ps, ps + 16) of the source,
-// of which [.., end) are wanted; xb is X's address.
-__device__ __forceinline__ void stage_piece(uint32_t dst, uintptr_t ps, uintptr_t end, uintptr_t xb) {
-  const int64_t left = (int64_t)end - (int64_t)ps;
-  const uint32_t nb = left <= 0 ? 0u : (left >= 16 ? 16u : (uint32_t)left);
-  if (ps >= xb || nb == 0u) {
-    cp_async16(dst, reinterpret_cast<const void*>(nb ? ps : xb), nb);
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {  // the range starts before X: element by element
-      const uintptr_t q = ps + 4 * e;
-      const bool ok = q >= xb && q + 4 <= end;
-      cp_async4(dst + 4 * e, reinterpret_cast<const void*>(ok ? q : xb), ok ? 4u : 0u);
-    }
-  }
-}
-
-// Stage half `h` (rows 64h .. 64h + 63 of the band) of k chunk kc into the
-// staging buffer at shared address stg: KCONTIG [row][36 floats], else
-// [k][68 floats].  Zeros outside the operand.
-template <bool KCONTIG, int TS>
-__device__ __forceinline__ void stage_half(const PackJob& P, int64_t kc, int h, uint32_t stg, int tid) {
-  const int64_t r0 = P.rb * 128 + 64 * h, p0 = kc * 32;
-  const uintptr_t xb = reinterpret_cast<uintptr_t>(P.X);
-  if (KCONTIG) {
-    const int64_t kv = P.k - p0 < 32 ? P.k - p0 : 32;  // k values of the chunk (> 0)
-    for (int id = tid; id < 64 * 9; id += TS) {
-      const int row = id / 9, piece = id - row * 9;
-      const int64_t r = r0 + row;
-      const uintptr_t addr = xb + (uintptr_t)(r * P.ld + p0) * 4;
-      const uintptr_t a = addr & ~(uintptr_t)15;
-      const uintptr_t end = (r < P.rows) ? addr + (uintptr_t)kv * 4 : 0;
-      stage_piece(stg + (uint32_t)(row * kStageRowPitch * 4 + piece * 16), a + 16 * piece, end, xb);
-    }
-  } else {
-    const int64_t rv = P.rows - r0 < 64 ? P.rows - r0 : 64;  // rows of the half (may be <= 0)
-    for (int id = tid; id < 32 * 17; id += TS) {
-      const int kk = id / 17, piece = id - kk * 17;
-      const int64_t p = p0 + kk;
-      const uintptr_t addr = xb + (uintptr_t)(r0 + p * P.ld) * 4;
-      const uintptr_t a = addr & ~(uintptr_t)15;
-      const uintptr_t end = (p < P.k && rv > 0) ? addr + (uintptr_t)rv * 4 : 0;
-      stage_piece(stg + (uint32_t)(kk * kStageColPitch * 4 + piece * 16), a + 16 * piece, end, xb);
-    }
-  }
-}
-
-// Split and store half h of k chunk kc of a task from the staging buffer at
-// sf (store_split8 / store_split8_3), folding the rows' maxima into mxr.
-template <bool KCONTIG, int TS>
-__device__ __forceinline__ void convert_half(const PackJob& P, int64_t kc, int h, const float* sf, int tid,
-                                             uint32_t (&mxr)[2][256 / TS]) {
-  constexpr int IT = 256 / TS;
-  const int64_t r0 = P.rb * 128 + 64 * h, p0 = kc * 32;
-  const int64_t xw = (int64_t)(reinterpret_cast<uintptr_t>(P.X) >> 2);  // X in floats
-  uint8_t* blk = P.panel + ((size_t)kc * P.rows_alloc + P.rb * 128) * 128;
-  uint8_t* blk2 = P.panel2 ? P.panel2 + ((size_t)(kc >> 1) * P.rows_alloc + P.rb * 128) * 128 : nullptr;
-#pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    int rr, cc;
-    item_of<KCONTIG, TS>(tid, it, rr, cc);
-    float x[8];
-    if (KCONTIG) {
-      const int sh = (int)((xw + (r0 + rr) * P.ld + p0) & 3);
-      const float* src = sf + rr * kStageRowPitch + sh + cc * 8;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = src[q];
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int kk = cc * 8 + q;
-        const int sh = (int)((xw + r0 + (p0 + kk) * P.ld) & 3);
-        x[q] = sf[kk * kStageColPitch + sh + rr];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) mxr[h][it] = max(mxr[h][it], __float_as_uint(x[q]) & 0x7FFFFFFFu);
-    const int row = 64 * h + rr;
-    if (P.rb * 128 + row < P.rows_alloc) {
-      if (blk2) store_split8_3(blk, blk2, (int)(kc & 1), row, cc, x);
-      else store_split8(blk, row, cc, x);
-    }
-  }
-}
-
 __device__ __forceinline__ int task_chunks(const PackJob& P) {
   return (P.nkc - P.kc0 < kPackChunks) ? P.nkc - P.kc0 : kPackChunks;
-}
-
-template <int TS>
-__device__ __forceinline__ void stage_any(const PackJob& P, int64_t kc, int h, uint32_t stg, int tid) {
-  if (P.kcontig) stage_half<true, TS>(P, kc, h, stg, tid);
-  else stage_half<false, TS>(P, kc, h, stg, tid);
-  cp_async_commit();
 }
 
 // ---------------------------------------------------------------------------
@@ -491,8 +320,7 @@ __device__ __forceinline__ void stage_any(const PackJob& P, int64_t kc, int h, u
 // scheduler, the operand read straight into registers (all loads of two
 // chunks in flight before any is split), several CTAs per SM.  Counts the
 // task on its band's counter; the task that completes a band re-packs the
-// band's badly scaled rows.  Used where the GEMM kernel runs without packer
-// warps: the two launches are ordered on the stream.
+// band's badly scaled rows.
 // ---------------------------------------------------------------------------
 template <bool KCONTIG>
 __device__ __forceinline__ void load8(const PackJob& P, int64_t r, int64_t p, bool vec, float (&x)[8]) {
@@ -526,7 +354,7 @@ __device__ __forceinline__ void pack_task_regs(const PackJob& P, uint32_t* smax)
 #pragma unroll
       for (int it = 0; it < 2; ++it) {
         int rr, cc;
-        item_of<KCONTIG, 256>(tid, it, rr, cc);
+        item_of<KCONTIG>(tid, it, rr, cc);
         if (c0 + c < nch) load8<KCONTIG>(P, r0 + rr, (int64_t)(P.kc0 + c0 + c) * 32 + cc * 8, vec, x[c][it]);
       }
 #pragma unroll
@@ -538,7 +366,7 @@ __device__ __forceinline__ void pack_task_regs(const PackJob& P, uint32_t* smax)
 #pragma unroll
       for (int it = 0; it < 2; ++it) {
         int rr, cc;
-        item_of<KCONTIG, 256>(tid, it, rr, cc);
+        item_of<KCONTIG>(tid, it, rr, cc);
 #pragma unroll
         for (int q = 0; q < 8; ++q) mxr[it] = max(mxr[it], __float_as_uint(x[c][it][q]) & 0x7FFFFFFFu);
         if (r0 + rr < P.rows_alloc) {
@@ -552,7 +380,7 @@ __device__ __forceinline__ void pack_task_regs(const PackJob& P, uint32_t* smax)
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     int rr, cc;
-    item_of<KCONTIG, 256>(tid, it, rr, cc);
+    item_of<KCONTIG>(tid, it, rr, cc);
     if (mxr[it] != 0u) atomicMax(&smax[rr], mxr[it]);
   }
   __syncthreads();
@@ -576,19 +404,16 @@ __global__ void __launch_bounds__(256) pack_tasks_kernel(const Sched S) {
   __syncthreads();
   if (finisher) {
     __threadfence();
-    rescale_block<256>(P.rows, P.k, P.X, P.ld, P.kcontig != 0, P.amax, P.panel, P.panel2, P.rows_alloc, P.nkc, P.rb,
-                       reinterpret_cast<int*>(smax), threadIdx.x, TeamBar{0, 256});
+    rescale_block(P.rows, P.k, P.X, P.ld, P.kcontig != 0, P.amax, P.panel, P.panel2, P.rows_alloc, P.nkc, P.rb,
+                  reinterpret_cast<int*>(smax));
   }
 }
 
 // One CTA per SM.  Registers are handed out to whole groups of four warps,
 // so the 19 warps are charged as 20: 96 registers per thread.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, int PSTG = kPackStages>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
-  constexpr int kEpiWarps = epi_warps(PSTG);
-  constexpr int kPackWarp0 = kEpiWarp0 + kEpiWarps;
-  constexpr bool kFused = PSTG > 0;
   constexpr uint32_t A_BYTES = kBlockBytes;        // 128 rows x 128 B
   constexpr uint32_t B_STAGE = MAXBN * 128;        // room for MAXBN rows x 128 B
   constexpr uint32_t kTmemCols = 2 * MAXBN;        // two accumulator buffers
@@ -601,8 +426,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   uint8_t* const base_ptr = smem_raw + (base - raw_addr);
   const uint32_t sA = base;                                   // kStages x A_BYTES
   const uint32_t sB = base + kStages * A_BYTES;               // kStages x B_STAGE
-  const uint32_t sP = sB + kStages * B_STAGE;                 // PSTG packer staging buffers
-  const uint32_t bar0 = sP + PSTG * kStageBytes;              // barriers
+  const uint32_t bar0 = sB + kStages * B_STAGE;               // barriers
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
   auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
@@ -614,8 +438,6 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tail + 4);
   volatile int* tile_q = reinterpret_cast<volatile int*>(tail + 16);          // kTileQ ints
-  volatile int* pack_slot = reinterpret_cast<volatile int*>(tail + 64);    // 4 ints per packing team
-  uint32_t* team_smax = reinterpret_cast<uint32_t*>(tail + 128);            // 128 words per packing team
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_items = S.num_items();
@@ -662,17 +484,6 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
         if (t < 0) break;
         const TileJob J = S.job(t);
-        if (kFused) {
-          // the panel bands this tile reads must be packed
-          bool ready = wait_counter(S.band_cnt + J.bandA, J.ready, abort_flag, timeout_ns);
-          for (int b = 0; b < J.nbandB && ready; ++b)
-            ready = wait_counter(S.band_cnt + J.bandB0 + b, J.ready, abort_flag, timeout_ns);
-          if (!ready) {
-            raise_status(status, abort_flag);
-            break;
-          }
-          fence_proxy_async_global();
-        }
         const uint32_t b_bytes = (uint32_t)J.bn * 128u;
         // one ring slot per k chunk, and with three parts one more per pair
         // of chunks (the compact [lo3 | lo3] block, loaded with the even chunk)
@@ -712,7 +523,6 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       uint32_t aphase = 0;
       int tq = 0;
       uint32_t tqph = 0;
-      int* const done = S.done_counters();
       bool ok = true;
       while (ok) {
         if (!mbar_wait_hint(tqf_bar(tq), tqph, abort_flag, timeout_ns, kHintNs)) {
@@ -781,13 +591,6 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         if (!ok) break;
         mma_commit(accf_bar(abuf));      // the tile's accumulator is complete
         if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
-        // Every copy of this tile has landed (each full barrier was waited
-        // on): its panel bytes may now be reused.
-        if (kFused && done && J.problem >= 0) {
-          fence_proxy_async_global();
-          __threadfence();
-          atomicAdd(done + J.problem, 1);
-        }
       }
       // Wait until every MMA issued here has finished before TMEM is released.
       mma_commit(drain_bar);
@@ -795,10 +598,10 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       if (!mbar_wait(drain_bar, 0u, &never, kDrainTimeoutNs)) raise_status(status, abort_flag);
     }
     __syncwarp();
-  } else if (warp < kPackWarp0) {
+  } else if (warp < kCpfWarp) {
     // ---------------- epilogue ----------------
     const int q = warp & 3;
-    const int part = (warp - kEpiWarp0) >> 2;  // column half: 0 or 1
+    const int part = (warp - 2) >> 2;  // column quarter: 0 .. 3
     int abuf = 0;
     uint32_t aphase = 0;
     int tq = 0;
@@ -834,36 +637,37 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       const int ea = row_ok ? scale_exp_from_bits(__ldcg(J.amaxA + i)) : 0;
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kMaxBN);
       float* const crow = J.C + i;
+      constexpr int EC = 32;
       const int cols = (J.bn / (kEpiWarps / 4)) > 32 ? J.bn / (kEpiWarps / 4) : 32;
       const int c_begin = part * cols, c_end = (c_begin + cols < J.bn) ? c_begin + cols : J.bn;
       if (J.partial) {
         // split-K slice: the raw accumulator, whole tile, 32 consecutive rows per warp store
         float* pp = J.partial + q * 32 + lane;
-        for (int c0 = c_begin; c0 < c_end; c0 += 32) {
-          uint32_t r[32];
+        for (int c0 = c_begin; c0 < c_end; c0 += EC) {
+          uint32_t r[EC];
           tmem_ld32(taddr + (uint32_t)c0, r);
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) __stcg(pp + (size_t)(c0 + jj) * 128, __uint_as_float(r[jj]));
+          for (int jj = 0; jj < EC; ++jj) __stcg(pp + (size_t)(c0 + jj) * 128, __uint_as_float(r[jj]));
         }
       }
-      for (int c0 = c_begin; c0 < c_end && !J.partial; c0 += 32) {
+      for (int c0 = c_begin; c0 < c_end && !J.partial; c0 += EC) {
         if (J.n0 + c0 >= J.n) break;  // warp-uniform
-        const int jmax = (J.n - (J.n0 + c0) < 32) ? (int)(J.n - (J.n0 + c0)) : 32;
+        const int jmax = (J.n - (J.n0 + c0) < EC) ? (int)(J.n - (J.n0 + c0)) : EC;
         float* cp = crow + (J.n0 + c0) * J.ldc;
         // All loads of the chunk are issued before any result is formed, so
-        // the 32 column reads of C overlap instead of queueing one by one.
-        float cv[32];
+        // the column reads of C overlap instead of queueing one by one.
+        float cv[EC];
         if (J.beta != 0.f) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) cv[jj] = (row_ok && jj < jmax) ? __ldcs(cp + jj * J.ldc) : 0.f;
+          for (int jj = 0; jj < EC; ++jj) cv[jj] = (row_ok && jj < jmax) ? __ldcs(cp + jj * J.ldc) : 0.f;
         }
         const int64_t jl = J.n0 + c0 + lane;
-        const int eb_l = (jl < J.n) ? scale_exp_from_bits(__ldcg(J.amaxB + jl)) : 0;
-        uint32_t r[32];
+        const int eb_l = (lane < EC && jl < J.n) ? scale_exp_from_bits(__ldcg(J.amaxB + jl)) : 0;
+        uint32_t r[EC];
         tmem_ld32(taddr + (uint32_t)c0, r);
         // Every lane runs every shuffle; only the stores are predicated.
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
+        for (int jj = 0; jj < EC; ++jj) {
           const int s = ea + __shfl_sync(0xFFFFFFFFu, eb_l, jj);
           const float acc = __uint_as_float(r[jj]);
           // acc * 2^s: one multiply when 2^s is a normal float, else scalbnf.
@@ -907,145 +711,6 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         prefetch_l2(col + rows * 4 - 4);
       }
     }
-  } else if (kFused) {
-    // ---------------- packers ----------------
-    constexpr int NT = PSTG >= 8 ? 2 : 1;  // teams
-    constexpr int NB = PSTG / NT > 0 ? PSTG / NT : 1;  // staging buffers per team
-    constexpr int TS = 256 / NT;           // threads per team
-    constexpr int IT = 256 / TS;           // items per thread and half chunk
-    const int pt = threadIdx.x - kPackWarp0 * 32;
-    const int team = pt / TS, tid = pt % TS;
-    const TeamBar bar{1 + team, TS};
-    volatile int* slot = pack_slot + 4 * team;
-    uint32_t* smax = team_smax + 128 * team;
-    const uint32_t stg0 = sP + (uint32_t)(team * NB) * kStageBytes;
-    const uint8_t* const stg_ptr0 = base_ptr + (stg0 - base);
-    const int n_tasks = S.num_pack_tasks();
-    int* const done = S.done_counters();
-    int verified = -1;  // the last problem whose ring waits this team has seen through
-    int nxt = 0;
-    if (tid == 0) {
-      slot[0] = atomicAdd(&S.ctl->pack_next, 1);
-      nxt = atomicAdd(&S.ctl->pack_next, 1);
-    }
-    bar();
-    const int first = slot[0];
-    PackJob P, N;
-    int nhP = 0, issP = 0, nhN = 0, issN = 0;  // half chunks of a task, and those issued
-    bool haveN = false;
-    int sidx = 0, sissue = 0;  // half-chunk stream: next to split, next to issue (buffer = index % NB)
-    // keep every buffer busy: the current task's half chunks, then the next task's
-    auto refill = [&]() {
-      while (sissue - sidx < NB) {
-        const uint32_t dst = stg0 + (uint32_t)(sissue % NB) * kStageBytes;
-        if (issP < nhP) {
-          stage_any<TS>(P, P.kc0 + (issP >> 1), issP & 1, dst, tid);
-          ++issP;
-        } else if (haveN && issN < nhN) {
-          stage_any<TS>(N, N.kc0 + (issN >> 1), issN & 1, dst, tid);
-          ++issN;
-        } else {
-          break;
-        }
-        ++sissue;
-      }
-    };
-    bool ok = first < n_tasks;
-    if (ok) {
-      P = S.pack_job(first);
-      nhP = 2 * task_chunks(P);
-      refill();
-    }
-    while (ok) {
-      // the next task: its index was taken while the previous one ran
-      if (tid == 0) slot[1] = (*abort_flag) ? n_tasks : nxt;
-      bar();
-      const int ni = slot[1];
-      haveN = ni < n_tasks;
-      issN = 0;
-      if (haveN) {
-        N = S.pack_job(ni);
-        nhN = 2 * task_chunks(N);
-        if (tid == 0) nxt = atomicAdd(&S.ctl->pack_next, 1);
-      }
-      refill();
-      if (P.wait_count > 0 && P.problem != verified) {
-        // the ring bytes of this problem: every earlier problem that wrote
-        // them last must have been read by the GEMM
-        bool wok = true;
-        for (int w = tid; w < P.wait_count && wok; w += TS) {
-          const int qp = P.wait_list[w];
-          wok = wait_counter(done + qp, S.need_of(qp), abort_flag, timeout_ns);
-        }
-        if (bar.any(!wok)) {
-          if (tid == 0) raise_status(status, abort_flag);
-          break;
-        }
-        __threadfence();
-        verified = P.problem;
-      }
-      uint32_t mxr[2][IT];
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int it = 0; it < IT; ++it) mxr[h][it] = 0u;
-      for (int c = 0; c < nhP; ++c) {
-        cp_async_wait(sissue - sidx - 1);
-        bar();  // the half chunk has landed for every thread of the team
-        const float* sf = reinterpret_cast<const float*>(stg_ptr0 + (sidx % NB) * kStageBytes);
-        if (P.kcontig) convert_half<true, TS>(P, P.kc0 + (c >> 1), c & 1, sf, tid, mxr);
-        else convert_half<false, TS>(P, P.kc0 + (c >> 1), c & 1, sf, tid, mxr);
-        ++sidx;
-        bar();  // the buffer may be refilled
-        refill();
-      }
-      // the rows' maxima of the task
-      const int64_t r0 = P.rb * 128;
-      for (int r = tid; r < 128; r += TS) smax[r] = 0u;
-      bar();
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int it = 0; it < IT; ++it) {
-          int rr, cc;
-          if (P.kcontig) item_of<true, TS>(tid, it, rr, cc);
-          else item_of<false, TS>(tid, it, rr, cc);
-          if (mxr[h][it] != 0u) atomicMax(&smax[64 * h + rr], mxr[h][it]);
-        }
-      bar();
-      for (int r = tid; r < 128; r += TS)
-        if (r0 + r < P.rows && smax[r] != 0u) atomicMax(&P.amax[r0 + r], smax[r]);
-      // publish the task on its band's counter
-      fence_proxy_async_global();
-      bar();
-      if (tid == 0) {
-        __threadfence();
-        const int old = atomicAdd(S.band_cnt + P.band, 1);
-        __threadfence();  // the other tasks' maxima are visible from here on
-        slot[2] = (old == P.band_tasks - 1) ? 1 : 0;
-      }
-      bar();
-      if (slot[2]) {
-        // this task completed the band: every task's maxima are in, so the
-        // badly scaled rows can be re-packed (usually none), then the band
-        // is marked ready
-        __threadfence();
-        rescale_block<TS>(P.rows, P.k, P.X, P.ld, P.kcontig != 0, P.amax, P.panel, P.panel2, P.rows_alloc, P.nkc,
-                          P.rb, reinterpret_cast<int*>(smax), tid, bar);
-        fence_proxy_async_global();
-        bar();
-        if (tid == 0) {
-          __threadfence();
-          atomicAdd(S.band_cnt + P.band, 1);
-        }
-      }
-      if (!haveN) break;
-      P = N;
-      nhP = nhN;
-      issP = issN;
-      haveN = false;
-    }
-    cp_async_wait(0);  // no copy of this team is left in flight
   }
 
   tc_fence_before();
@@ -1058,15 +723,15 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
 
 // The shared-memory opt-in is a per-device function attribute: set it once
 // for every device a kernel instance is launched on.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, int PSTG = kPackStages>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
 cudaError_t ensure_gemm_smem_attr() {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN, PSTG>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem_bytes<STAGES, MAXBN, PSTG>());
+    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gemm_smem_bytes<STAGES, MAXBN>());
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }

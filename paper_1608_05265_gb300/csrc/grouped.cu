@@ -4,11 +4,11 @@
 // across problems: every problem is cut into tiles, the tiles of all
 // problems form one work list per kernel, and persistent CTAs drain it.
 //
-// Graph (one launch): zero the counters and row maxima, then one persistent
-// tcgen05 kernel whose packer warps split the operands of the split-path
-// problems into a panel ring that stays in L2 while its tile roles multiply
-// them; the SIMT-configured problems run on side branches, one grouped SIMT
-// kernel per tile shape and variant.
+// Graph (one launch): zero the counters and row maxima, pack every operand
+// of the split-path problems (one CTA per 128-row band and four k chunks),
+// then the persistent tcgen05 GEMM over all their tiles; the SIMT-configured
+// problems run on side branches, one grouped SIMT kernel per tile shape and
+// variant.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -119,33 +119,6 @@ void simt_tile_shape(int cfg, int& bm, int& bn) {
   }
 }
 
-void ring_layout(const std::vector<size_t>& sizes, size_t ring, size_t granule, std::vector<size_t>& off,
-                 std::vector<int>& wait_begin, std::vector<int>& wait_count, std::vector<int>& wait_list) {
-  const size_t n = sizes.size();
-  off.assign(n, 0);
-  wait_begin.assign(n, 0);
-  wait_count.assign(n, 0);
-  wait_list.clear();
-  std::vector<int> last_writer(ring / granule + 1, -1);
-  std::vector<int> seen(n, -1);
-  size_t o = 0;
-  for (size_t i = 0; i < n; ++i) {
-    if (o + sizes[i] > ring) o = 0;
-    off[i] = o;
-    wait_begin[i] = (int)wait_list.size();
-    for (size_t gr = o / granule; gr < (o + sizes[i]) / granule; ++gr) {
-      const int w = last_writer[gr];
-      if (w >= 0 && seen[w] != (int)i) {
-        seen[w] = (int)i;
-        wait_list.push_back(w);
-      }
-      last_writer[gr] = (int)i;
-    }
-    wait_count[i] = (int)wait_list.size() - wait_begin[i];
-    o += sizes[i];
-  }
-}
-
 GroupedPlan::~GroupedPlan() {
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -159,7 +132,7 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     int64_t g;             // index into probs
     int bn, nkc, parts, ra, rb, tiles;
     int64_t rowsA, rowsB;
-    size_t offA, offB, offA2, offB2, size;  // ring layout
+    size_t offA, offB, offA2, offB2, size;  // panel layout inside the problem's region
     double cost;           // per tile: k chunks x width x products
   };
   std::vector<SplitProb> sp;
@@ -199,45 +172,33 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   // that the cheap tiles come last and even out the CTAs' finishing times.
   std::stable_sort(sp.begin(), sp.end(), [](const SplitProb& a, const SplitProb& b) { return a.cost > b.cost; });
 
-  // ---- the panel ring ----
+  // ---- panels ----
   // Each problem's panels ([hi | lo] or [hi | mid] of op(A) and op(B), and
-  // with three parts the compact lo3 panels) take one contiguous region of a
-  // ring of ring_bytes, whole granules of kGranule bytes, allocated in
-  // packing order and wrapping to the start when the next region does not
-  // fit.  A problem may be packed once every problem that last wrote one of
-  // its granules has been read by the GEMM (its wait list).  When the whole
-  // batch fits, nothing waits.  A tile copy may run up to 32 KiB past its
-  // panel's end: into the next region, or into slack after the ring; those
-  // rows only feed outputs that are never stored.
-  constexpr size_t kGranule = 4096;
-  auto gran = [&](size_t x) { return (x + kGranule - 1) / kGranule * kGranule; };
-  size_t total = 0, largest = 0;
-  for (SplitProb& x : sp) {
-    const size_t a = gran((size_t)x.rowsA * x.nkc * 128), b = gran((size_t)x.rowsB * x.nkc * 128);
+  // with three parts the compact lo3 panels) take one contiguous region.  A
+  // tile copy may run up to 32 KiB past its panel's end: into the next
+  // region, or into slack after the last; those rows only feed outputs that
+  // are never stored.
+  auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t total = 0;
+  std::vector<size_t> prob_off(sp.size());
+  for (size_t i = 0; i < sp.size(); ++i) {
+    SplitProb& x = sp[i];
+    const size_t a = a256((size_t)x.rowsA * x.nkc * 128), b = a256((size_t)x.rowsB * x.nkc * 128);
     const int pairs = (x.nkc + 1) / 2;
-    const size_t a2 = x.parts == 2 ? gran((size_t)x.rowsA * pairs * 128) : 0;
-    const size_t b2 = x.parts == 2 ? gran((size_t)x.rowsB * pairs * 128) : 0;
+    const size_t a2 = x.parts == 2 ? a256((size_t)x.rowsA * pairs * 128) : 0;
+    const size_t b2 = x.parts == 2 ? a256((size_t)x.rowsB * pairs * 128) : 0;
     x.offA = 0; x.offB = a; x.offA2 = a + b; x.offB2 = a + b + a2;
     x.size = a + b + a2 + b2;
+    prob_off[i] = total;
     total += x.size;
-    largest = std::max(largest, x.size);
   }
-  size_t ring = P->ring_bytes > 0 ? gran(P->ring_bytes) : kGroupedRingBytes;
-  ring = std::max(ring, largest);
-  // packed ahead of the GEMM, every panel needs its own bytes
-  if (total <= ring || !P->fused) ring = total;
-  std::vector<size_t> sizes(sp.size());
-  for (size_t i = 0; i < sp.size(); ++i) sizes[i] = sp[i].size;
-  std::vector<int> wait_list, wait_begin, wait_count;
-  std::vector<size_t> ring_off;
-  ring_layout(sizes, ring, kGranule, ring_off, wait_begin, wait_count, wait_list);
 
   // ---- bands, packing tasks, tiles ----
   std::vector<PackBand> bands;
+  std::vector<int> band_prob, band_isa;  // host only: each band's problem and operand
   std::vector<int> task_band;
   std::vector<int4> split_items;
   std::vector<GroupDev> gdev(sp.size());
-  std::vector<int> need(sp.size());
   int64_t amax_words = 0, n_cnt = 0;
   for (size_t i = 0; i < sp.size(); ++i) {
     amax_words += probs[sp[i].g].m + probs[sp[i].g].n;
@@ -249,7 +210,6 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   auto take = [&](size_t bytes) { Region r{off, bytes}; off = align256(off + bytes); return r; };
   const Region ctl_r = take(kSplitCtlBytes);
   const Region cnt_r = take((size_t)n_cnt * 4);
-  const Region done_r = take(sp.size() * 4);
   const Region amax_r = take((size_t)amax_words * 4 + 4);
   const size_t head_bytes = off;
   int64_t cnt_base = 0, aw = 0;
@@ -259,12 +219,7 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     GroupDev& d = gdev[i];
     d.m = q.m; d.n = q.n; d.nkc = x.nkc; d.bn = x.bn; d.rowsA = x.rowsA; d.rowsB = x.rowsB;
     d.parts = x.parts;
-    d.ready = (x.nkc + kPackChunks - 1) / kPackChunks + 1;
     d.alpha = q.alpha; d.beta = q.beta; d.C = q.C; d.ldc = q.ldc;
-    d.bandA0 = (int)cnt_base;
-    d.bandB0 = (int)cnt_base + x.ra;
-    d.rbB = x.rb;
-    need[i] = x.tiles;
     // bands in the order of the first tile that reads them (tiles go column
     // of tiles by column of tiles): op(B)'s bands of tile column 0, every
     // band of op(A), the remaining bands of op(B)
@@ -283,12 +238,11 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
       b.kcontig = is_a ? (ta == 1) : (tb == 0);
       b.ngroups = ngroups;
       b.first_task = (int)task_band.size();
-      b.problem = (int)i;
-      b.wait_begin = wait_begin[i];
-      b.wait_count = wait_count[i];
       b.cnt = (int)cnt_base + (is_a ? 0 : x.ra) + j;
       for (int t = 0; t < ngroups; ++t) task_band.push_back((int)bands.size());
       bands.push_back(b);
+      band_prob.push_back((int)i);
+      band_isa.push_back(is_a ? 1 : 0);
     };
     for (int j = 0; j < nb0; ++j) add_band(false, j);
     for (int j = 0; j < x.ra; ++j) add_band(true, j);
@@ -318,12 +272,10 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   const Region sitems_r = take(split_items.size() * sizeof(int4) + 16);
   const Region bands_r = take(bands.size() * sizeof(PackBand) + 16);
   const Region tband_r = take(task_band.size() * 4 + 16);
-  const Region wait_r = take(wait_list.size() * 4 + 16);
-  const Region need_r = take(need.size() * 4 + 16);
   const Region sprob_r = take(sprobs.size() * sizeof(Problem) + 16);
   Region simt_items_r[24];
   for (int c = 0; c < 24; ++c) simt_items_r[c] = take(simt_items[c].size() * sizeof(int4) + 16);
-  const Region ring_r = take(sp.empty() ? 16 : ring + 32768);
+  const Region panels_r = take(sp.empty() ? 16 : total + 32768);
 
   if (off > 0 && cudaMalloc(&P->dmem, off) != cudaSuccess) {
     cudaGetLastError();
@@ -331,7 +283,6 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     return GBGEMM_ERR_ALLOC;
   }
   P->dbytes = off;
-  P->ring_used = sp.empty() ? 0 : ring;
   uint8_t* base = static_cast<uint8_t*>(P->dmem);
   // device addresses of the panels and maxima
   uint32_t* amax_base = reinterpret_cast<uint32_t*>(base + amax_r.off);
@@ -340,7 +291,7 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   for (size_t i = 0; i < sp.size(); ++i) {
     const SplitProb& x = sp[i];
     const gbgemm_problem& q = probs[x.g];
-    uint8_t* r0 = base + ring_r.off + ring_off[i];
+    uint8_t* r0 = base + panels_r.off + prob_off[i];
     pa[i] = r0 + x.offA;
     pb[i] = r0 + x.offB;
     pa2[i] = x.parts == 2 ? r0 + x.offA2 : nullptr;
@@ -354,9 +305,10 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     d.amaxB = amax_base + aw + q.m;
     aw += q.m + q.n;
   }
-  for (PackBand& b : bands) {
-    const int i = b.problem;
-    const bool is_a = b.cnt < gdev[i].bandB0;
+  for (size_t bi = 0; bi < bands.size(); ++bi) {
+    PackBand& b = bands[bi];
+    const int i = band_prob[bi];
+    const bool is_a = band_isa[bi] != 0;
     b.amax = const_cast<uint32_t*>(is_a ? gdev[i].amaxA : gdev[i].amaxB);
     b.panel = is_a ? pa[i] : pb[i];
     b.panel2 = is_a ? pa2[i] : pb2[i];
@@ -367,8 +319,8 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   bool ok = h2d(gdev_r, gdev.data(), gdev.size() * sizeof(GroupDev)) &&
             h2d(sitems_r, split_items.data(), split_items.size() * sizeof(int4)) &&
             h2d(bands_r, bands.data(), bands.size() * sizeof(PackBand)) &&
-            h2d(tband_r, task_band.data(), task_band.size() * 4) && h2d(wait_r, wait_list.data(), wait_list.size() * 4) &&
-            h2d(need_r, need.data(), need.size() * 4) && h2d(sprob_r, sprobs.data(), sprobs.size() * sizeof(Problem));
+            h2d(tband_r, task_band.data(), task_band.size() * 4) &&
+            h2d(sprob_r, sprobs.data(), sprobs.size() * sizeof(Problem));
   for (int c = 0; c < 24; ++c) ok = ok && h2d(simt_items_r[c], simt_items[c].data(), simt_items[c].size() * sizeof(int4));
   if (!ok) return GBGEMM_ERR_CUDA;
   P->n_split = (int64_t)sp.size();
@@ -381,13 +333,8 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
   bool narrow = true;
   for (const GroupDev& gd : gdev) narrow = narrow && gd.bn <= kNarrowBN;
   if (!gdev.empty()) {
-    cudaError_t ea;
-    if (P->fused)
-      ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowStages, kNarrowBN, kNarrowPackStages>()
-                  : ensure_gemm_smem_attr<GroupedSched>();
-    else
-      ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowPrepackStages, kNarrowBN, 0>()
-                  : ensure_gemm_smem_attr<GroupedSched, kStages, kMaxBN, 0>();
+    const cudaError_t ea = narrow ? ensure_gemm_smem_attr<GroupedSched, kNarrowStages, kNarrowBN>()
+                                  : ensure_gemm_smem_attr<GroupedSched>();
     if (ea != cudaSuccess) return GBGEMM_ERR_CUDA;
   }
   // Graph: the SIMT launches run on side branches, concurrently with the
@@ -441,38 +388,23 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
     GroupedSched S;
     S.ctl = reinterpret_cast<WorkCtl*>(base + ctl_r.off);
     S.band_cnt = reinterpret_cast<int*>(base + cnt_r.off);
-    S.done = reinterpret_cast<int*>(base + done_r.off);
     S.items = reinterpret_cast<const int4*>(base + sitems_r.off);
     S.groups = reinterpret_cast<const GroupDev*>(base + gdev_r.off);
     S.bands = reinterpret_cast<const PackBand*>(base + bands_r.off);
     S.task_band = reinterpret_cast<const int*>(base + tband_r.off);
-    S.wait_list = reinterpret_cast<const int*>(base + wait_r.off);
-    S.need = reinterpret_cast<const int*>(base + need_r.off);
     S.n_items = (int)split_items.size();
     S.n_tasks = (int)task_band.size();
-    if (e == cudaSuccess && P->fused) {
-      const int grid = (int)std::min<int64_t>(
-          std::max<int64_t>((int64_t)split_items.size(), (int64_t)task_band.size()), P->num_sms);
-      if (narrow)
-        split_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN, kNarrowPackStages>
-            <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowStages, kNarrowBN, kNarrowPackStages>(), capture_stream>>>(
-                S, P->status, kTimeoutNs);
-      else
-        split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status,
-                                                                                              kTimeoutNs);
-      P->kernels_per_run += 2;  // the memset and the kernel
-    } else if (e == cudaSuccess) {
-      // every packing task as its own CTA, then the GEMM without packer warps
+    if (e == cudaSuccess) {
+      // every packing task as its own CTA, then the GEMM
       pack_tasks_kernel<GroupedSched><<<(unsigned)task_band.size(), 256, 0, capture_stream>>>(S);
       const int grid = (int)std::min<int64_t>((int64_t)split_items.size(), P->num_sms);
       if (narrow)
-        split_gemm_kernel<GroupedSched, kNarrowPrepackStages, kNarrowBN, 0>
-            <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowPrepackStages, kNarrowBN, 0>(), capture_stream>>>(
-                S, P->status, kTimeoutNs);
+        split_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN>
+            <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowStages, kNarrowBN>(), capture_stream>>>(S, P->status,
+                                                                                                 kTimeoutNs);
       else
-        split_gemm_kernel<GroupedSched, kStages, kMaxBN, 0>
-            <<<grid, kGemmThreads, gemm_smem_bytes<kStages, kMaxBN, 0>(), capture_stream>>>(S, P->status,
-                                                                                           kTimeoutNs);
+        split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status,
+                                                                                              kTimeoutNs);
       P->kernels_per_run += 3;  // the memset, the packing and the GEMM
     }
   }
@@ -499,30 +431,3 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
 }
 
 }  // namespace gbg
-
-extern "C" int gbgemm_grouped_ring_layout(const uint64_t* sizes, int64_t count, uint64_t ring_bytes,
-                                          uint64_t granule, uint64_t* offsets, int32_t* wait_begin,
-                                          int32_t* wait_count, int32_t* wait_list, int64_t wait_capacity,
-                                          int64_t* wait_total) {
-  if (count < 0 || (count > 0 && (!sizes || !offsets || !wait_begin || !wait_count)) || !wait_total ||
-      granule == 0 || wait_capacity < 0 || (wait_capacity > 0 && !wait_list))
-    return GBGEMM_ERR_INVALID_VALUE;
-  std::vector<size_t> sz((size_t)count);
-  for (int64_t i = 0; i < count; ++i) {
-    if (sizes[i] == 0 || sizes[i] % granule != 0 || sizes[i] > ring_bytes) return GBGEMM_ERR_INVALID_VALUE;
-    sz[(size_t)i] = (size_t)sizes[i];
-  }
-  if (ring_bytes % granule != 0) return GBGEMM_ERR_INVALID_VALUE;
-  std::vector<size_t> off;
-  std::vector<int> wb, wc, wl;
-  gbg::ring_layout(sz, (size_t)ring_bytes, (size_t)granule, off, wb, wc, wl);
-  for (int64_t i = 0; i < count; ++i) {
-    offsets[i] = off[(size_t)i];
-    wait_begin[i] = wb[(size_t)i];
-    wait_count[i] = wc[(size_t)i];
-  }
-  *wait_total = (int64_t)wl.size();
-  if ((int64_t)wl.size() > wait_capacity) return GBGEMM_ERR_INVALID_VALUE;
-  for (size_t i = 0; i < wl.size(); ++i) wait_list[i] = wl[i];
-  return GBGEMM_OK;
-}

@@ -110,7 +110,7 @@ struct SplitLayout {
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t k, int64_t batch, int splitk, int bn);
 
-// One split-path call: packing fused into the persistent tcgen05 GEMM.
+// One split-path call: the packing launch, then the persistent tcgen05 GEMM.
 struct SplitCall {
   int ta = 0, tb = 0;
   int64_t m = 0, n = 0, k = 0;
@@ -125,16 +125,14 @@ struct SplitCall {
   void* ws = nullptr;    // split_layout(...).total bytes
   int* status = nullptr;
   int num_sms = 0;
-  // packing inside the GEMM kernel (its packer warps) or by a separate
-  // launch ahead of it
-  bool fused = true;
   // panel inspection: pack op(A)'s rows only, into these caller buffers
   bool pack_only = false;
   void* panel_out = nullptr;
   void* panel2_out = nullptr;
   uint32_t* amax_out = nullptr;
 };
-// Zero the workspace head, run the fused kernel (and the split-K reduction).
+// Zero the workspace head, pack both operands, run the GEMM (and the split-K
+// reduction).
 cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s);
 
 struct SplitGemmArgs {

@@ -188,23 +188,14 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   }
   const int64_t items = tm * tn * c.batch * splitk;
   const int64_t sms = c.num_sms > 0 ? c.num_sms : 148;
-  if (c.fused) {
-    e = ensure_gemm_smem_attr<SingleSched>();
-    if (e != cudaSuccess) return e;
-    const int64_t want = items > tasks ? items : tasks;
-    const int grid = (int)(want < sms ? (want > 0 ? want : 1) : sms);
-    split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, c.status, kTimeoutNs);
-  } else {
-    // packing tasks first, each its own CTA, then the GEMM without packer warps
-    if (tasks > 0) pack_tasks_kernel<SingleSched><<<(unsigned)tasks, 256, 0, s>>>(S);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || items == 0) return e;
-    e = ensure_gemm_smem_attr<SingleSched, kStages, kMaxBN, 0>();
-    if (e != cudaSuccess) return e;
-    const int grid = (int)(items < sms ? items : sms);
-    split_gemm_kernel<SingleSched, kStages, kMaxBN, 0>
-        <<<grid, kGemmThreads, gemm_smem_bytes<kStages, kMaxBN, 0>(), s>>>(S, c.status, kTimeoutNs);
-  }
+  // packing tasks first, each its own CTA, then the GEMM
+  if (tasks > 0) pack_tasks_kernel<SingleSched><<<(unsigned)tasks, 256, 0, s>>>(S);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || items == 0) return e;
+  e = ensure_gemm_smem_attr<SingleSched>();
+  if (e != cudaSuccess) return e;
+  const int grid = (int)(items < sms ? items : sms);
+  split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, c.status, kTimeoutNs);
   e = cudaGetLastError();
   if (e != cudaSuccess || splitk == 1 || c.pack_only) return e;
   SplitGemmArgs a;

@@ -220,56 +220,9 @@ __device__ __noinline__ bool mbar_wait_hint(uint32_t bar, uint32_t parity, volat
   }
 }
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Orders this thread's generic-proxy accesses of global memory against
-// async-proxy ones (bulk copies) on either side of it.
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-// Wait until *p >= target (acquire).  Gives up (returns false) once
-// `timeout_ns` has passed or another role raised the abort flag.
-__device__ __noinline__ bool wait_counter(const int* p, int target, volatile int* abort_flag, uint64_t timeout_ns) {
-  if (ld_acquire(p) >= target) return true;
-  const uint64_t t0 = globaltimer();
-  for (uint32_t it = 1;; ++it) {
-    __nanosleep(100);
-    if (ld_acquire(p) >= target) return true;
-    if ((it & 7u) == 0u) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > timeout_ns) return false;
-    }
-  }
-}
-
 // Ask L2 for the 128-byte line holding `p`.
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// Asynchronous copies into shared memory that hold no registers while in
-// flight: 16 bytes (16-byte aligned source) or 4 bytes; bytes past
-// `src_bytes` are filled with zeros (src_bytes 0: nothing is read).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Wait until at most `pending` of this thread's committed groups are still in flight.
-__device__ __forceinline__ void cp_async_wait(int pending) {
-  switch (pending) {
-    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-  }
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -347,48 +300,26 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // With a second panel the three-part split is written ([hi | mid] into the
 // panel, lo3 into the compact panel2: block kc / 2, half kc % 2).
 
-// Named barrier `id` of `n` threads: one packing team inside the GEMM CTA.
-struct TeamBar {
-  int id, n;
-  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-  __device__ __forceinline__ bool any(bool p) const {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred a, b;\n\t"
-        "setp.ne.u32 a, %1, 0;\n\t"
-        "bar.red.or.pred b, %2, %3, a;\n\t"
-        "selp.u32 %0, 1, 0, b;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)p), "r"(id), "r"(n)
-        : "memory");
-    return r != 0u;
-  }
-};
-
 // Re-pack the badly scaled K-vectors of one 128-row block over all k chunks
-// with x' = x * 2^-e, by a team of TS threads.  A block without such rows
+// with x' = x * 2^-e (one CTA of 256 threads).  A block without such rows
 // returns at once.  The maxima are read through L2 (they were built by
 // atomics of other CTAs).  se: 128 ints of shared memory.
-template <int TS>
 __device__ __forceinline__ void rescale_block(int64_t rows, int64_t k, const float* __restrict__ X, int64_t ld,
                                               bool kcontig, const uint32_t* __restrict__ amax,
                                               uint8_t* __restrict__ panel, uint8_t* __restrict__ panel2,
-                                              int64_t rows_alloc, int64_t nkc, int64_t rb, int* se, int tid,
-                                              TeamBar bar) {
+                                              int64_t rows_alloc, int64_t nkc, int64_t rb, int* se) {
   const int64_t r0 = rb * 128;
-  bool any = false;
-  for (int r = tid; r < 128; r += TS) {
-    const int e = (r0 + r < rows) ? scale_exp_from_bits(__ldcg(&amax[r0 + r])) : 0;
-    se[r] = e;
-    any = any || e != 0;
-  }
-  if (!bar.any(any)) return;
+  const int tid = threadIdx.x;
+  int e = 0;
+  if (tid < 128 && r0 + tid < rows) e = scale_exp_from_bits(__ldcg(&amax[r0 + tid]));
+  if (tid < 128) se[tid] = e;
+  if (!__syncthreads_or(e != 0)) return;
   for (int64_t kc = 0; kc < nkc; ++kc) {
     const size_t boff = ((size_t)kc * rows_alloc + r0) * 128;
     const size_t boff2 = ((size_t)(kc >> 1) * rows_alloc + r0) * 128;
     uint8_t* blk = panel + boff;
-    for (int idx = tid; idx < 512; idx += TS) {
-      const int rr = idx >> 2, cc = idx & 3;
+    for (int it = 0; it < 2; ++it) {
+      const int idx = tid + 256 * it, rr = idx >> 2, cc = idx & 3;
       const int er = se[rr];
       if (er == 0 || r0 + rr >= rows_alloc) continue;
       const int64_t r = r0 + rr, p = kc * 32 + cc * 8;

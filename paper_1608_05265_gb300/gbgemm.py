@@ -42,10 +42,6 @@ CFG_SPLIT_BN128 = 4
 CFG_SPLIT_BN256 = 5
 NUM_CONFIGS = 6
 
-PACKING_AUTO = 0
-PACKING_SEPARATE = 1
-PACKING_FUSED = 2
-
 CONFIG_PREDICTED = 0
 CONFIG_TUNED = 1
 CONFIG_DEFAULT = 2
@@ -65,12 +61,11 @@ EXPORTS = [
     "gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path", "gbgemm_last_path",
     "gbgemm_reserve_workspace", "gbgemm_split_workspace_bytes", "gbgemm_sgemm", "gbgemm_sgemm_strided_batched",
     "gbgemm_sgemv", "gbgemm_sgetrf", "gbgemm_sgetrs",
-    "gbgemm_get_device_status", "gbgemm_debug_expire_wait", "gbgemm_set_packing",
+    "gbgemm_get_device_status", "gbgemm_debug_expire_wait",
     "gbgemm_status_string", "gbgemm_panel_bytes", "gbgemm_split_pack", "gbgemm_profile_begin",
     "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
     "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run", "gbgemm_grouped_plan_configs",
-    "gbgemm_grouped_plan_stats", "gbgemm_grouped_plan_destroy", "gbgemm_set_grouped_ring_bytes",
-    "gbgemm_grouped_ring_layout", "gbgemm_autotune", "gbgemm_tuning_save",
+    "gbgemm_grouped_plan_stats", "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
     "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
     "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
     "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error",
@@ -84,31 +79,6 @@ class GbgemmError(RuntimeError):
     def __init__(self, fn: str, status: int):
         super().__init__(f"{fn} returned {status} ({status_string(status)})")
         self.status = status
-
-
-def grouped_ring_layout(sizes, ring_bytes: int, granule: int):
-    """(offsets, wait lists) of gbgemm_grouped_ring_layout (host only, no GPU)."""
-    import numpy as np
-    sz = np.ascontiguousarray(sizes, dtype=np.uint64)
-    n = sz.size
-    off = np.zeros(max(n, 1), dtype=np.uint64)
-    wb = np.zeros(max(n, 1), dtype=np.int32)
-    wc = np.zeros(max(n, 1), dtype=np.int32)
-    total = ctypes.c_int64(0)
-    cap = 4 * n + 16
-    while True:
-        wl = np.zeros(cap, dtype=np.int32)
-        rc = lib().gbgemm_grouped_ring_layout(sz.ctypes.data, n, int(ring_bytes), int(granule), off.ctypes.data,
-                                              wb.ctypes.data, wc.ctypes.data, wl.ctypes.data, cap,
-                                              ctypes.byref(total))
-        if rc == OK:
-            break
-        if total.value > cap:
-            cap = total.value
-            continue
-        raise GbgemmError("gbgemm_grouped_ring_layout", rc)
-    waits = [wl[wb[i]:wb[i] + wc[i]].tolist() for i in range(n)]
-    return off[:n].astype(np.int64).tolist(), waits
 
 
 def lib():
@@ -136,10 +106,6 @@ def lib():
             L.gbgemm_sgetrs.argtypes = [vp, i64, i64, vp, i64, vp, vp, i64]
             L.gbgemm_get_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.gbgemm_debug_expire_wait.argtypes = [vp, ctypes.c_uint64]
-            L.gbgemm_set_grouped_ring_bytes.argtypes = [vp, ctypes.c_size_t]
-            L.gbgemm_set_packing.argtypes = [vp, ctypes.c_int]
-            L.gbgemm_grouped_ring_layout.argtypes = [vp, i64, ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp, i64,
-                                                     ctypes.POINTER(i64)]
             L.gbgemm_status_string.argtypes = [ctypes.c_int]
             L.gbgemm_status_string.restype = ctypes.c_char_p
             L.gbgemm_panel_bytes.argtypes = [i64, i64]
@@ -180,13 +146,12 @@ def lib():
             for name in ("gbgemm_create", "gbgemm_destroy", "gbgemm_set_stream", "gbgemm_set_path",
                          "gbgemm_last_path", "gbgemm_reserve_workspace", "gbgemm_sgemm",
                          "gbgemm_sgemm_strided_batched", "gbgemm_sgemv", "gbgemm_sgetrf", "gbgemm_sgetrs",
-                         "gbgemm_get_device_status", "gbgemm_debug_expire_wait", "gbgemm_set_packing", "gbgemm_split_pack",
+                         "gbgemm_get_device_status", "gbgemm_debug_expire_wait", "gbgemm_split_pack",
                          "gbgemm_profile_begin",
                          "gbgemm_profile_end", "gbgemm_sgemm_split_noalloc", "gbgemm_grouped_plan_create",
                          "gbgemm_grouped_plan_create_with_configs", "gbgemm_grouped_plan_run",
                          "gbgemm_grouped_plan_configs", "gbgemm_grouped_plan_stats",
-                         "gbgemm_grouped_plan_destroy", "gbgemm_set_grouped_ring_bytes",
-                         "gbgemm_grouped_ring_layout", "gbgemm_set_packing", "gbgemm_autotune", "gbgemm_tuning_save",
+                         "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
                          "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
                          "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
                          "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error"):
@@ -306,12 +271,6 @@ class Handle:
         v = ctypes.c_int()
         _check("gbgemm_get_device_status", lib().gbgemm_get_device_status(self._h, ctypes.byref(v)))
         return v.value
-
-    def set_packing(self, mode: int):
-        _check("gbgemm_set_packing", lib().gbgemm_set_packing(self._h, int(mode)))
-
-    def set_grouped_ring_bytes(self, nbytes: int):
-        _check("gbgemm_set_grouped_ring_bytes", lib().gbgemm_set_grouped_ring_bytes(self._h, int(nbytes)))
 
     def debug_expire_wait(self, timeout_ns: int):
         """Queue a bounded wait that nothing completes (failure-detection test)."""

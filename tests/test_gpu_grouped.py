@@ -161,31 +161,6 @@ def test_grouped_bad_plans(h):
     assert rc == gbgemm.ERR_BAD_PLAN and bad == 0
 
 
-@pytest.mark.parametrize("ring", [0, 1 << 20])
-def test_grouped_fused_packing_ring(h, ring):
-    """Packing inside the GEMM kernel with its panel ring: the default ring,
-    and a 1 MiB ring that forces many wraps (problems packed only once the
-    problems whose ring bytes they reuse have been read)."""
-    import torch
-    from paper_1608_05265_gb300 import gbgemm
-    specs = random_specs(37, 300, 16, 700, alphas=(1.0, -1.5), betas=(0.0, 0.5))
-    b = Batch(specs, 37)
-    h.set_packing(gbgemm.PACKING_FUSED)
-    h.set_grouped_ring_bytes(ring)
-    try:
-        plan = run_plan(h, b)
-        b.check(nthreads=4)
-        b.reset_c()
-        plan.run(torch.cuda.current_stream())  # a replay reuses the ring from the start
-        torch.cuda.synchronize()
-        assert h.get_device_status() == 0
-        b.check(nthreads=4)
-        plan.close()
-    finally:
-        h.set_packing(gbgemm.PACKING_AUTO)
-        h.set_grouped_ring_bytes(0)
-
-
 def test_grouped_uneven_batch_4096(h):
     """The uneven batch: 4096 problems, m, n, k log-uniform in [16, 1024], random
     transposes, tight leading dimensions, uniform data, alpha 1, beta 0 (seed 3);

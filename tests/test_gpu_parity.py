@@ -255,16 +255,14 @@ def unpack_compact_lo3(panel2: np.ndarray, rows: int, k: int):
     return both.transpose(1, 2, 0, 3).reshape(RB * 128, KC * 32)
 
 
-@pytest.mark.parametrize("packing", [1, 2], ids=["separate", "fused"])
 @pytest.mark.parametrize("which,trans", [("A", "N"), ("A", "T"), ("B", "N"), ("B", "T")])
 @pytest.mark.parametrize("rows,k", [(1, 1), (130, 37), (300, 300), (257, 1000), (200, 600), (70, 160), (90, 480)])
-def test_split_pack_bit_exact(h, which, trans, rows, k, packing):
-    """The panels and row maxima of both packers (the separate packing launch
-    and the GEMM kernel's packer warps) equal the oracle's split bit for bit,
-    rows scaled by 2^-60 .. 2^60 so that the re-pack of badly scaled rows runs."""
+def test_split_pack_bit_exact(h, which, trans, rows, k):
+    """The packing launch's panels and row maxima equal the oracle's split bit
+    for bit, rows scaled by 2^-60 .. 2^60 so that the re-pack of badly scaled
+    rows runs."""
     import torch
     from paper_1608_05265_gb300 import gbgemm
-    h.set_packing(packing)
     kcontig = (which == "A") == (trans == "T")
     sr, sc = (k, rows) if kcontig else (rows, k)   # stored shape of X
     ld = sr + 3
@@ -291,22 +289,15 @@ def test_split_pack_bit_exact(h, which, trans, rows, k, packing):
     vec = L.T if kcontig else L
     want = np.abs(vec).max(axis=1).astype(np.float32).view(np.uint32)
     assert np.array_equal(am, want)
-    h.set_packing(0)
 
 
-@pytest.mark.parametrize("packing", [1, 2], ids=["separate", "fused"])
 @pytest.mark.parametrize("ta,tb", TRANS)
 @pytest.mark.parametrize("m,n,k,pad", [(1000, 777, 555, 3), (129, 2000, 300, 1), (300, 260, 64, 0), (257, 513, 129, 5)])
-def test_both_packings_against_oracle(h, packing, ta, tb, m, n, k, pad):
-    """Both places the split path packs its operands give results within the
-    bound, two-part and three-part splits, odd leading dimensions (unaligned
-    rows and columns)."""
-    h.set_packing(packing)
+def test_odd_leading_dimensions(h, ta, tb, m, n, k, pad):
+    """Two-part and three-part splits with odd leading dimensions (rows and
+    columns that are not 16-byte aligned) stay within the bound."""
     A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 17, ta, tb, m, n, k, pad=pad)
-    try:
-        check_full(h, SPLIT, ta, tb, m, n, k, 1.5, A, lda, B, ldb, -0.25, C, ldc, nthreads=4)
-    finally:
-        h.set_packing(0)
+    check_full(h, SPLIT, ta, tb, m, n, k, 1.5, A, lda, B, ldb, -0.25, C, ldc, nthreads=4)
 
 
 @pytest.mark.parametrize("path", [SIMT, SPLIT])
@@ -326,15 +317,3 @@ def test_auto_path_choice(h):
         check_full(h, gbgemm.PATH_AUTO, "N", "N", m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc)
         assert h.last_path() == want
 
-
-def test_packings_give_identical_bits(h):
-    """The two packers write the same panels and the GEMM does the same
-    arithmetic, so the results agree bit for bit (single call and batch)."""
-    from paper_1608_05265_gb300 import gbgemm
-    outs = []
-    for packing in (gbgemm.PACKING_SEPARATE, gbgemm.PACKING_FUSED):
-        h.set_packing(packing)
-        A, lda, B, ldb, C, ldc = synth.gemm_problem("normal_rowscaled", 19, "T", "N", 700, 650, 900, pad=1)
-        outs.append(run_sgemm(h, SPLIT, "T", "N", 700, 650, 900, -1.0, A, lda, B, ldb, 1.0, C, ldc))
-    h.set_packing(gbgemm.PACKING_AUTO)
-    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
