@@ -35,9 +35,9 @@
 //                   column-major C with one 128-byte store per warp and
 //                   column (Section III-D: each core owns whole column
 //                   blocks of the result so that stores stay contiguous);
-//   warp 18         with beta != 0, asks L2 for each tile's C columns as soon
-//                   as the tile is handed out, so that the epilogue's reads
-//                   of C find them there.
+//   warp 18         with beta != 0 and k <= 512, asks L2 for each tile's C
+//                   columns as soon as the tile is handed out, so that the
+//                   epilogue's reads of C find them there.
 // Every wait is bounded: on expiry the kernel records GBGEMM_ERR_DEVICE_TIMEOUT,
 // raises a CTA-wide abort flag, drains its own copies and MMAs, frees TMEM
 // and returns.  Waiting threads sleep (mbarrier try_wait with a suspend
@@ -73,6 +73,14 @@ constexpr uint64_t kDrainTimeoutNs = 4000000000ull;
 template <int STAGES, int MAXBN>
 constexpr int gemm_smem_bytes() { return STAGES * (kBlockBytes + MAXBN * 128) + 1024 + 256; }
 constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN>();
+
+// The dependent launch of a kernel started with programmatic stream
+// serialisation may begin before this grid finishes; it waits (below) for
+// the grid's completion before it reads what the grid wrote.
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Wait until the grid this one depends on has completed and its memory is
+// visible (returns at once without such a dependency).
+__device__ __forceinline__ void wait_prerequisite_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Per-launch control words; zeroed before every launch together with the
 // band counters and the row maxima.
@@ -391,6 +399,7 @@ template <class Sched>
 __global__ void __launch_bounds__(256) pack_tasks_kernel(const Sched S) {
   __shared__ uint32_t smax[128];
   __shared__ int finisher;
+  launch_dependents();  // the GEMM may launch and set up while the packing runs
   const PackJob P = S.pack_job((int)blockIdx.x);
   if (P.kcontig) pack_task_regs<true>(P, smax);
   else pack_task_regs<false>(P, smax);
@@ -460,6 +469,10 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  // everything above overlaps the packing launch; the panels and maxima it
+  // writes are read only from here on
+  wait_prerequisite_grid();
+  launch_dependents();
 
   if (warp == 0) {
     // ---------------- producer ----------------
@@ -701,7 +714,11 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
       if (!ok || t < 0) break;
       const TileJob J = S.job(t);
-      if (J.beta == 0.f || J.partial) continue;
+      // Only short tiles (k <= 512), whose epilogue rather than their MMAs
+      // sets the pace, are prefetched: for long ones the C reads overlap the
+      // next tile's MMAs anyway, and prefetching several 128 KB tiles ahead
+      // would push the operand panels out of L2.
+      if (J.beta == 0.f || J.partial || J.nkc > 16) continue;
       const int64_t rows = (J.m - J.m0 < 128) ? J.m - J.m0 : 128;
       const int64_t ncols = (J.n - J.n0 < J.bn) ? J.n - J.n0 : J.bn;
       const float* c0 = J.C + J.m0 + J.n0 * J.ldc;
@@ -736,6 +753,26 @@ cudaError_t ensure_gemm_smem_attr() {
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   return cudaSuccess;
+}
+
+// Launch the GEMM on stream s; with `dependent` it may start while the
+// kernel before it on the stream (the packing launch) still runs, and waits
+// for that kernel's results after setting itself up.
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
+cudaError_t launch_gemm_kernel(const Sched& S, int grid, int* status, cudaStream_t s, bool dependent) {
+  cudaError_t e = ensure_gemm_smem_attr<Sched, STAGES, MAXBN>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kGemmThreads);
+  cfg.dynamicSmemBytes = gemm_smem_bytes<STAGES, MAXBN>();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<Sched, STAGES, MAXBN>, S, status, (uint64_t)kTimeoutNs);
 }
 
 }  // namespace

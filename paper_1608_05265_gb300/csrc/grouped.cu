@@ -398,13 +398,10 @@ int build_grouped_plan(GroupedPlan* P, const gbgemm_problem* probs, int64_t coun
       // every packing task as its own CTA, then the GEMM
       pack_tasks_kernel<GroupedSched><<<(unsigned)task_band.size(), 256, 0, capture_stream>>>(S);
       const int grid = (int)std::min<int64_t>((int64_t)split_items.size(), P->num_sms);
-      if (narrow)
-        split_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN>
-            <<<grid, kGemmThreads, gemm_smem_bytes<kNarrowStages, kNarrowBN>(), capture_stream>>>(S, P->status,
-                                                                                                 kTimeoutNs);
-      else
-        split_gemm_kernel<GroupedSched><<<grid, kGemmThreads, kGemmSmemBytes, capture_stream>>>(S, P->status,
-                                                                                              kTimeoutNs);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = narrow ? launch_gemm_kernel<GroupedSched, kNarrowStages, kNarrowBN>(S, grid, P->status, capture_stream, true)
+                   : launch_gemm_kernel<GroupedSched>(S, grid, P->status, capture_stream, true);
       P->kernels_per_run += 3;  // the memset, the packing and the GEMM
     }
   }

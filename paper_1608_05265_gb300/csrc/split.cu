@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t m, int64_t n
                                                             const uint32_t* __restrict__ amaxA,
                                                             const uint32_t* __restrict__ amaxB, float alpha,
                                                             float beta, float* __restrict__ C, int64_t ldc) {
+  wait_prerequisite_grid();  // launched as a dependent of the GEMM
   const int64_t total = m * n;
   const size_t tile_elems = (size_t)128 * bn, slice_elems = (size_t)tiles_m * tiles_n * tile_elems;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -192,10 +193,9 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   if (tasks > 0) pack_tasks_kernel<SingleSched><<<(unsigned)tasks, 256, 0, s>>>(S);
   e = cudaGetLastError();
   if (e != cudaSuccess || items == 0) return e;
-  e = ensure_gemm_smem_attr<SingleSched>();
-  if (e != cudaSuccess) return e;
   const int grid = (int)(items < sms ? items : sms);
-  split_gemm_kernel<SingleSched><<<grid, kGemmThreads, kGemmSmemBytes, s>>>(S, c.status, kTimeoutNs);
+  e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, tasks > 0);
+  if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e != cudaSuccess || splitk == 1 || c.pack_only) return e;
   SplitGemmArgs a;
@@ -212,9 +212,17 @@ cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s) {
   int64_t blocks = (total + 255) / 256;
   const int64_t cap = (int64_t)(a.num_sms > 0 ? a.num_sms : 148) * 8;
   if (blocks > cap) blocks = cap;
-  splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.m, a.n, a.bn, tm, tn, a.splitk, a.partial, a.amaxA,
-                                                         a.amaxB, a.alpha, a.beta, a.C, a.ldc);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, splitk_reduce_kernel, a.m, a.n, a.bn, tm, tn, a.splitk, (const float*)a.partial,
+                            a.amaxA, a.amaxB, a.alpha, a.beta, a.C, a.ldc);
 }
 
 }  // namespace gbg
