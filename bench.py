@@ -568,7 +568,7 @@ def run_extras(h, stream, flop8192):
         "ms_median": med_k, "tflops": flk / (med_k * 1e-3) / 1e12, "tflops_best": flk / (min_k * 1e-3) / 1e12,
         "kernels_per_call": launches_k, "max_error_ratio": errk,
         "note": ("split path; the k range is cut into slices so that the 4-16 output tiles fill the SMs, "
-                 "and a reduction sums the slices in order (kernels_per_call 6 = 2 packing, 2 re-packing, "
+                 "and a reduction sums the slices in order (kernels_per_call 3 = packing of both operands, "
                  "GEMM, reduction); error ratio over the whole 512 x 512 result (FP64 on the GPU)")}
     del As_, Bs_, Cs_
     # -- sgemv (Level 2, HBM-bound): A 32768 x 32768 (4.3 GB), both transposes --

@@ -96,8 +96,10 @@ int gbgemm_destroy(gbgemm_handle* h);
 /* Set the cudaStream_t (passed as void*) that later calls queue work on. */
 int gbgemm_set_stream(gbgemm_handle* h, void* cuda_stream);
 
-/* Force a path (gbgemm_path).  SPLIT_BF16 forced with k < 128 still runs but
- * the error bound is then not guaranteed.  Bad code: GBGEMM_ERR_INVALID_VALUE. */
+/* Force a path (gbgemm_path).  SPLIT_BF16 forced with 16 <= k < 128 holds the
+ * error bound (AUTO leaves those sizes to SIMT only because they are faster
+ * there); with k < 16 it still runs but the bound is then not guaranteed.
+ * Bad code: GBGEMM_ERR_INVALID_VALUE. */
 int gbgemm_set_path(gbgemm_handle* h, int path);
 
 /* Path taken by the handle's most recent gbgemm_sgemm (0 when it returned
@@ -243,7 +245,10 @@ int gbgemm_debug_expire_wait(gbgemm_handle* h, uint64_t timeout_ns);
 
 /* Profiling (benchmark use).  Between begin and end the handle records a
  * pair of CUDA events on its stream around every launch of the split-path
- * GEMM kernel, and counts every kernel the library launches.
+ * GEMM kernel, and counts every kernel the library launches.  While it
+ * profiles, the GEMM is launched after the packing completes (not as a
+ * programmatic dependent that may start early), so each pair brackets the
+ * GEMM kernel alone.
  * gbgemm_profile_end synchronises the stream and returns the summed GEMM
  * kernel time in milliseconds, the number of GEMM launches and the number
  * of kernels launched by the library (memsets not included).  Any output
@@ -281,7 +286,9 @@ const char* gbgemm_status_string(int status);
  *
  *   GBGEMM_CFG_SIMT_128x128, _64x64, _128x64   FP32 SIMT path, CTA tile shape
  *   GBGEMM_CFG_SPLIT_BN64, _BN128, _BN256      split-BF16 tensor path, 128 x BN
- *                                              tiles (needs k >= 128, alpha != 0)
+ *                                              tiles (needs k >= 16, alpha != 0:
+ *                                              below k = 16 the three-part split
+ *                                              can miss the error bound)
  *
  * Plan creation checks every problem (in problem order; *bad_index = the
  * first bad problem and the return value is GBGEMM_ERR_BAD_PLAN), chooses the
@@ -316,8 +323,10 @@ typedef enum {
 } gbgemm_config;
 
 /* Every source keeps the default rule's path for a problem (split from
- * k = 128, SIMT below); the tuner and the predictor choose the tile shape
- * within that path. */
+ * k = 16 with alpha != 0, SIMT otherwise); the tuner and the predictor choose
+ * the tile shape within that path.  A grouped plan runs many problems in one
+ * launch, so the launch overhead that keeps the single call on SIMT below
+ * k = 128 does not apply. */
 typedef enum {
   GBGEMM_CONFIG_PREDICTED = 0,  /* learned predictor, tuner as fallback */
   GBGEMM_CONFIG_TUNED = 1,      /* exhaustive autotuner (timed on the GPU) */

@@ -84,16 +84,22 @@ int ensure_workspace(gbgemm_handle* h, size_t bytes) {
 
 bool split_supported(const gbgemm_handle* h) { return h->cc_major == 10 && h->cc_minor == 3; }
 
-// Record the next profiling event on the handle's stream (no-op when not profiling).
-cudaError_t prof_record(gbgemm_handle* h) {
+// The next pair of profiling events (both null when not profiling); the
+// split launch records them again around its GEMM launch.
+cudaError_t prof_pair(gbgemm_handle* h, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
   if (!h->profiling) return cudaSuccess;
-  if (h->ev_used == h->ev_pool.size()) {
+  while (h->ev_used + 2 > h->ev_pool.size()) {
     cudaEvent_t e;
     cudaError_t err = cudaEventCreate(&e);
     if (err != cudaSuccess) return err;
     h->ev_pool.push_back(e);
   }
-  return cudaEventRecord(h->ev_pool[h->ev_used++], h->stream);
+  *e0 = h->ev_pool[h->ev_used++];
+  *e1 = h->ev_pool[h->ev_used++];
+  // recorded once here so that a call that launches no GEMM counts 0 ms
+  cudaError_t err = cudaEventRecord(*e0, h->stream);
+  return err != cudaSuccess ? err : cudaEventRecord(*e1, h->stream);
 }
 
 }  // namespace
@@ -259,9 +265,8 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   c.bn = split_bn; c.raster = 16; c.splitk = splitk;
   c.ws = h->ws; c.status = h->d_status; c.num_sms = h->num_sms;
   h->kernel_launches += 1;  // the packing launch (the memset of the workspace head is not a kernel of ours)
-  if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  if (prof_pair(h, &c.gemm_begin, &c.gemm_end) != cudaSuccess) return GBGEMM_ERR_CUDA;
   if (gbg::launch_split_call(c, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
-  if (prof_record(h) != cudaSuccess) return GBGEMM_ERR_CUDA;
   h->kernel_launches += splitk > 1 ? 2 : 1;
   h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;

@@ -678,15 +678,36 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         const int eb_l = (lane < EC && jl < J.n) ? scale_exp_from_bits(__ldcg(J.amaxB + jl)) : 0;
         uint32_t r[EC];
         tmem_ld32(taddr + (uint32_t)c0, r);
-        // Every lane runs every shuffle; only the stores are predicated.
+        if (__all_sync(0xFFFFFFFFu, ea == 0 && eb_l == 0)) {
+          // No badly scaled row or column in this 32 x 32 block (the usual
+          // case): the scale factor is 1 and acc * 1 = acc exactly.
+          if (__all_sync(0xFFFFFFFFu, row_ok) && jmax == EC) {
+            if (J.beta != 0.f) {
 #pragma unroll
-        for (int jj = 0; jj < EC; ++jj) {
-          const int s = ea + __shfl_sync(0xFFFFFFFFu, eb_l, jj);
-          const float acc = __uint_as_float(r[jj]);
-          // acc * 2^s: one multiply when 2^s is a normal float, else scalbnf.
-          const float v = (s >= -126 && s <= 127) ? acc * __int_as_float((s + 127) << 23) : scalbnf(acc, s);
-          const float out = (J.beta != 0.f) ? fmaf(J.alpha, v, J.beta * cv[jj]) : J.alpha * v;
-          if (row_ok && jj < jmax) __stcs(cp + jj * J.ldc, out);
+              for (int jj = 0; jj < EC; ++jj) __stcs(cp + jj * J.ldc, fmaf(J.alpha, __uint_as_float(r[jj]), J.beta * cv[jj]));
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < EC; ++jj) __stcs(cp + jj * J.ldc, J.alpha * __uint_as_float(r[jj]));
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < EC; ++jj) {
+              const float acc = __uint_as_float(r[jj]);
+              const float out = (J.beta != 0.f) ? fmaf(J.alpha, acc, J.beta * cv[jj]) : J.alpha * acc;
+              if (row_ok && jj < jmax) __stcs(cp + jj * J.ldc, out);
+            }
+          }
+        } else {
+          // Every lane runs every shuffle; only the stores are predicated.
+#pragma unroll
+          for (int jj = 0; jj < EC; ++jj) {
+            const int s = ea + __shfl_sync(0xFFFFFFFFu, eb_l, jj);
+            const float acc = __uint_as_float(r[jj]);
+            // acc * 2^s: one multiply when 2^s is a normal float, else scalbnf.
+            const float v = (s >= -126 && s <= 127) ? acc * __int_as_float((s + 127) << 23) : scalbnf(acc, s);
+            const float out = (J.beta != 0.f) ? fmaf(J.alpha, v, J.beta * cv[jj]) : J.alpha * v;
+            if (row_ok && jj < jmax) __stcs(cp + jj * J.ldc, out);
+          }
         }
       }
       tc_fence_before();

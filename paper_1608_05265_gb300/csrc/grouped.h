@@ -25,7 +25,7 @@ struct GroupedPlan {
 
 // Argument check of one problem: 0, or minus the BLAS position of the first bad argument.
 int validate_problem(const gbgemm_problem& q);
-// Whether configuration `cfg` may run problem q (split configurations need k >= 128 and alpha != 0).
+// Whether configuration `cfg` may run problem q (split configurations need k >= 16 and alpha != 0).
 bool config_legal(const gbgemm_problem& q, int cfg);
 // The heuristic configuration used when no tuner or predictor is asked for.
 int default_config(const gbgemm_problem& q);

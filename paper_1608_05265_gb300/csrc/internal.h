@@ -130,6 +130,10 @@ struct SplitCall {
   void* panel_out = nullptr;
   void* panel2_out = nullptr;
   uint32_t* amax_out = nullptr;
+  // profiling: when set, recorded on the stream around the GEMM launch alone
+  // (the GEMM is then launched as a plain launch, not as a programmatic
+  // dependent of the packing, so the pair brackets the GEMM only)
+  cudaEvent_t gemm_begin = nullptr, gemm_end = nullptr;
 };
 // Zero the workspace head, pack both operands, run the GEMM (and the split-K
 // reduction).

@@ -194,8 +194,11 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   e = cudaGetLastError();
   if (e != cudaSuccess || items == 0) return e;
   const int grid = (int)(items < sms ? items : sms);
-  e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, tasks > 0);
+  const bool timed = c.gemm_begin && c.gemm_end;
+  if (timed && (e = cudaEventRecord(c.gemm_begin, s)) != cudaSuccess) return e;
+  e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, tasks > 0 && !timed);
   if (e != cudaSuccess) return e;
+  if (timed && (e = cudaEventRecord(c.gemm_end, s)) != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e != cudaSuccess || splitk == 1 || c.pack_only) return e;
   SplitGemmArgs a;
