@@ -113,8 +113,8 @@ struct TileJob {
   float* partial;
 };
 
-// One packing task: chunks kc0 .. kc0 + kPackChunks - 1 (those below nkc) of
-// the 128-row band rb of one operand.
+// One packing task: chunks kc0 .. kc0 + chunks - 1 (those below nkc) of the
+// 128-row band rb of one operand.
 struct PackJob {
   const float* X;
   int64_t ld;
@@ -125,6 +125,7 @@ struct PackJob {
   int64_t rows_alloc;       // panel rows per k chunk
   int64_t rb;
   int kc0, nkc;
+  int chunks;               // k chunks per task of this operand (1, 2 or kPackChunks)
   int kcontig;
   int band, band_tasks;     // band counter and the tasks that fill it
 };
@@ -166,7 +167,8 @@ struct SingleSched {
   int tiles_m, tiles_n, nkc, raster, bn, parts;
   int64_t rbA, rbB;          // panel row blocks (padded to even)
   int ra, rb;                // bands packed (ceil(m/128), ceil(n/128))
-  int ngroups;               // packing tasks per band
+  int pchunks;               // k chunks per packing task
+  int ngroups;               // packing tasks per band (ceil(nkc / pchunks))
   int64_t a_part, b_part;
   int batch;
   int64_t ps, as, cs;
@@ -221,7 +223,8 @@ struct SingleSched {
     P.panel2 = parts == 2 ? P.panel + (is_a ? a_part : b_part) : nullptr;
     P.rows_alloc = (is_a ? rbA : rbB) * 128;
     P.rb = idx;
-    P.kc0 = g * kPackChunks;
+    P.kc0 = g * pchunks;
+    P.chunks = pchunks;
     P.nkc = nkc;
     P.band = z * (ra + rb) + (is_a ? 0 : ra) + idx;
     P.band_tasks = ngroups;
@@ -292,6 +295,7 @@ struct GroupedSched {
     P.X = B.X; P.ld = B.ld; P.amax = B.amax; P.panel = B.panel; P.panel2 = B.panel2;
     P.rows = B.rows; P.k = B.k; P.rows_alloc = B.rows_alloc; P.rb = B.rb;
     P.kc0 = (i - B.first_task) * kPackChunks;
+    P.chunks = kPackChunks;
     P.nkc = B.nkc;
     P.kcontig = B.kcontig;
     P.band = B.cnt;
@@ -320,7 +324,7 @@ __device__ __forceinline__ void item_of(int tid, int it, int& rr, int& cc) {
 }
 
 __device__ __forceinline__ int task_chunks(const PackJob& P) {
-  return (P.nkc - P.kc0 < kPackChunks) ? P.nkc - P.kc0 : kPackChunks;
+  return (P.nkc - P.kc0 < P.chunks) ? P.nkc - P.kc0 : P.chunks;
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,13 @@ namespace {
 
 constexpr int BK = 16;
 
+// Register-staged tiles (k-contiguous float4 operands) put row r of k row p
+// at column r ^ 8((p / 4) mod 4): a warp's transposing stores (eight rows of
+// k rows p, p + 4, p + 8, p + 12, same q) then fall in 32 different banks
+// instead of two rows per bank, and groups of four consecutive rows stay
+// together for the 16-byte reads of the multiply loop.
+__device__ __forceinline__ int swz(int p, int r) { return r ^ (((p >> 2) & 3) << 3); }
+
 template <int BM, int BN, bool TA, bool TB, bool VEC>
 struct SimtTile {
   static constexpr int NT = (BM / 8) * (BN / 8);
@@ -100,14 +107,15 @@ struct SliceLoader {
       p += vstep;
     }
   }
-  // ... and from the registers into the k-major shared tile S[p][r].
+  // ... and from the registers into the k-major shared tile S[p][r], row r
+  // of k row p at S[p LDS + swz(p, r)] (see swz).
   template <int LDS>
   __device__ __forceinline__ void store(float* S, const float* reg, int tid) const {
     const int fx = (tid % PER) * W, vr = tid / PER;
 #pragma unroll
     for (int v = 0; v < NL; ++v)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) S[(fx + q) * LDS + vr + v * STRIDE] = reg[4 * v + q];
+      for (int q = 0; q < 4; ++q) S[(fx + q) * LDS + swz(fx + q, vr + v * STRIDE)] = reg[4 * v + q];
   }
 
   // Copy slice kt of an operand with kdim k indices into the k-major shared
@@ -205,10 +213,12 @@ __device__ __forceinline__ void simt_tile(const Problem& P, int64_t m0, int64_t 
     // tiles stalled mostly on instruction fetch).
 #pragma unroll 2
     for (int p = 0; p < BK; ++p) {
-      const float4 a0 = *reinterpret_cast<const float4*>(a_s + p * T::LDS_A + ty * 4);
-      const float4 a1 = *reinterpret_cast<const float4*>(a_s + p * T::LDS_A + BM / 2 + ty * 4);
-      const float4 b0 = *reinterpret_cast<const float4*>(b_s + p * T::LDS_B + tx * 4);
-      const float4 b1 = *reinterpret_cast<const float4*>(b_s + p * T::LDS_B + BN / 2 + tx * 4);
+      const int ca0 = REG_A ? swz(p, ty * 4) : ty * 4, ca1 = REG_A ? swz(p, BM / 2 + ty * 4) : BM / 2 + ty * 4;
+      const int cb0 = REG_B ? swz(p, tx * 4) : tx * 4, cb1 = REG_B ? swz(p, BN / 2 + tx * 4) : BN / 2 + tx * 4;
+      const float4 a0 = *reinterpret_cast<const float4*>(a_s + p * T::LDS_A + ca0);
+      const float4 a1 = *reinterpret_cast<const float4*>(a_s + p * T::LDS_A + ca1);
+      const float4 b0 = *reinterpret_cast<const float4*>(b_s + p * T::LDS_B + cb0);
+      const float4 b1 = *reinterpret_cast<const float4*>(b_s + p * T::LDS_B + cb1);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll

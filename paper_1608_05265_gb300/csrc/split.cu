@@ -32,28 +32,55 @@
 namespace gbg {
 namespace {
 
-// Split-K reduction: thread per C element (i, j), the slices' raw
-// accumulators summed in slice order (deterministic), then the epilogue of
-// split_gemm_kernel: x 2^(e_i + f_j), alpha, and beta C with one rounding of
-// beta C and one fused multiply-add.
+// Split-K reduction: a thread per four consecutive rows i .. i+3 of one
+// column j of C (rows of a 128-row tile, so the partials are 16-byte
+// vectors), the slices' raw accumulators summed in slice order
+// (deterministic), then the epilogue of split_gemm_kernel: x 2^(e_i + f_j),
+// alpha, and beta C with one rounding of beta C and one fused multiply-add.
+// Every load of a thread is independent, so one pass over the grid keeps
+// them all in flight.
 __global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t m, int64_t n, int bn, int tiles_m, int tiles_n,
                                                             int splitk, const float* __restrict__ partial,
                                                             const uint32_t* __restrict__ amaxA,
                                                             const uint32_t* __restrict__ amaxB, float alpha,
                                                             float beta, float* __restrict__ C, int64_t ldc) {
   wait_prerequisite_grid();  // launched as a dependent of the GEMM
-  const int64_t total = m * n;
+  const int64_t mq = (m + 3) / 4, total = mq * n;
   const size_t tile_elems = (size_t)128 * bn, slice_elems = (size_t)tiles_m * tiles_n * tile_elems;
+  const bool c_vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t % m, j = t / m;
-    const int64_t tm = i >> 7, tn = j / bn;
-    const float* p = partial + (size_t)(tm * tiles_n + tn) * tile_elems + (size_t)(j - tn * bn) * 128 + (i & 127);
-    float acc = 0.f;
-    for (int s = 0; s < splitk; ++s) acc += p[(size_t)s * slice_elems];
-    const int e = scale_exp_from_bits(amaxA[i]) + scale_exp_from_bits(amaxB[j]);
-    const float v = (e >= -126 && e <= 127) ? acc * __int_as_float((e + 127) << 23) : scalbnf(acc, e);
-    float* c = C + i + j * ldc;
-    *c = (beta != 0.f) ? fmaf(alpha, v, beta * *c) : alpha * v;
+    const int64_t i0 = (t % mq) * 4, j = t / mq;
+    const int64_t tm = i0 >> 7, tn = j / bn;
+    const float4* p = reinterpret_cast<const float4*>(
+        partial + (size_t)(tm * tiles_n + tn) * tile_elems + (size_t)(j - tn * bn) * 128 + (i0 & 127));
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < splitk; ++s) {
+      const float4 v = __ldcs(p + (size_t)s * (slice_elems / 4));
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    const int fj = scale_exp_from_bits(amaxB[j]);
+    float* c = C + i0 + j * ldc;
+    const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+    float o[4];
+    if (c_vec && i0 + 3 < m) {
+      const float4 cv = beta != 0.f ? *reinterpret_cast<const float4*>(c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = scale_exp_from_bits(amaxA[i0 + q]) + fj;
+        const float v = (e >= -126 && e <= 127) ? a4[q] * __int_as_float((e + 127) << 23) : scalbnf(a4[q], e);
+        o[q] = (beta != 0.f) ? fmaf(alpha, v, beta * c4[q]) : alpha * v;
+      }
+      *reinterpret_cast<float4*>(c) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (i0 + q >= m) break;
+        const int e = scale_exp_from_bits(amaxA[i0 + q]) + fj;
+        const float v = (e >= -126 && e <= 127) ? a4[q] * __int_as_float((e + 127) << 23) : scalbnf(a4[q], e);
+        c[q] = (beta != 0.f) ? fmaf(alpha, v, beta * c[q]) : alpha * v;
+      }
+    }
   }
 }
 
@@ -142,7 +169,13 @@ SingleSched make_single_sched(const SplitCall& c, const SplitLayout& L) {
   S.rbB = panel_row_blocks(c.n);
   S.ra = (int)((c.m + 127) / 128);
   S.rb = (int)((c.n + 127) / 128);
-  S.ngroups = (S.nkc + kPackChunks - 1) / kPackChunks;
+  // Chunks per packing task: kPackChunks, halved (down to 1) while the
+  // tasks would not give every SM three of them, so that small operands are
+  // packed in one round of loads.
+  const int64_t sms = c.num_sms > 0 ? c.num_sms : 148;
+  S.pchunks = kPackChunks;
+  while (S.pchunks > 1 && c.batch * (S.ra + S.rb) * ((S.nkc + S.pchunks - 1) / S.pchunks) < 3 * sms) S.pchunks >>= 1;
+  S.ngroups = (S.nkc + S.pchunks - 1) / S.pchunks;
   // per problem [A | B | A2 | B2]: A2 - A = B2 - B = pa + pb
   S.a_part = S.parts == 2 ? (int64_t)(L.pa + L.pb) : 0;
   S.b_part = S.a_part;
@@ -171,6 +204,8 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   if (tm * tn * c.batch * splitk > (int64_t)0x7FFFFFFF || tasks > (int64_t)0x7FFFFFFF) return cudaErrorInvalidValue;
   const SplitLayout L = split_layout(c.m, c.n, c.k, c.batch, splitk, c.bn);
   SingleSched S = make_single_sched(c, L);
+  // fewer chunks per task only below 3 tasks per SM: still far below 2^31
+  const int64_t ptasks = c.batch * (int64_t)(S.ra + S.rb) * S.ngroups;
   if (c.pack_only) {
     S.tiles_n = 0;  // no tiles: the packers only
     if (c.panel_out) {
@@ -190,13 +225,13 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   const int64_t items = tm * tn * c.batch * splitk;
   const int64_t sms = c.num_sms > 0 ? c.num_sms : 148;
   // packing tasks first, each its own CTA, then the GEMM
-  if (tasks > 0) pack_tasks_kernel<SingleSched><<<(unsigned)tasks, 256, 0, s>>>(S);
+  if (ptasks > 0) pack_tasks_kernel<SingleSched><<<(unsigned)ptasks, 256, 0, s>>>(S);
   e = cudaGetLastError();
   if (e != cudaSuccess || items == 0) return e;
   const int grid = (int)(items < sms ? items : sms);
   const bool timed = c.gemm_begin && c.gemm_end;
   if (timed && (e = cudaEventRecord(c.gemm_begin, s)) != cudaSuccess) return e;
-  e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, tasks > 0 && !timed);
+  e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, ptasks > 0 && !timed);
   if (e != cudaSuccess) return e;
   if (timed && (e = cudaEventRecord(c.gemm_end, s)) != cudaSuccess) return e;
   e = cudaGetLastError();
@@ -211,9 +246,9 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
 cudaError_t launch_splitk_reduce(const SplitGemmArgs& a, cudaStream_t s) {
   if (a.m <= 0 || a.n <= 0 || a.splitk <= 1) return cudaSuccess;
   const int tm = (int)((a.m + 127) / 128), tn = (int)((a.n + a.bn - 1) / a.bn);
-  const int64_t total = a.m * a.n;
+  const int64_t total = (a.m + 3) / 4 * a.n;  // a thread per four rows of a column
   int64_t blocks = (total + 255) / 256;
-  const int64_t cap = (int64_t)(a.num_sms > 0 ? a.num_sms : 148) * 8;
+  const int64_t cap = (int64_t)(a.num_sms > 0 ? a.num_sms : 148) * 16;
   if (blocks > cap) blocks = cap;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);

@@ -9,6 +9,9 @@ beyond a one-line summary.  Names:
   split4096   sgemm 4096^3 NN, ld 4104, split path (alpha 1.5, beta -0.25)
   simt4096    the same on the FP32 SIMT path
   split8192   sgemm 8192^3 NN, ld 8200, split path (the headline shape)
+  split1024 / split2048 / simt8192
+              the same shape family at n = 1024 and 2048 (split path), and
+              8192 on the SIMT path
   grouped     the uneven batch (m, n, k log-uniform in [16, 1024], seed 3;
               4096 problems, or --count), one plan with the default
               configurations
@@ -139,8 +142,8 @@ def _lu(h, reps):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=["split4096", "simt4096", "split8192", "grouped", "lu4608", "linpack8192",
-                                     "linpack16384", "gemv", "splitk", "mlp"])
+    ap.add_argument("name", choices=["split1024", "split2048", "split4096", "simt4096", "split8192", "simt8192",
+                                     "grouped", "lu4608", "linpack8192", "linpack16384", "gemv", "splitk", "mlp"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--count", type=int, default=4096, help="problems of the grouped batch")
     args = ap.parse_args(argv)
@@ -149,7 +152,7 @@ def main(argv=None) -> int:
     build.build()
     h = gbgemm.Handle(0)
     h.set_stream(torch.cuda.current_stream())
-    if args.name in ("split4096", "simt4096", "split8192"):
+    if args.name in ("split1024", "split2048", "split4096", "simt4096", "split8192", "simt8192"):
         _split_or_simt(h, args.name[:-4], args.reps, int(args.name[-4:]))
     elif args.name == "grouped":
         _grouped(h, args.reps, args.count)
