@@ -54,9 +54,15 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t m, int64_t n
     const float4* p = reinterpret_cast<const float4*>(
         partial + (size_t)(tm * tiles_n + tn) * tile_elems + (size_t)(j - tn * bn) * 128 + (i0 & 127));
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s = 0; s < splitk; ++s) {
-      const float4 v = __ldcs(p + (size_t)s * (slice_elems / 4));
-      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    for (int s0 = 0; s0 < splitk; s0 += 8) {
+      // eight slices' loads in flight, then summed in slice order
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < splitk) v[u] = __ldcs(p + (size_t)(s0 + u) * (slice_elems / 4));
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < splitk) { acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w; }
     }
     const int fj = scale_exp_from_bits(amaxB[j]);
     float* c = C + i0 + j * ldc;
