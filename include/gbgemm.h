@@ -378,10 +378,59 @@ int gbgemm_autotune(gbgemm_handle* h, const gbgemm_problem* prob, int reps, floa
 int gbgemm_tuning_save(gbgemm_handle* h, const char* path);
 int gbgemm_tuning_load(gbgemm_handle* h, const char* path);
 int gbgemm_tuning_clear(gbgemm_handle* h);
-/* mode 0 (default): gbgemm_sgemm picks its tile configuration by a fixed
- * heuristic.  mode 1: by the tuner's lowest latency among the legal
- * configurations of the handle's path (tuning a new shape on first use,
- * which synchronises; do it before any stream capture). */
+/* ---------------------------------------------------------------------- */
+/* Schedules of a single call.  The paper fixes the division of one sgemm
+ * into micro-kernel work and the order of that work by hand (Sections
+ * III-A, III-C: the ir / or ratios, KSUB, the Task / Column / K loops); here
+ * a schedule fixes, for one gbgemm_sgemm call, the path, the tile, the order
+ * of the tiles and the division of k:
+ *   s = 0, 1, 2          SIMT path, CTA tile 128x128, 64x64, 128x64;
+ *   s = 3 + 12 b + 4 r + q   split-BF16 path, tile 128 x BN with BN = 64 << b
+ *                        (b = 0, 1, 2), tiles visited in groups of R tile
+ *                        rows (all tile columns of a group before the next
+ *                        group) with R = 1, 4, 16 for r = 0, 1, 2, and the k
+ *                        range cut into S = 1, 2, 4, 8 slices for q = 0..3
+ *                        (S > 1: split-K, the slices' raw accumulators summed
+ *                        in slice order by a reduction).
+ * 39 schedules; the tile shapes are those of gbgemm_config.  Legal: SIMT
+ * schedules always; split schedules when k >= 16 and alpha != 0 (the error
+ * bound, as for the grouped configurations); S > 1 only when k >= 512 (two
+ * BF16 parts), every slice gets at least 4 k chunks of 32, no slice is empty
+ * and the output has at most 2 x (number of SMs) tiles of 128 x BN. */
+#define GBGEMM_NUM_SCHEDULES 39
+/* Decode schedule s (host only, no GPU): path (gbgemm_path value), tile
+ * rows and columns, R and S as above.  Bad s: GBGEMM_ERR_INVALID_VALUE.
+ * Any output pointer may be NULL. */
+int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster, int* splitk);
+/* Whether schedule s may run problem prob on this handle's GPU (*legal = 0 or 1). */
+int gbgemm_schedule_legal(gbgemm_handle* h, const gbgemm_problem* prob, int s, int* legal);
+/* The schedule the fixed heuristic (tuning mode 0, path AUTO) gives prob. */
+int gbgemm_schedule_default(gbgemm_handle* h, const gbgemm_problem* prob, int* s);
+/* Time every legal schedule of prob's shape as one call (latency, CUDA
+ * events, one warm-up, median of `reps`; -1 when illegal) on the tuner's
+ * scratch buffers; cached in the handle like gbgemm_autotune's results.
+ * *best = the lowest latency (ties to the lower index).  Synchronises the
+ * handle's stream.  latency_us: host array of GBGEMM_NUM_SCHEDULES, or NULL. */
+int gbgemm_autotune_schedules(gbgemm_handle* h, const gbgemm_problem* prob, int reps, float* latency_us, int* best);
+/* Schedule of the handle's most recent gbgemm_sgemm that launched the product
+ * kernels (-1 before the first). */
+int gbgemm_last_schedule(gbgemm_handle* h, int* s);
+/* Pin schedule s for the handle's later single calls (s = -1 unpins).  A
+ * pinned schedule overrides the tuning mode for every call it is legal for
+ * (gbgemm_schedule_legal, and on the handle's path unless that is AUTO);
+ * other calls choose as the tuning mode says.  Bad s: GBGEMM_ERR_INVALID_VALUE. */
+int gbgemm_set_schedule(gbgemm_handle* h, int s);
+
+/* How gbgemm_sgemm (one problem) chooses its schedule:
+ *   mode 0 (default): the fixed heuristic;
+ *   mode 1: the schedule tuner's lowest latency among the legal schedules of
+ *           the handle's path (tuning a new shape on first use, which
+ *           synchronises; do it before any stream capture);
+ *   mode 2: the learned schedule predictor (gbgemm_predictor_select(h, 1)),
+ *           among the legal schedules of the handle's path; mode 1 when the
+ *           predictor has no parameters or a dimension lies outside
+ *           [8, 16384].
+ * Strided batches (batch > 1) always use the fixed heuristic. */
 int gbgemm_set_tuning(gbgemm_handle* h, int mode);
 
 /* ---------------------------------------------------------------------- */
@@ -405,6 +454,19 @@ int gbgemm_set_tuning(gbgemm_handle* h, int mode);
  * dimension in [8, 16384]); other shapes, or a handle without parameters,
  * use the tuner. */
 #define GBGEMM_MLP_PARAMS 5126
+/* The schedule predictor: the same network with GBGEMM_NUM_SCHEDULES outputs
+ * (predicted log2(latency_s / latency_best) of every schedule s), trained on
+ * gbgemm_autotune_schedules latencies; W3[39][64], b3[39]. */
+#define GBGEMM_SCHED_MLP_PARAMS 7271
+/* Select the network that the gbgemm_predictor_* calls below address:
+ * which = 0, the configuration predictor (GBGEMM_NUM_CONFIGS outputs,
+ * GBGEMM_MLP_PARAMS parameters, grouped plans); which = 1, the schedule
+ * predictor (GBGEMM_NUM_SCHEDULES outputs, GBGEMM_SCHED_MLP_PARAMS
+ * parameters, tuning mode 2).  A new handle addresses network 0.  Where the
+ * descriptions below say 6 outputs or GBGEMM_MLP_PARAMS, read the selected
+ * network's outputs and parameter count; legal then holds (outputs + 7) / 8
+ * bytes per sample, bit c % 8 of byte c / 8 for output c. */
+int gbgemm_predictor_select(gbgemm_handle* h, int which);
 int gbgemm_predictor_set(gbgemm_handle* h, const float* params /* host */);
 int gbgemm_predictor_get(gbgemm_handle* h, float* params /* host */);
 int gbgemm_predictor_features(const gbgemm_problem* prob, float* x /* host, 8 floats */);

@@ -2,11 +2,12 @@
 
 Only the tests import this module.  A plain float64 numpy restatement of the
 3-layer MLP the library trains on the GPU: x (8) -> W1, b1 -> ReLU (64) ->
-W2, b2 -> ReLU (64) -> W3, b3 (6), with the loss
+W2, b2 -> ReLU (64) -> W3, b3 (OUT outputs: 6 for the configuration network,
+39 for the schedule network, read off the parameter count), with the loss
     L = sum_{s,c} mask[s,c] (out[s,c] - y[s,c])^2 / sum_{s,c} mask[s,c]
 and its gradient by the chain rule.  Parameters are one flat vector in the
-order W1[64][8], b1[64], W2[64][64], b2[64], W3[6][64], b3[6] (row = output
-unit), the layout of the library's parameter array.
+order W1[64][8], b1[64], W2[64][64], b2[64], W3[OUT][64], b3[OUT] (row =
+output unit), the layout of the library's parameter arrays.
 """
 
 from __future__ import annotations
@@ -14,14 +15,28 @@ from __future__ import annotations
 import numpy as np
 
 N_IN, N_H, N_OUT = 8, 64, 6
-SIZES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)), ("W3", (N_OUT, N_H)),
-         ("b3", (N_OUT,))]
+
+
+def sizes(n_out: int = N_OUT):
+    return [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)), ("W3", (n_out, N_H)),
+            ("b3", (n_out,))]
+
+
+SIZES = sizes(N_OUT)
 N_PARAMS = sum(int(np.prod(s)) for _, s in SIZES)
+N_HIDDEN_PARAMS = N_H * N_IN + N_H + N_H * N_H + N_H
+
+
+def n_outputs(theta) -> int:
+    """Output count of a parameter vector: (len - hidden parameters) / (64 + 1)."""
+    n = (len(theta) - N_HIDDEN_PARAMS) // (N_H + 1)
+    assert N_HIDDEN_PARAMS + n * (N_H + 1) == len(theta), "not a parameter vector of this network"
+    return n
 
 
 def unpack(theta: np.ndarray) -> dict:
     out, off = {}, 0
-    for name, shape in SIZES:
+    for name, shape in sizes(n_outputs(theta)):
         n = int(np.prod(shape))
         out[name] = np.asarray(theta[off:off + n], dtype=np.float64).reshape(shape)
         off += n
@@ -29,7 +44,7 @@ def unpack(theta: np.ndarray) -> dict:
 
 
 def pack(p: dict) -> np.ndarray:
-    return np.concatenate([p[name].reshape(-1) for name, _ in SIZES])
+    return np.concatenate([p[name].reshape(-1) for name, _ in sizes(p["b3"].shape[0])])
 
 
 def forward(theta, X):
@@ -78,7 +93,7 @@ def predict(theta, X, legal):
     res = []
     for s in range(out.shape[0]):
         best = -1
-        for c in range(N_OUT):
+        for c in range(out.shape[1]):
             if not (int(legal[s]) >> c) & 1:
                 continue
             if best < 0 or out[s, c] < out[s, best]:

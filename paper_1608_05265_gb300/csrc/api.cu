@@ -8,6 +8,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <map>
+#include <string>
 #include <vector>
 
 #include "grouped.h"
@@ -39,7 +41,13 @@ struct gbgemm_handle {
   // tuning
   int tuning = 0;
   gbg::Tuner tuner;
-  gbg::Predictor predictor;
+  gbg::Predictor predictor{GBGEMM_NUM_CONFIGS};
+  gbg::Predictor sched_predictor{GBGEMM_NUM_SCHEDULES};
+  int pred_sel = 0;                          // network addressed by gbgemm_predictor_*
+  std::map<std::string, int> sched_choice;   // tuning mode 2: predicted schedule per shape key
+  void* pred_scratch = nullptr;              // device scratch of one schedule prediction
+  int last_schedule = -1;
+  int pinned_schedule = -1;                  // gbgemm_set_schedule
 };
 
 namespace {
@@ -158,6 +166,7 @@ int gbgemm_destroy(gbgemm_handle* h) {
     if (e) cudaEventDestroy(e);
   if (h->lu_side) cudaStreamDestroy(h->lu_side);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->pred_scratch) cudaFree(h->pred_scratch);
   delete h;
   return GBGEMM_OK;
 }
@@ -190,6 +199,104 @@ int gbgemm_reserve_workspace(gbgemm_handle* h, size_t bytes) {
   return ensure_workspace(h, bytes);
 }
 
+namespace {
+
+// The fixed heuristic's schedule of a call (tuning mode 0).  Path AUTO: split
+// from k = 128 on a GPU that has the split path, SIMT below.  Split: the
+// widest tile that still gives at least half of the SMs a tile (measured at
+// 2048^3: 128 BN-256 tiles beat 256 BN-128 tiles, 208 against 150 TFLOP/s),
+// tile rows in groups of 16, and for one problem with a long k and too few
+// tiles the k range cut into slices (keeping the widest tile).  SIMT: 64 x 64
+// for small outputs, else 128 x 128.
+gbg::Schedule default_schedule(const gbgemm_handle* h, int path, int64_t m, int64_t n, int64_t k, int64_t batch) {
+  if (path == GBGEMM_PATH_AUTO) path = (k >= gbg::kSplitMinK && split_supported(h)) ? GBGEMM_PATH_SPLIT_BF16 : GBGEMM_PATH_SIMT;
+  gbg::Schedule d{};
+  d.path = path;
+  d.raster = 16;
+  d.splitk = 1;
+  d.simt_cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
+  auto tiles = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn) * batch; };
+  const int64_t half_sms = h->num_sms / 2;
+  d.bn = tiles(128, 256) >= half_sms ? 256 : tiles(128, 128) >= half_sms ? 128 : 64;
+  if (batch == 1) {
+    const int s = gbg::choose_splitk(tiles(128, 256), k, h->num_sms);
+    if (s > 1) {
+      d.bn = 256;
+      d.splitk = s;
+    }
+  }
+  return d;
+}
+
+bool in_training_range3(int64_t m, int64_t n, int64_t k) {
+  auto ok = [](int64_t v) { return v >= 8 && v <= 16384; };
+  return ok(m) && ok(n) && ok(k);
+}
+
+// Schedules a call may take on this handle: legal for the problem, on the
+// handle's path (AUTO: either), the split path only where the GPU has it.
+bool schedule_allowed(const gbgemm_handle* h, const gbgemm_problem& q, int s) {
+  gbg::Schedule d;
+  if (!gbg::schedule_decode(s, &d)) return false;
+  if (h->path != GBGEMM_PATH_AUTO && d.path != h->path) return false;
+  if (d.path == GBGEMM_PATH_SPLIT_BF16 && !split_supported(h)) return false;
+  return gbg::schedule_legal(q.m, q.n, q.k, q.alpha, s, h->num_sms);
+}
+
+// Tuning modes 1 and 2: the tuner's fastest allowed schedule, or the schedule
+// predictor's choice (cached per shape key; the tuner where the predictor
+// has no parameters or the shape is outside its training range).  *best = -1
+// when nothing is allowed.  Synchronises the stream on a shape's first call.
+int choose_schedule(gbgemm_handle* h, const gbgemm_problem& q, int* best) {
+  *best = -1;
+  if (h->tuning == 2 && h->sched_predictor.ready() && in_training_range3(q.m, q.n, q.k)) {
+    const std::string key = gbg::tune_key(q) + (h->path == GBGEMM_PATH_AUTO ? " a" : h->path == GBGEMM_PATH_SIMT ? " s" : " b");
+    auto it = h->sched_choice.find(key);
+    if (it != h->sched_choice.end()) {
+      *best = it->second;
+      return GBGEMM_OK;
+    }
+    constexpr int kLB = (GBGEMM_NUM_SCHEDULES + 7) / 8;
+    float x[8];
+    gbg::predictor_features(q, x);
+    uint8_t legal[kLB] = {};
+    for (int s = 0; s < GBGEMM_NUM_SCHEDULES; ++s)
+      if (schedule_allowed(h, q, s)) legal[s >> 3] |= (uint8_t)(1u << (s & 7));
+    if (!h->pred_scratch && cudaMalloc(&h->pred_scratch, 256) != cudaSuccess) {
+      cudaGetLastError();
+      h->pred_scratch = nullptr;
+      return GBGEMM_ERR_ALLOC;
+    }
+    float* dx = static_cast<float*>(h->pred_scratch);
+    uint8_t* dl = reinterpret_cast<uint8_t*>(static_cast<char*>(h->pred_scratch) + 64);
+    int* dc = reinterpret_cast<int*>(static_cast<char*>(h->pred_scratch) + 128);
+    int choice = -1;
+    if (cudaMemcpyAsync(dx, x, sizeof(x), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dl, legal, sizeof(legal), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return GBGEMM_ERR_CUDA;
+    int rc = h->sched_predictor.predict(dx, dl, 1, nullptr, dc, h->stream);
+    if (rc != GBGEMM_OK) return rc;
+    if (cudaMemcpyAsync(&choice, dc, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return GBGEMM_ERR_CUDA;
+    if (choice >= 0) {
+      h->sched_choice[key] = choice;
+      *best = choice;
+      return GBGEMM_OK;
+    }
+  }
+  std::vector<float> lat;
+  h->tuner.bind(h->stream, h->d_status, h->num_sms);
+  if (h->tuner.measure_schedules(q, 3, &lat) != GBGEMM_OK) return GBGEMM_ERR_CUDA;
+  for (int s = 0; s < GBGEMM_NUM_SCHEDULES; ++s) {
+    if (lat[(size_t)s] < 0.f || !schedule_allowed(h, q, s)) continue;
+    if (*best < 0 || lat[(size_t)s] < lat[(size_t)*best]) *best = s;
+  }
+  return GBGEMM_OK;
+}
+
+}  // namespace
+
 // The call after argument checks: one problem (batch 1) or a strided batch of
 // equal problems, problem z at A + z*sa, B + z*sb, C + z*sc.
 static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb, int64_t m, int64_t n, int64_t k,
@@ -206,45 +313,26 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
     h->kernel_launches += 1;
     return GBGEMM_OK;
   }
-  int path = h->path;
-  if (path == GBGEMM_PATH_AUTO) path = (k >= gbg::kSplitMinK && split_supported(h)) ? GBGEMM_PATH_SPLIT_BF16 : GBGEMM_PATH_SIMT;
   gbg::Problem p{ta, tb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
-  // Default tiles.  Split: the widest tile that still gives at least half of
-  // the SMs a tile (measured at 2048^3: 128 BN-256 tiles beat 256 BN-128
-  // tiles, 208 against 150 TFLOP/s).  SIMT: 64 x 64 for small outputs.
-  auto tiles = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn) * batch; };
-  const int64_t half_sms = h->num_sms / 2;
-  int simt_cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
-  int split_bn = tiles(128, 256) >= half_sms ? 256 : tiles(128, 128) >= half_sms ? 128 : 64;
-  // a long k with few tiles is cut into k slices instead: keep the widest tile
-  if (batch == 1 && gbg::choose_splitk(tiles(128, 256), k, h->num_sms) > 1) split_bn = 256;
-  if (h->tuning == 1 && batch == 1) {
+  gbg::Schedule d = default_schedule(h, h->path, m, n, k, batch);
+  const gbgemm_problem q1{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
+  if (batch == 1 && h->pinned_schedule >= 0 && schedule_allowed(h, q1, h->pinned_schedule)) {
+    gbg::schedule_decode(h->pinned_schedule, &d);
+  } else if (h->tuning >= 1 && batch == 1) {
     const gbgemm_problem q{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
-    gbg::TuneResult r;
-    h->tuner.bind(h->stream, h->d_status, h->num_sms);
-    if (h->tuner.measure(q, 3, &r) != GBGEMM_OK) return GBGEMM_ERR_CUDA;
     int best = -1;
-    for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c) {
-      if (r.latency_us[c] < 0.f) continue;
-      const bool is_split = c >= GBGEMM_CFG_SPLIT_BN64;
-      if (h->path == GBGEMM_PATH_SIMT && is_split) continue;
-      if (h->path == GBGEMM_PATH_SPLIT_BF16 && !is_split) continue;
-      if (is_split && !split_supported(h)) continue;
-      if (best < 0 || r.latency_us[c] < r.latency_us[best]) best = c;
-    }
-    if (best >= GBGEMM_CFG_SPLIT_BN64) {
-      path = GBGEMM_PATH_SPLIT_BF16;
-      split_bn = best == GBGEMM_CFG_SPLIT_BN64 ? 64 : best == GBGEMM_CFG_SPLIT_BN128 ? 128 : 256;
-    } else if (best >= 0) {
-      path = GBGEMM_PATH_SIMT;
-      simt_cfg = best;
-    }
+    const int rc = choose_schedule(h, q, &best);
+    if (rc != GBGEMM_OK) return rc;
+    if (best >= 0) gbg::schedule_decode(best, &d);
   }
+  const int path = d.path;
+  const int simt_cfg = d.simt_cfg, split_bn = d.bn;
   if (path == GBGEMM_PATH_SIMT) {
     const int cfg = simt_cfg;
     if (gbg::launch_simt_batched(p, cfg, batch, sa, sb, sc, h->stream) != cudaSuccess) return GBGEMM_ERR_CUDA;
     h->kernel_launches += 1;
     h->last_path = GBGEMM_PATH_SIMT;
+    h->last_schedule = cfg;
     return GBGEMM_OK;
   }
   if (!split_supported(h)) return GBGEMM_ERR_UNSUPPORTED_DEVICE;
@@ -252,8 +340,7 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   // and row maxima (zeroed per call), the packed panels, and with split-K
   // (one problem, long k, too few tiles for the SMs) splitk x tiles raw
   // 128 x bn accumulators, summed by a reduction.
-  const int64_t tiles_mn = ((m + 127) / 128) * ((n + split_bn - 1) / split_bn);
-  const int splitk = batch == 1 ? gbg::choose_splitk(tiles_mn, k, h->num_sms) : 1;
+  const int splitk = batch == 1 ? d.splitk : 1;
   const gbg::SplitLayout L = gbg::split_layout(m, n, k, batch, splitk, split_bn);
   if (L.block > ((size_t)1 << 62) / (size_t)batch) return GBGEMM_ERR_ALLOC;
   int rc = ensure_workspace(h, L.total);
@@ -262,7 +349,7 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   c.ta = ta; c.tb = tb; c.m = m; c.n = n; c.k = k; c.alpha = alpha; c.beta = beta;
   c.A = A; c.lda = lda; c.B = B; c.ldb = ldb; c.C = C; c.ldc = ldc;
   c.batch = batch; c.sa = sa; c.sb = sb; c.sc = sc;
-  c.bn = split_bn; c.raster = 16; c.splitk = splitk;
+  c.bn = split_bn; c.raster = d.raster; c.splitk = splitk;
   c.ws = h->ws; c.status = h->d_status; c.num_sms = h->num_sms;
   h->kernel_launches += 1;  // the packing launch (the memset of the workspace head is not a kernel of ours)
   if (prof_pair(h, &c.gemm_begin, &c.gemm_end) != cudaSuccess) return GBGEMM_ERR_CUDA;
@@ -270,6 +357,7 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   h->kernel_launches += splitk > 1 ? 2 : 1;
   h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;
+  h->last_schedule = gbg::schedule_encode_split(split_bn, d.raster, splitk);
   return GBGEMM_OK;
 }
 
@@ -858,14 +946,22 @@ int gbgemm_predictor_set(gbgemm_handle* h, const float* params) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!params) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard dg(h->device);
-  return h->predictor.set(params);
+  if (h->pred_sel == 1) h->sched_choice.clear();
+  return (h->pred_sel == 1 ? h->sched_predictor : h->predictor).set(params);
+}
+
+int gbgemm_predictor_select(gbgemm_handle* h, int which) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (which != 0 && which != 1) return GBGEMM_ERR_INVALID_VALUE;
+  h->pred_sel = which;
+  return GBGEMM_OK;
 }
 
 int gbgemm_predictor_get(gbgemm_handle* h, float* params) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!params) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard dg(h->device);
-  return h->predictor.get(params);
+  return (h->pred_sel == 1 ? h->sched_predictor : h->predictor).get(params);
 }
 
 int gbgemm_predictor_features(const gbgemm_problem* prob, float* x) {
@@ -879,7 +975,7 @@ int gbgemm_predictor_predict(gbgemm_handle* h, const float* x, const uint8_t* le
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (n < 0 || (n > 0 && !x)) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard dg(h->device);
-  return h->predictor.predict(x, legal, n, scores, configs, h->stream);
+  return (h->pred_sel == 1 ? h->sched_predictor : h->predictor).predict(x, legal, n, scores, configs, h->stream);
 }
 
 int gbgemm_predictor_loss_grad(gbgemm_handle* h, const float* x, const float* y, const float* mask, int64_t n,
@@ -887,7 +983,7 @@ int gbgemm_predictor_loss_grad(gbgemm_handle* h, const float* x, const float* y,
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!x || !y || !mask || !grad) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard dg(h->device);
-  return h->predictor.loss_grad(x, y, mask, n, loss, grad, h->stream);
+  return (h->pred_sel == 1 ? h->sched_predictor : h->predictor).loss_grad(x, y, mask, n, loss, grad, h->stream);
 }
 
 int gbgemm_predictor_train(gbgemm_handle* h, const float* x, const float* y, const float* mask, int64_t n, int epochs,
@@ -895,7 +991,9 @@ int gbgemm_predictor_train(gbgemm_handle* h, const float* x, const float* y, con
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!x || !y || !mask) return GBGEMM_ERR_INVALID_VALUE;
   DeviceGuard dg(h->device);
-  return h->predictor.train(x, y, mask, n, epochs, batch, lr, seed, final_loss, h->stream);
+  if (h->pred_sel == 1) h->sched_choice.clear();
+  return (h->pred_sel == 1 ? h->sched_predictor : h->predictor)
+      .train(x, y, mask, n, epochs, batch, lr, seed, final_loss, h->stream);
 }
 
 int gbgemm_tuning_save(gbgemm_handle* h, const char* path) {
@@ -913,13 +1011,80 @@ int gbgemm_tuning_load(gbgemm_handle* h, const char* path) {
 int gbgemm_tuning_clear(gbgemm_handle* h) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   h->tuner.cache.clear();
+  h->tuner.sched_cache.clear();
+  h->sched_choice.clear();
   return GBGEMM_OK;
 }
 
 int gbgemm_set_tuning(gbgemm_handle* h, int mode) {
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
-  if (mode != 0 && mode != 1) return GBGEMM_ERR_INVALID_VALUE;
+  if (mode != 0 && mode != 1 && mode != 2) return GBGEMM_ERR_INVALID_VALUE;
   h->tuning = mode;
+  return GBGEMM_OK;
+}
+
+int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster, int* splitk) {
+  gbg::Schedule d;
+  if (!gbg::schedule_decode(s, &d)) return GBGEMM_ERR_INVALID_VALUE;
+  const bool simt = d.path == GBGEMM_PATH_SIMT;
+  if (path) *path = d.path;
+  if (tile_m) *tile_m = simt ? (d.simt_cfg == gbg::SIMT_64x64 ? 64 : 128) : 128;
+  if (tile_n) *tile_n = simt ? (d.simt_cfg == gbg::SIMT_128x128 ? 128 : 64) : d.bn;
+  if (raster) *raster = simt ? 1 : d.raster;
+  if (splitk) *splitk = d.splitk;
+  return GBGEMM_OK;
+}
+
+int gbgemm_schedule_legal(gbgemm_handle* h, const gbgemm_problem* prob, int s, int* legal) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!prob || !legal || s < 0 || s >= GBGEMM_NUM_SCHEDULES) return GBGEMM_ERR_INVALID_VALUE;
+  gbg::Schedule d;
+  gbg::schedule_decode(s, &d);
+  *legal = gbg::schedule_legal(prob->m, prob->n, prob->k, prob->alpha, s, h->num_sms) &&
+           !(d.path == GBGEMM_PATH_SPLIT_BF16 && !split_supported(h));
+  return GBGEMM_OK;
+}
+
+int gbgemm_schedule_default(gbgemm_handle* h, const gbgemm_problem* prob, int* s) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!prob || !s) return GBGEMM_ERR_INVALID_VALUE;
+  const gbg::Schedule d = default_schedule(h, GBGEMM_PATH_AUTO, prob->m, prob->n, prob->k, 1);
+  *s = d.path == GBGEMM_PATH_SIMT ? d.simt_cfg : gbg::schedule_encode_split(d.bn, d.raster, d.splitk);
+  return GBGEMM_OK;
+}
+
+int gbgemm_autotune_schedules(gbgemm_handle* h, const gbgemm_problem* prob, int reps, float* latency_us, int* best) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!prob || reps < 1) return GBGEMM_ERR_INVALID_VALUE;
+  if (gbg::validate_problem(*prob) != 0 || prob->m == 0 || prob->n == 0 || prob->k == 0) return GBGEMM_ERR_INVALID_VALUE;
+  DeviceGuard dg(h->device);
+  std::vector<float> lat;
+  h->tuner.bind(h->stream, h->d_status, h->num_sms);
+  const int rc = h->tuner.measure_schedules(*prob, reps, &lat);
+  if (rc != GBGEMM_OK) return rc;
+  int b = -1;
+  for (int s = 0; s < GBGEMM_NUM_SCHEDULES; ++s) {
+    gbg::Schedule d;
+    gbg::schedule_decode(s, &d);
+    if (d.path == GBGEMM_PATH_SPLIT_BF16 && !split_supported(h)) lat[(size_t)s] = -1.f;
+    if (lat[(size_t)s] >= 0.f && (b < 0 || lat[(size_t)s] < lat[(size_t)b])) b = s;
+  }
+  if (latency_us) std::memcpy(latency_us, lat.data(), sizeof(float) * GBGEMM_NUM_SCHEDULES);
+  if (best) *best = b;
+  return GBGEMM_OK;
+}
+
+int gbgemm_last_schedule(gbgemm_handle* h, int* s) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (!s) return GBGEMM_ERR_INVALID_VALUE;
+  *s = h->last_schedule;
+  return GBGEMM_OK;
+}
+
+int gbgemm_set_schedule(gbgemm_handle* h, int s) {
+  if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (s < -1 || s >= GBGEMM_NUM_SCHEDULES) return GBGEMM_ERR_INVALID_VALUE;
+  h->pinned_schedule = s;
   return GBGEMM_OK;
 }
 

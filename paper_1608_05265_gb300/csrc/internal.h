@@ -110,6 +110,43 @@ struct SplitLayout {
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t k, int64_t batch, int splitk, int bn);
 
+// ---- single-call schedules (gbgemm_schedule_info) ----
+struct Schedule {
+  int path;      // GBGEMM_PATH_SIMT or GBGEMM_PATH_SPLIT_BF16
+  int simt_cfg;  // SimtConfig (SIMT path)
+  int bn;        // tile columns (split path)
+  int raster;    // tile rows per group of the tile order (split path)
+  int splitk;    // k slices (split path)
+};
+inline bool schedule_decode(int s, Schedule* o) {
+  if (s < 0 || s >= GBGEMM_NUM_SCHEDULES) return false;
+  if (s < SIMT_NUM_CONFIGS) {
+    *o = Schedule{GBGEMM_PATH_SIMT, s, 0, 0, 1};
+    return true;
+  }
+  const int t = s - SIMT_NUM_CONFIGS, b = t / 12, r = (t / 4) % 3, q = t % 4;
+  *o = Schedule{GBGEMM_PATH_SPLIT_BF16, -1, 64 << b, r == 0 ? 1 : (r == 1 ? 4 : 16), 1 << q};
+  return true;
+}
+inline int schedule_encode_split(int bn, int raster, int splitk) {
+  const int b = bn == 64 ? 0 : (bn == 128 ? 1 : 2);
+  const int r = raster == 1 ? 0 : (raster == 4 ? 1 : 2);
+  const int q = splitk >= 8 ? 3 : (splitk >= 4 ? 2 : (splitk >= 2 ? 1 : 0));
+  return SIMT_NUM_CONFIGS + 12 * b + 4 * r + q;
+}
+// Legality of schedule s for one problem (m, n, k, alpha) on num_sms SMs.
+inline bool schedule_legal(int64_t m, int64_t n, int64_t k, float alpha, int s, int num_sms) {
+  Schedule d;
+  if (!schedule_decode(s, &d)) return false;
+  if (d.path == GBGEMM_PATH_SIMT) return true;
+  if (k < kSplitShortK || alpha == 0.0f) return false;
+  if (d.splitk == 1) return true;
+  if (split_parts(k) != 1) return false;
+  const int64_t nkc = panel_k_chunks(k), per = (nkc + d.splitk - 1) / d.splitk;
+  const int64_t tiles = ((m + 127) / 128) * ((n + d.bn - 1) / d.bn);
+  return nkc >= 4 * (int64_t)d.splitk && (int64_t)(d.splitk - 1) * per < nkc && tiles <= 2 * (int64_t)num_sms;
+}
+
 // One split-path call: the packing launch, then the persistent tcgen05 GEMM.
 struct SplitCall {
   int ta = 0, tb = 0;

@@ -1,5 +1,6 @@
-// Learned configuration predictor: a 3-layer MLP, 8 -> 64 -> 64 -> 6 with
-// ReLU, FP32, trained and evaluated on the GPU by the kernels below.
+// Learned configuration predictors: 3-layer MLPs, 8 -> 64 -> 64 -> OUT with
+// ReLU, FP32, trained and evaluated on the GPU by the kernels below: OUT = 6
+// for the grouped plans' configurations, OUT = 39 for single-call schedules.
 //
 // The paper chooses its micro-kernel parameters by hand and notes the
 // trade-off between input and output ratios (Section III-C); here a small
@@ -7,11 +8,12 @@
 // (path and tile shape) is cheapest for a shape, so that grouped plans can
 // skip timing every problem.
 //
-// Parameters (one flat FP32 array of GBGEMM_MLP_PARAMS):
-//   W1[64][8], b1[64], W2[64][64], b2[64], W3[6][64], b3[6]   (row = output)
+// Parameters (one flat FP32 array of GBGEMM_MLP_PARAMS, or
+// GBGEMM_SCHED_MLP_PARAMS for the schedule network):
+//   W1[64][8], b1[64], W2[64][64], b2[64], W3[OUT][64], b3[OUT]   (row = output)
 // Inputs x[8]: log2 m/14, log2 n/14, log2 k/14, transa, transb, and the
 // 16-byte alignment class of A, B, C (0/1).  Outputs: predicted
-// log2(cost_c / cost_best) of every configuration c.
+// log2(cost_c / cost_best) of every configuration (or schedule) c.
 // Loss: mean over (sample, legal configuration) of (output - target)^2.
 #include <algorithm>
 #include <cmath>
@@ -23,16 +25,26 @@
 namespace gbg {
 namespace {
 
-constexpr int kIn = 8, kH = 64, kOut = GBGEMM_NUM_CONFIGS;
-constexpr int oW1 = 0, oB1 = oW1 + kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH,
-              oB3 = oW3 + kOut * kH, kParams = oB3 + kOut;
-static_assert(kParams == GBGEMM_MLP_PARAMS, "parameter count");
+constexpr int kIn = 8, kH = 64;
+constexpr int oW1 = 0, oB1 = oW1 + kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH;
+// Layout of a network with OUT outputs (the hidden layers are the same for every OUT).
+template <int OUT>
+struct Net {
+  static constexpr int kOut = OUT;
+  static constexpr int oB3 = oW3 + OUT * kH;
+  static constexpr int kParams = oB3 + OUT;
+  static constexpr int kLegalBytes = (OUT + 7) / 8;  // legal-mask bytes per sample
+};
+static_assert(Net<GBGEMM_NUM_CONFIGS>::kParams == GBGEMM_MLP_PARAMS, "parameter count");
+static_assert(Net<GBGEMM_NUM_SCHEDULES>::kParams == GBGEMM_SCHED_MLP_PARAMS, "parameter count");
 constexpr int kTrainBatch = 256;  // samples per mini-batch = threads of the training kernel
 
 // Forward pass of one sample held by one thread; writes h1, h2 (post-ReLU)
 // and the outputs.
+template <int OUT>
 __device__ __forceinline__ void forward_one(const float* __restrict__ P, const float* x, float* h1, float* h2,
                                             float* out) {
+  constexpr int kOut = OUT, oB3 = Net<OUT>::oB3;
   for (int j = 0; j < kH; ++j) {
     float a = P[oB1 + j];
 #pragma unroll
@@ -53,9 +65,12 @@ __device__ __forceinline__ void forward_one(const float* __restrict__ P, const f
 
 // Batched inference: scores (optional) and the masked argmin per sample
 // (ties to the lower configuration index; -1 when no configuration is legal).
+// legal: kLegalBytes bytes per sample, bit c % 8 of byte c / 8 for output c.
+template <int OUT>
 __global__ void mlp_predict_kernel(const float* __restrict__ P, const float* __restrict__ X,
                                    const uint8_t* __restrict__ legal, int64_t n, float* __restrict__ scores,
                                    int* __restrict__ configs) {
+  constexpr int kOut = OUT, kParams = Net<OUT>::kParams, kLB = Net<OUT>::kLegalBytes;
   __shared__ float sp[kParams];
   for (int i = threadIdx.x; i < kParams; i += blockDim.x) sp[i] = P[i];
   __syncthreads();
@@ -63,11 +78,11 @@ __global__ void mlp_predict_kernel(const float* __restrict__ P, const float* __r
     float x[kIn], h1[kH], h2[kH], out[kOut];
 #pragma unroll
     for (int i = 0; i < kIn; ++i) x[i] = X[s * kIn + i];
-    forward_one(sp, x, h1, h2, out);
+    forward_one<OUT>(sp, x, h1, h2, out);
     int best = -1;
     for (int c = 0; c < kOut; ++c) {
       if (scores) scores[s * kOut + c] = out[c];
-      if (legal && !((legal[s] >> c) & 1)) continue;
+      if (legal && !((legal[s * kLB + (c >> 3)] >> (c & 7)) & 1)) continue;
       if (best < 0 || out[c] < out[best]) best = c;
     }
     if (configs) configs[s] = best;
@@ -77,10 +92,12 @@ __global__ void mlp_predict_kernel(const float* __restrict__ P, const float* __r
 // One mini-batch (up to kTrainBatch samples, one thread each): forward,
 // masked MSE, backward; writes the gradient of the mean loss into G and the
 // loss sum / legal count into loss2[0..1].
+template <int OUT>
 __global__ void __launch_bounds__(kTrainBatch) mlp_grad_kernel(const float* __restrict__ P, const float* __restrict__ X,
                                                               const float* __restrict__ Y, const float* __restrict__ M,
                                                               const int* __restrict__ idx, int nb,
                                                               float* __restrict__ G, float* __restrict__ loss2) {
+  constexpr int kOut = OUT, kParams = Net<OUT>::kParams, oB3 = Net<OUT>::oB3;
   extern __shared__ float sm[];
   float* sp = sm;                                  // kParams
   float* sh1 = sp + kParams;                       // [nb][kH]
@@ -98,7 +115,7 @@ __global__ void __launch_bounds__(kTrainBatch) mlp_grad_kernel(const float* __re
     float x[kIn], out[kOut];
 #pragma unroll
     for (int i = 0; i < kIn; ++i) { x[i] = X[(int64_t)s * kIn + i]; sx[t * kIn + i] = x[i]; }
-    forward_one(sp, x, sh1 + t * kH, sh2 + t * kH, out);
+    forward_one<OUT>(sp, x, sh1 + t * kH, sh2 + t * kH, out);
     for (int c = 0; c < kOut; ++c) {
       const float m = M[(int64_t)s * kOut + c];
       const float d = (out[c] - Y[(int64_t)s * kOut + c]) * m;
@@ -202,8 +219,35 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
   P[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
 }
 
+template <int OUT>
 constexpr size_t grad_smem_bytes() {
-  return (size_t)(kParams + 2 * kTrainBatch * kH + kTrainBatch * kOut + kTrainBatch * kIn) * sizeof(float);
+  return (size_t)(Net<OUT>::kParams + 2 * kTrainBatch * kH + kTrainBatch * OUT + kTrainBatch * kIn) * sizeof(float);
+}
+
+// The shared-memory opt-in of the training kernel, once per process and OUT.
+template <int OUT>
+cudaError_t ensure_grad_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)grad_smem_bytes<OUT>());
+  done = e == cudaSuccess;
+  return e;
+}
+
+// He-uniform initialisation (zero biases) of a network with OUT outputs.
+template <int OUT>
+std::vector<float> he_init(std::mt19937_64& rng) {
+  std::vector<float> p(Net<OUT>::kParams, 0.f);
+  auto init = [&](int off, int fan_out, int fan_in) {
+    const double b = std::sqrt(6.0 / fan_in);
+    std::uniform_real_distribution<double> u(-b, b);
+    for (int i = 0; i < fan_out * fan_in; ++i) p[off + i] = (float)u(rng);
+  };
+  init(oW1, kH, kIn);
+  init(oW2, kH, kH);
+  init(oW3, OUT, kH);
+  return p;
 }
 
 }  // namespace
@@ -223,53 +267,24 @@ void predictor_features(const gbgemm_problem& q, float* x) {
   x[7] = al(q.ldc, q.C);
 }
 
-Predictor::~Predictor() {
-  if (dparams_) cudaFree(dparams_);
-}
+namespace {
 
-int Predictor::set(const float* host_params) {
-  if (!dparams_ && cudaMalloc(&dparams_, kParams * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
-    dparams_ = nullptr;
-    return GBGEMM_ERR_ALLOC;
-  }
-  if (cudaMemcpy(dparams_, host_params, kParams * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
-    return GBGEMM_ERR_CUDA;
-  ready_ = true;
-  return GBGEMM_OK;
-}
-
-int Predictor::get(float* host_params) const {
-  if (!ready_) return GBGEMM_ERR_NOT_INITIALIZED;
-  return cudaMemcpy(host_params, dparams_, kParams * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess
-             ? GBGEMM_OK
-             : GBGEMM_ERR_CUDA;
-}
-
-int Predictor::predict(const float* dx, const uint8_t* dlegal, int64_t n, float* dscores, int* dconfigs,
-                       cudaStream_t s) const {
-  if (!ready_) return GBGEMM_ERR_NOT_INITIALIZED;
-  if (n <= 0) return GBGEMM_OK;
+template <int OUT>
+int predict_impl(const float* P, const float* dx, const uint8_t* dlegal, int64_t n, float* dscores, int* dconfigs,
+                 cudaStream_t s) {
   const int64_t blocks = (n + 127) / 128;
-  mlp_predict_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 128, 0, s>>>(dparams_, dx, dlegal, n, dscores,
-                                                                              dconfigs);
+  mlp_predict_kernel<OUT><<<(unsigned)(blocks < 1024 ? blocks : 1024), 128, 0, s>>>(P, dx, dlegal, n, dscores,
+                                                                                   dconfigs);
   return cudaGetLastError() == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
 }
 
-int Predictor::loss_grad(const float* dx, const float* dy, const float* dmask, int64_t n, float* host_loss,
-                         float* dgrad, cudaStream_t s) const {
-  if (!ready_) return GBGEMM_ERR_NOT_INITIALIZED;
-  if (n <= 0 || n > kTrainBatch) return GBGEMM_ERR_INVALID_VALUE;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem_bytes()) !=
-        cudaSuccess)
-      return GBGEMM_ERR_CUDA;
-    attr = true;
-  }
+template <int OUT>
+int loss_grad_impl(const float* P, const float* dx, const float* dy, const float* dmask, int64_t n, float* host_loss,
+                   float* dgrad, cudaStream_t s) {
+  if (ensure_grad_attr<OUT>() != cudaSuccess) return GBGEMM_ERR_CUDA;
   float* dl = nullptr;
   if (cudaMalloc(&dl, 2 * sizeof(float)) != cudaSuccess) return GBGEMM_ERR_ALLOC;
-  mlp_grad_kernel<<<1, kTrainBatch, grad_smem_bytes(), s>>>(dparams_, dx, dy, dmask, nullptr, (int)n, dgrad, dl);
+  mlp_grad_kernel<OUT><<<1, kTrainBatch, grad_smem_bytes<OUT>(), s>>>(P, dx, dy, dmask, nullptr, (int)n, dgrad, dl);
   float l2[2] = {0.f, 0.f};
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(l2, dl, sizeof(l2), cudaMemcpyDeviceToHost, s);
@@ -280,32 +295,12 @@ int Predictor::loss_grad(const float* dx, const float* dy, const float* dmask, i
   return GBGEMM_OK;
 }
 
-int Predictor::train(const float* dx, const float* dy, const float* dmask, int64_t n, int epochs, int batch, float lr,
-                     uint64_t seed, float* host_loss, cudaStream_t s) {
-  if (n <= 0 || epochs < 1 || batch < 1 || batch > kTrainBatch || !(lr > 0.f)) return GBGEMM_ERR_INVALID_VALUE;
-  if (n > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
-  std::mt19937_64 rng(seed);
-  if (!ready_) {
-    // He-uniform initialisation, zero biases.
-    std::vector<float> p(kParams, 0.f);
-    auto init = [&](int off, int fan_out, int fan_in) {
-      const double b = std::sqrt(6.0 / fan_in);
-      std::uniform_real_distribution<double> u(-b, b);
-      for (int i = 0; i < fan_out * fan_in; ++i) p[off + i] = (float)u(rng);
-    };
-    init(oW1, kH, kIn);
-    init(oW2, kH, kH);
-    init(oW3, kOut, kH);
-    const int rc = set(p.data());
-    if (rc != GBGEMM_OK) return rc;
-  }
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem_bytes()) !=
-        cudaSuccess)
-      return GBGEMM_ERR_CUDA;
-    attr = true;
-  }
+// Adam on mini-batches from the parameters at P (updated in place).
+template <int OUT>
+int train_impl(float* P, const float* dx, const float* dy, const float* dmask, int64_t n, int epochs, int batch,
+               float lr, std::mt19937_64& rng, float* host_loss, cudaStream_t s) {
+  constexpr int kParams = Net<OUT>::kParams;
+  if (ensure_grad_attr<OUT>() != cudaSuccess) return GBGEMM_ERR_CUDA;
   // work buffers: gradient, Adam moments, epoch permutation, loss
   float* work = nullptr;
   const size_t nperm = (size_t)n;
@@ -327,10 +322,10 @@ int Predictor::train(const float* dx, const float* dy, const float* dmask, int64
     e = cudaMemcpyAsync(perm, hp.data(), nperm * sizeof(int), cudaMemcpyHostToDevice, s);
     for (int64_t b0 = 0; b0 < n && e == cudaSuccess; b0 += batch) {
       const int nb = (int)((n - b0) < batch ? (n - b0) : batch);
-      mlp_grad_kernel<<<1, kTrainBatch, grad_smem_bytes(), s>>>(dparams_, dx, dy, dmask, perm + b0, nb, G, dl);
+      mlp_grad_kernel<OUT><<<1, kTrainBatch, grad_smem_bytes<OUT>(), s>>>(P, dx, dy, dmask, perm + b0, nb, G, dl);
       ++step;
       const float c1 = 1.f - (float)std::pow(b1, (double)step), c2 = 1.f - (float)std::pow(b2, (double)step);
-      adam_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(dparams_, G, m1, m2, kParams, lr, b1, b2, eps, c1, c2);
+      adam_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(P, G, m1, m2, kParams, lr, b1, b2, eps, c1, c2);
       e = cudaGetLastError();
     }
     // stream order keeps the host copy of the epoch permutation alive until use
@@ -344,7 +339,7 @@ int Predictor::train(const float* dx, const float* dy, const float* dmask, int64
       for (int i = 0; i < nb; ++i) hp[i] = (int)(b0 + i);
       e = cudaMemcpy(perm, hp.data(), nb * sizeof(int), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) break;
-      mlp_grad_kernel<<<1, kTrainBatch, grad_smem_bytes(), s>>>(dparams_, dx, dy, dmask, perm, nb, G, dl);
+      mlp_grad_kernel<OUT><<<1, kTrainBatch, grad_smem_bytes<OUT>(), s>>>(P, dx, dy, dmask, perm, nb, G, dl);
       float l2[2];
       e = cudaMemcpyAsync(l2, dl, sizeof(l2), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -360,6 +355,71 @@ int Predictor::train(const float* dx, const float* dy, const float* dmask, int64
   }
   if (host_loss) *host_loss = (float)last_epoch_loss;
   return GBGEMM_OK;
+}
+
+}  // namespace
+
+Predictor::Predictor(int outputs) : out_(outputs == GBGEMM_NUM_SCHEDULES ? GBGEMM_NUM_SCHEDULES : GBGEMM_NUM_CONFIGS) {}
+
+Predictor::~Predictor() {
+  if (dparams_) cudaFree(dparams_);
+}
+
+int Predictor::params() const {
+  return out_ == GBGEMM_NUM_SCHEDULES ? Net<GBGEMM_NUM_SCHEDULES>::kParams : Net<GBGEMM_NUM_CONFIGS>::kParams;
+}
+
+int Predictor::set(const float* host_params) {
+  const size_t bytes = (size_t)params() * sizeof(float);
+  if (!dparams_ && cudaMalloc(&dparams_, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    dparams_ = nullptr;
+    return GBGEMM_ERR_ALLOC;
+  }
+  if (cudaMemcpy(dparams_, host_params, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return GBGEMM_ERR_CUDA;
+  ready_ = true;
+  return GBGEMM_OK;
+}
+
+int Predictor::get(float* host_params) const {
+  if (!ready_) return GBGEMM_ERR_NOT_INITIALIZED;
+  return cudaMemcpy(host_params, dparams_, (size_t)params() * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess
+             ? GBGEMM_OK
+             : GBGEMM_ERR_CUDA;
+}
+
+int Predictor::predict(const float* dx, const uint8_t* dlegal, int64_t n, float* dscores, int* dconfigs,
+                       cudaStream_t s) const {
+  if (!ready_) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (n <= 0) return GBGEMM_OK;
+  return out_ == GBGEMM_NUM_SCHEDULES
+             ? predict_impl<GBGEMM_NUM_SCHEDULES>(dparams_, dx, dlegal, n, dscores, dconfigs, s)
+             : predict_impl<GBGEMM_NUM_CONFIGS>(dparams_, dx, dlegal, n, dscores, dconfigs, s);
+}
+
+int Predictor::loss_grad(const float* dx, const float* dy, const float* dmask, int64_t n, float* host_loss,
+                         float* dgrad, cudaStream_t s) const {
+  if (!ready_) return GBGEMM_ERR_NOT_INITIALIZED;
+  if (n <= 0 || n > kTrainBatch) return GBGEMM_ERR_INVALID_VALUE;
+  return out_ == GBGEMM_NUM_SCHEDULES
+             ? loss_grad_impl<GBGEMM_NUM_SCHEDULES>(dparams_, dx, dy, dmask, n, host_loss, dgrad, s)
+             : loss_grad_impl<GBGEMM_NUM_CONFIGS>(dparams_, dx, dy, dmask, n, host_loss, dgrad, s);
+}
+
+int Predictor::train(const float* dx, const float* dy, const float* dmask, int64_t n, int epochs, int batch, float lr,
+                     uint64_t seed, float* host_loss, cudaStream_t s) {
+  if (n <= 0 || epochs < 1 || batch < 1 || batch > kTrainBatch || !(lr > 0.f)) return GBGEMM_ERR_INVALID_VALUE;
+  if (n > 0x7FFFFFFF) return GBGEMM_ERR_INVALID_VALUE;
+  std::mt19937_64 rng(seed);
+  if (!ready_) {
+    const std::vector<float> p = out_ == GBGEMM_NUM_SCHEDULES ? he_init<GBGEMM_NUM_SCHEDULES>(rng)
+                                                              : he_init<GBGEMM_NUM_CONFIGS>(rng);
+    const int rc = set(p.data());
+    if (rc != GBGEMM_OK) return rc;
+  }
+  return out_ == GBGEMM_NUM_SCHEDULES
+             ? train_impl<GBGEMM_NUM_SCHEDULES>(dparams_, dx, dy, dmask, n, epochs, batch, lr, rng, host_loss, s)
+             : train_impl<GBGEMM_NUM_CONFIGS>(dparams_, dx, dy, dmask, n, epochs, batch, lr, rng, host_loss, s);
 }
 
 }  // namespace gbg

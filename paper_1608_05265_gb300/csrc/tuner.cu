@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,91 @@ int Tuner::ensure(size_t bytes) {
   return cudaGetLastError() == cudaSuccess ? GBGEMM_OK : GBGEMM_ERR_CUDA;
 }
 
+// Scratch operands with q0's shape, leading dimensions and 16-byte alignment
+// classes, followed by ws_bytes of split workspace.
+int Tuner::scratch(const gbgemm_problem& q0, size_t ws_bytes, gbgemm_problem* q, uint8_t** wsp) {
+  const int ta = (q0.transa == 'N' || q0.transa == 'n') ? 0 : 1;
+  const int tb = (q0.transb == 'N' || q0.transb == 'n') ? 0 : 1;
+  // scratch layout: A | B | C | split workspace (panels, maxima); same leading dimensions as the problem
+  const int64_t acols = ta ? q0.m : q0.k, bcols = tb ? q0.k : q0.n;
+  const size_t a_bytes = (size_t)q0.lda * std::max<int64_t>(acols, 1) * 4 + 16;
+  const size_t b_bytes = (size_t)q0.ldb * std::max<int64_t>(bcols, 1) * 4 + 16;
+  const size_t c_bytes = (size_t)q0.ldc * std::max<int64_t>(q0.n, 1) * 4 + 16;
+  auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  int rc = ensure(r256(a_bytes) + r256(b_bytes) + r256(c_bytes) + ws_bytes);
+  if (rc != GBGEMM_OK) return rc;
+  uint8_t* base = static_cast<uint8_t*>(buf_);
+  // keep the problem's 16-byte alignment class
+  const size_t aoff = (reinterpret_cast<uintptr_t>(q0.A) & 15), boff = (reinterpret_cast<uintptr_t>(q0.B) & 15);
+  const size_t coff = (reinterpret_cast<uintptr_t>(q0.C) & 15);
+  *q = q0;
+  q->A = reinterpret_cast<const float*>(base + aoff);
+  q->B = reinterpret_cast<const float*>(base + r256(a_bytes) + boff);
+  q->C = reinterpret_cast<float*>(base + r256(a_bytes) + r256(b_bytes) + coff);
+  *wsp = base + r256(a_bytes) + r256(b_bytes) + r256(c_bytes);
+  return GBGEMM_OK;
+}
+
+// Median of `reps` CUDA-event timings of run() after one warm-up, in us.
+int Tuner::time_us(const std::function<cudaError_t()>& run, int reps, float* us) {
+  if (run() != cudaSuccess) return GBGEMM_ERR_CUDA;  // warm-up
+  std::vector<float> t;
+  for (int r = 0; r < std::max(reps, 1); ++r) {
+    if (cudaEventRecord(e0_, stream_) != cudaSuccess || run() != cudaSuccess || cudaEventRecord(e1_, stream_) != cudaSuccess ||
+        cudaEventSynchronize(e1_) != cudaSuccess)
+      return GBGEMM_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0_, e1_);
+    t.push_back(ms * 1000.f);
+  }
+  std::sort(t.begin(), t.end());
+  *us = t[t.size() / 2];
+  return GBGEMM_OK;
+}
+
+int Tuner::measure_schedules(const gbgemm_problem& q0, int reps, std::vector<float>* out) {
+  const std::string key = tune_key(q0);
+  auto it = sched_cache.find(key);
+  if (it != sched_cache.end()) {
+    *out = it->second;
+    return GBGEMM_OK;
+  }
+  const int ta = (q0.transa == 'N' || q0.transa == 'n') ? 0 : 1;
+  const int tb = (q0.transb == 'N' || q0.transb == 'n') ? 0 : 1;
+  size_t ws = 0;  // the largest split workspace of the legal schedules
+  for (int sc = 0; sc < GBGEMM_NUM_SCHEDULES; ++sc) {
+    Schedule d;
+    schedule_decode(sc, &d);
+    if (d.path == GBGEMM_PATH_SPLIT_BF16 && schedule_legal(q0.m, q0.n, q0.k, q0.alpha, sc, num_sms_))
+      ws = std::max(ws, split_layout(q0.m, q0.n, q0.k, 1, d.splitk, d.bn).total);
+  }
+  gbgemm_problem q;
+  uint8_t* wsp = nullptr;
+  int rc = scratch(q0, ws, &q, &wsp);
+  if (rc != GBGEMM_OK) return rc;
+  Problem p{ta, tb, q.m, q.n, q.k, 1.0f, 0.0f, q.A, q.lda, q.B, q.ldb, q.C, q.ldc};
+  std::vector<float> lat((size_t)GBGEMM_NUM_SCHEDULES, -1.f);
+  for (int sc = 0; sc < GBGEMM_NUM_SCHEDULES; ++sc) {
+    if (!schedule_legal(q.m, q.n, q.k, q.alpha, sc, num_sms_)) continue;
+    Schedule d;
+    schedule_decode(sc, &d);
+    auto run = [&]() -> cudaError_t {
+      if (d.path == GBGEMM_PATH_SIMT) return launch_simt(p, d.simt_cfg, stream_);
+      SplitCall c;
+      c.ta = ta; c.tb = tb; c.m = q.m; c.n = q.n; c.k = q.k; c.alpha = 1.0f; c.beta = 0.0f;
+      c.A = q.A; c.lda = q.lda; c.B = q.B; c.ldb = q.ldb; c.C = q.C; c.ldc = q.ldc;
+      c.bn = d.bn; c.raster = d.raster; c.splitk = d.splitk;
+      c.ws = wsp; c.status = status_; c.num_sms = num_sms_;
+      return launch_split_call(c, stream_);
+    };
+    rc = time_us(run, reps, &lat[(size_t)sc]);
+    if (rc != GBGEMM_OK) return rc;
+  }
+  sched_cache[key] = lat;
+  *out = lat;
+  return GBGEMM_OK;
+}
+
 int Tuner::measure(const gbgemm_problem& q0, int reps, TuneResult* out) {
   const std::string key = tune_key(q0);
   auto it = cache.find(key);
@@ -104,27 +190,16 @@ int Tuner::measure(const gbgemm_problem& q0, int reps, TuneResult* out) {
   }
   const int ta = (q0.transa == 'N' || q0.transa == 'n') ? 0 : 1;
   const int tb = (q0.transb == 'N' || q0.transb == 'n') ? 0 : 1;
-  // scratch layout: A | B | C | split workspace (panels, maxima); same leading dimensions as the problem
-  const int64_t acols = ta ? q0.m : q0.k, bcols = tb ? q0.k : q0.n;
-  const size_t a_bytes = (size_t)q0.lda * std::max<int64_t>(acols, 1) * 4 + 16;
-  const size_t b_bytes = (size_t)q0.ldb * std::max<int64_t>(bcols, 1) * 4 + 16;
-  const size_t c_bytes = (size_t)q0.ldc * std::max<int64_t>(q0.n, 1) * 4 + 16;
   size_t ws = 0;  // the largest split workspace of the three tile widths
   for (int bn : {64, 128, 256}) ws = std::max(ws, split_layout(q0.m, q0.n, q0.k, 1, 1, bn).total);
-  auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
-  int rc = ensure(r256(a_bytes) + r256(b_bytes) + r256(c_bytes) + ws);
+  gbgemm_problem q;
+  uint8_t* wsp = nullptr;
+  int rc = scratch(q0, ws, &q, &wsp);
   if (rc != GBGEMM_OK) return rc;
-  uint8_t* base = static_cast<uint8_t*>(buf_);
-  // keep the problem's 16-byte alignment class
-  const size_t aoff = (reinterpret_cast<uintptr_t>(q0.A) & 15), boff = (reinterpret_cast<uintptr_t>(q0.B) & 15);
-  const size_t coff = (reinterpret_cast<uintptr_t>(q0.C) & 15);
-  const float* A = reinterpret_cast<const float*>(base + aoff);
-  const float* B = reinterpret_cast<const float*>(base + r256(a_bytes) + boff);
-  float* C = reinterpret_cast<float*>(base + r256(a_bytes) + r256(b_bytes) + coff);
-  uint8_t* wsp = base + r256(a_bytes) + r256(b_bytes) + r256(c_bytes);
+  const float* A = q.A;
+  const float* B = q.B;
+  float* C = q.C;
   Problem p{ta, tb, q0.m, q0.n, q0.k, 1.0f, 0.0f, A, q0.lda, B, q0.ldb, C, q0.ldc};
-  gbgemm_problem q = q0;
-  q.A = A; q.B = B; q.C = C;
 
   TuneResult res;
   for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c) { res.latency_us[c] = -1.f; res.cost_us[c] = -1.f; }
@@ -140,18 +215,8 @@ int Tuner::measure(const gbgemm_problem& q0, int reps, TuneResult* out) {
       sc.ws = wsp; sc.status = status_; sc.num_sms = num_sms_;
       return launch_split_call(sc, stream_);
     };
-    if (run() != cudaSuccess) return GBGEMM_ERR_CUDA;  // warm-up
-    std::vector<float> t;
-    for (int r = 0; r < std::max(reps, 1); ++r) {
-      if (cudaEventRecord(e0_, stream_) != cudaSuccess || run() != cudaSuccess || cudaEventRecord(e1_, stream_) != cudaSuccess ||
-          cudaEventSynchronize(e1_) != cudaSuccess)
-        return GBGEMM_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0_, e1_);
-      t.push_back(ms * 1000.f);
-    }
-    std::sort(t.begin(), t.end());
-    res.latency_us[c] = t[t.size() / 2];
+    rc = time_us(run, reps, &res.latency_us[c]);
+    if (rc != GBGEMM_OK) return rc;
     // batch cost: replicas of the problem in one captured grouped plan
     const double slots = (double)num_sms_ * blocks_per_sm(c);
     const int64_t reps_in_batch =
@@ -211,6 +276,12 @@ int Tuner::save(const char* path) const {
     for (int c = 0; c < GBGEMM_NUM_CONFIGS; ++c) std::fprintf(f, " %.4f", kv.second.cost_us[c]);
     std::fprintf(f, "\n");
   }
+  // schedule latencies: "S key | latency_us x GBGEMM_NUM_SCHEDULES"
+  for (const auto& kv : sched_cache) {
+    std::fprintf(f, "S %s |", kv.first.c_str());
+    for (float v : kv.second) std::fprintf(f, " %.4f", v);
+    std::fprintf(f, "\n");
+  }
   std::fclose(f);
   return GBGEMM_OK;
 }
@@ -218,10 +289,28 @@ int Tuner::save(const char* path) const {
 int Tuner::load(const char* path) {
   FILE* f = std::fopen(path, "r");
   if (!f) return GBGEMM_ERR_INVALID_VALUE;
-  char line[512];
+  char line[1024];
   int rc = GBGEMM_OK;
   while (std::fgets(line, sizeof(line), f)) {
     if (line[0] == '#' || line[0] == '\n') continue;
+    if (line[0] == 'S' && line[1] == ' ') {
+      char* bar = std::strchr(line, '|');
+      if (!bar) { rc = GBGEMM_ERR_INVALID_VALUE; break; }
+      std::string key(line + 2, bar - line - 2);
+      while (!key.empty() && key.back() == ' ') key.pop_back();
+      std::vector<float> lat((size_t)GBGEMM_NUM_SCHEDULES);
+      bool ok = true;
+      char* sp = bar + 1;
+      for (int c = 0; c < GBGEMM_NUM_SCHEDULES && ok; ++c) {
+        char* end = nullptr;
+        lat[(size_t)c] = std::strtof(sp, &end);
+        ok = end != sp;
+        sp = end;
+      }
+      if (!ok) { rc = GBGEMM_ERR_INVALID_VALUE; break; }
+      sched_cache[key] = lat;
+      continue;
+    }
     char* bar = std::strchr(line, '|');
     char* bar2 = bar ? std::strchr(bar + 1, '|') : nullptr;
     if (!bar2) { rc = GBGEMM_ERR_INVALID_VALUE; break; }

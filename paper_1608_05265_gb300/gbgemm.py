@@ -29,6 +29,8 @@ ERR_INVALID_VALUE = -106
 ERR_SCRATCH_LIMIT = -107
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 MLP_PARAMS = 5126
+SCHED_MLP_PARAMS = 7271
+NUM_SCHEDULES = 39
 
 PATH_AUTO = 0
 PATH_SIMT = 1
@@ -69,6 +71,8 @@ EXPORTS = [
     "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
     "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
     "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error",
+    "gbgemm_schedule_info", "gbgemm_schedule_legal", "gbgemm_schedule_default", "gbgemm_autotune_schedules",
+    "gbgemm_last_schedule", "gbgemm_set_schedule", "gbgemm_predictor_select",
 ]
 
 _lock = threading.Lock()
@@ -140,6 +144,13 @@ def lib():
                                                  ctypes.c_uint64, fp]
             L.gbgemm_check_error.argtypes = [vp, c, c, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, vp, i64, i64,
                                              i64, i64, i64, ctypes.POINTER(ctypes.c_double)]
+            L.gbgemm_schedule_info.argtypes = [ctypes.c_int, ip, ip, ip, ip, ip]
+            L.gbgemm_schedule_legal.argtypes = [vp, PP, ctypes.c_int, ip]
+            L.gbgemm_schedule_default.argtypes = [vp, PP, ip]
+            L.gbgemm_autotune_schedules.argtypes = [vp, PP, ctypes.c_int, fp, ip]
+            L.gbgemm_last_schedule.argtypes = [vp, ip]
+            L.gbgemm_set_schedule.argtypes = [vp, ctypes.c_int]
+            L.gbgemm_predictor_select.argtypes = [vp, ctypes.c_int]
             L.gbgemm_profile_begin.argtypes = [vp]
             L.gbgemm_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                              ctypes.POINTER(i64)]
@@ -154,7 +165,10 @@ def lib():
                          "gbgemm_grouped_plan_destroy", "gbgemm_autotune", "gbgemm_tuning_save",
                          "gbgemm_tuning_load", "gbgemm_tuning_clear", "gbgemm_set_tuning", "gbgemm_predictor_set",
                          "gbgemm_predictor_get", "gbgemm_predictor_features", "gbgemm_predictor_predict",
-                         "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error"):
+                         "gbgemm_predictor_loss_grad", "gbgemm_predictor_train", "gbgemm_check_error",
+                         "gbgemm_schedule_info", "gbgemm_schedule_legal", "gbgemm_schedule_default",
+                         "gbgemm_autotune_schedules", "gbgemm_last_schedule", "gbgemm_set_schedule",
+                         "gbgemm_predictor_select"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -307,17 +321,53 @@ class Handle:
     def set_tuning(self, mode: int):
         _check("gbgemm_set_tuning", lib().gbgemm_set_tuning(self._h, int(mode)))
 
+    def predictor_select(self, which: int):
+        """0: the grouped configurations' network, 1: the single-call schedules' network."""
+        _check("gbgemm_predictor_select", lib().gbgemm_predictor_select(self._h, int(which)))
+        self._pred_sel = int(which)
+
+    def _pred_params(self) -> int:
+        return SCHED_MLP_PARAMS if getattr(self, "_pred_sel", 0) == 1 else MLP_PARAMS
+
     def predictor_set(self, params):
         import numpy as np
         arr = np.ascontiguousarray(params, dtype=np.float32)
-        assert arr.size == MLP_PARAMS
+        assert arr.size == self._pred_params()
         _check("gbgemm_predictor_set", lib().gbgemm_predictor_set(self._h, arr.ctypes.data))
 
     def predictor_get(self):
         import numpy as np
-        arr = np.zeros(MLP_PARAMS, dtype=np.float32)
+        arr = np.zeros(self._pred_params(), dtype=np.float32)
         _check("gbgemm_predictor_get", lib().gbgemm_predictor_get(self._h, arr.ctypes.data))
         return arr
+
+    def schedule_legal(self, prob: "Problem", s: int) -> bool:
+        v = ctypes.c_int()
+        _check("gbgemm_schedule_legal", lib().gbgemm_schedule_legal(self._h, ctypes.byref(prob), int(s),
+                                                                    ctypes.byref(v)))
+        return bool(v.value)
+
+    def schedule_default(self, prob: "Problem") -> int:
+        v = ctypes.c_int()
+        _check("gbgemm_schedule_default", lib().gbgemm_schedule_default(self._h, ctypes.byref(prob), ctypes.byref(v)))
+        return v.value
+
+    def autotune_schedules(self, prob: "Problem", reps: int = 3):
+        """(latency_us[39], best); -1 marks illegal schedules."""
+        lat = (ctypes.c_float * NUM_SCHEDULES)()
+        b = ctypes.c_int()
+        _check("gbgemm_autotune_schedules", lib().gbgemm_autotune_schedules(self._h, ctypes.byref(prob), int(reps),
+                                                                            lat, ctypes.byref(b)))
+        return list(lat), b.value
+
+    def set_schedule(self, s: int):
+        """Pin single-call schedule s (-1 unpins)."""
+        _check("gbgemm_set_schedule", lib().gbgemm_set_schedule(self._h, int(s)))
+
+    def last_schedule(self) -> int:
+        v = ctypes.c_int()
+        _check("gbgemm_last_schedule", lib().gbgemm_last_schedule(self._h, ctypes.byref(v)))
+        return v.value
 
     def predictor_predict(self, x, legal, scores=None, configs=None):
         """Device tensors: x (n x 8 float32), legal (n uint8); fills scores (n x 6) and configs (n int32)."""
@@ -446,3 +496,11 @@ def split_workspace_bytes(m, n, k) -> int:
 
 def panel_bytes(rows, k) -> int:
     return int(lib().gbgemm_panel_bytes(int(rows), int(k)))
+
+
+def schedule_info(s: int) -> dict:
+    """Decode single-call schedule s (host only): path, tile rows and columns, raster, k slices."""
+    v = [ctypes.c_int() for _ in range(5)]
+    _check("gbgemm_schedule_info", lib().gbgemm_schedule_info(int(s), *[ctypes.byref(x) for x in v]))
+    return {"path": v[0].value, "tile_m": v[1].value, "tile_n": v[2].value, "raster": v[3].value,
+            "splitk": v[4].value}

@@ -162,3 +162,24 @@ def test_no_cpu_fallback_without_gpu(L):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert L.gbgemm_create(ctypes.byref(h), 0) == gbgemm.ERR_CUDA
+
+
+def test_schedule_table(L):
+    # 3 SIMT schedules, then split schedules 3 + 12 b + 4 r + q (BN 64 << b, R in 1/4/16, S = 2^q)
+    seen = set()
+    for s in range(gbgemm.NUM_SCHEDULES):
+        d = gbgemm.schedule_info(s)
+        if s < 3:
+            assert d["path"] == gbgemm.PATH_SIMT and (d["tile_m"], d["tile_n"]) == [(128, 128), (64, 64), (128, 64)][s]
+            continue
+        b, r, q = (s - 3) // 12, ((s - 3) // 4) % 3, (s - 3) % 4
+        assert d == {"path": gbgemm.PATH_SPLIT_BF16, "tile_m": 128, "tile_n": 64 << b, "raster": (1, 4, 16)[r],
+                     "splitk": 1 << q}
+        seen.add((d["tile_n"], d["raster"], d["splitk"]))
+    assert len(seen) == 36 and gbgemm.NUM_SCHEDULES == 39
+    for bad in (-1, 39, 1000):
+        with pytest.raises(gbgemm.GbgemmError):
+            gbgemm.schedule_info(bad)
+    a = ctypes.c_void_p(16)
+    assert L.gbgemm_set_schedule(None, 3) == gbgemm.ERR_NOT_INITIALIZED
+    assert L.gbgemm_predictor_select(None, 1) == gbgemm.ERR_NOT_INITIALIZED

@@ -1,0 +1,141 @@
+"""GPU tests of single-call schedules (path, tile, tile order, split-K
+slices): the schedule tuner times exactly the legal schedules and picks the
+argmin; every legal schedule, pinned, gives oracle-correct results and is
+the one that ran; tuning modes 1 and 2 stay within the bound; the schedule
+network's kernels match the FP64 oracle; and the trained schedule predictor
+gains over the fixed heuristic on held-out shapes."""
+
+import numpy as np
+import pytest
+
+from oracle import mlp_ref as R
+from paper_1608_05265_gb300 import synth
+
+from gpu_util import check_full
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    import torch
+    from paper_1608_05265_gb300 import build, gbgemm
+    build.build()
+    hd = gbgemm.Handle(0)
+    hd.set_stream(torch.cuda.current_stream())
+    yield hd
+    hd.set_schedule(-1)
+    hd.set_tuning(0)
+    hd.close()
+
+
+SHAPES = [("N", "T", 300, 260, 640), ("T", "N", 520, 130, 1040), ("N", "N", 129, 257, 96), ("T", "T", 64, 700, 17)]
+
+
+def test_schedule_tuner_times_legal_schedules_only(h):
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    for (ta, tb, m, n, k) in SHAPES:
+        p = predictor.tuning_problem((ta, tb, m, n, k, 1, 0, 1))
+        lat, best = h.autotune_schedules(p, reps=2)
+        legal = [h.schedule_legal(p, s) for s in range(gbgemm.NUM_SCHEDULES)]
+        assert [x > 0 for x in lat] == legal
+        assert best == int(np.argmin([x if x > 0 else np.inf for x in lat]))
+        d = h.schedule_default(p)
+        assert legal[d]
+        for s in range(gbgemm.NUM_SCHEDULES):
+            info = gbgemm.schedule_info(s)
+            if info["splitk"] > 1:  # split-K needs two parts (k >= 512) and 4 chunks per slice
+                assert legal[s] == (k >= 512 and (k + 31) // 32 >= 4 * info["splitk"])
+            elif info["path"] == gbgemm.PATH_SPLIT_BF16:
+                assert legal[s] == (k >= 16)
+            else:
+                assert legal[s]
+
+
+def test_every_legal_schedule_pinned_is_correct(h):
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    h.set_path(gbgemm.PATH_AUTO)
+    try:
+        for i, (ta, tb, m, n, k) in enumerate(SHAPES[:3]):
+            A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 70 + i, ta, tb, m, n, k, pad=3)
+            p = predictor.tuning_problem((ta, tb, m, n, k, 1, 1, 1))
+            for s in range(gbgemm.NUM_SCHEDULES):
+                if not h.schedule_legal(p, s):
+                    continue
+                h.set_schedule(s)
+                check_full(h, gbgemm.PATH_AUTO, ta, tb, m, n, k, 1.5, A, lda, B, ldb, -0.25, C, ldc, nthreads=4)
+                assert h.last_schedule() == s, (s, h.last_schedule())
+    finally:
+        h.set_schedule(-1)
+
+
+def test_tuning_modes_stay_within_the_bound(h):
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    import os
+    for mode in (1, 2):
+        h.set_tuning(mode)
+        if mode == 2 and os.path.exists(predictor.DEFAULT_SCHED_WEIGHTS):
+            h.predictor_select(1)
+            h.predictor_set(predictor.load_weights(predictor.DEFAULT_SCHED_WEIGHTS, gbgemm.SCHED_MLP_PARAMS)[0])
+            h.predictor_select(0)
+        try:
+            for i, (ta, tb, m, n, k) in enumerate(SHAPES):
+                A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 80 + i, ta, tb, m, n, k, pad=1)
+                check_full(h, gbgemm.PATH_AUTO, ta, tb, m, n, k, -0.75, A, lda, B, ldb, 0.5, C, ldc, nthreads=4)
+                p = predictor.tuning_problem((ta, tb, m, n, k, 0, 0, 0))
+                assert h.schedule_legal(p, h.last_schedule())
+        finally:
+            h.set_tuning(0)
+
+
+def test_schedule_network_kernels_match_the_oracle(h):
+    import torch
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    h2 = gbgemm.Handle(0)
+    h2.set_stream(torch.cuda.current_stream())
+    h2.predictor_select(1)
+    rng = np.random.default_rng(11)
+    theta = rng.normal(0, 0.3, gbgemm.SCHED_MLP_PARAMS).astype(np.float32)
+    h2.predictor_set(theta)
+    X = rng.uniform(0, 1, (150, 8)).astype(np.float32)
+    y = rng.normal(0, 1, (150, gbgemm.NUM_SCHEDULES)).astype(np.float32)
+    M = (rng.uniform(0, 1, y.shape) < 0.6).astype(np.float32)
+    grad = torch.zeros(gbgemm.SCHED_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = h2.predictor_loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
+                                  torch.from_numpy(M).cuda(), grad)
+    L, g = R.loss_grad(theta.astype(np.float64), X, y, M)
+    assert abs(loss - L) <= 1e-4 * abs(L)
+    assert np.linalg.norm(grad.cpu().numpy() - g) <= 1e-4 * np.linalg.norm(g)
+    legal = predictor.legal_bytes(np.where(M > 0, 1.0, -1.0))
+    cfg, scores = predictor.predict(h2, X, legal, gbgemm.NUM_SCHEDULES)
+    out, _ = R.forward(theta.astype(np.float64), X)
+    assert np.allclose(scores, out, rtol=1e-4, atol=1e-4)
+    bits = [sum(1 << c for c in range(gbgemm.NUM_SCHEDULES) if M[s, c] > 0) for s in range(len(X))]
+    want = R.predict(theta.astype(np.float64), X, bits)
+    srt = np.sort(np.where(M > 0, out, np.inf), axis=1)
+    clear = (srt[:, 1] - srt[:, 0]) > 1e-4
+    assert np.array_equal(cfg[clear], want[clear])
+    h2.close()
+
+
+def test_trained_schedule_predictor_gains_over_the_heuristic(h):
+    """On 48 held-out shapes (seed 5, dimensions up to 4096), every legal
+    schedule is timed; the shipped schedule weights' choices must cost less,
+    in geometric mean, than the fixed heuristic's."""
+    import os
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    if not os.path.exists(predictor.DEFAULT_SCHED_WEIGHTS):
+        pytest.fail("trained schedule predictor weights are missing")
+    params, _ = predictor.load_weights(predictor.DEFAULT_SCHED_WEIGHTS, gbgemm.SCHED_MLP_PARAMS)
+    h.predictor_select(1)
+    try:
+        h.predictor_set(params)
+        shapes = predictor.shape_set(5, 48, hi=4096)
+        lat = predictor.label_schedules(h, shapes, reps=2)
+        choice, _ = predictor.predict(h, predictor.features(shapes), predictor.legal_bytes(lat), gbgemm.NUM_SCHEDULES)
+    finally:
+        h.predictor_select(0)
+    assert np.all(lat[np.arange(len(shapes)), choice] > 0)  # only legal schedules are chosen
+    learned = predictor.regret(lat, choice)
+    default = predictor.regret(lat, predictor.default_schedules(h, shapes))
+    assert learned["geomean_ratio"] < default["geomean_ratio"], (learned, default)

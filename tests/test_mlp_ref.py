@@ -98,3 +98,48 @@ def test_forward_of_a_hand_set_network():
     M[0, :2] = 1.0
     assert R.loss(theta, X, np.zeros((2, 6)), M) == (8.375 ** 2 + 6.75 ** 2) / 2
     assert list(R.predict(theta, X, np.array([0b111111, 0b111100]))) == [1, 2]
+
+
+def test_schedule_network_layout_and_hand_forward():
+    # The schedule network: the same hidden layers, 39 outputs (7271 parameters).
+    # The hand network's first six output rows placed in a 39-output vector
+    # give the same six outputs by hand; output 38 = b3[38] = -2 and output
+    # 20 = 2 h2[1] are set here, and the argmin over bits of a 39-bit mask.
+    p6 = R.unpack(hand_network())
+    p = {name: np.zeros(shape) for name, shape in R.sizes(39)}
+    for name in ("W1", "b1", "W2", "b2"):
+        p[name] = p6[name].copy()
+    p["W3"][:6] = p6["W3"]
+    p["b3"][:6] = p6["b3"]
+    p["W3"][20, 1] = 2.0
+    p["b3"][38] = -2.0
+    theta = R.pack(p)
+    assert theta.size == 7271 == R.N_HIDDEN_PARAMS + 39 * 65
+    assert R.n_outputs(theta) == 39
+    X = np.zeros((2, 8))
+    X[0, :3] = (1.0, 0.25, 2.0)
+    X[1, 2] = 0.5
+    out, _ = R.forward(theta, X)
+    assert out.shape == (2, 39)
+    assert np.array_equal(out[:, :6], [[8.375, -6.75, -0.5, 0.75, 0.0, 3.0], [2.875, -1.25, -0.5, 0.75, 0.0, 3.0]])
+    assert out[0, 20] == 1.5 and out[1, 20] == 1.5 and out[0, 38] == -2.0
+    full = (1 << 39) - 1
+    assert list(R.predict(theta, X, [full, full & ~(1 << 1) & ~(1 << 38)])) == [1, 2]
+    assert list(R.predict(theta, X, [1 << 38, 0])) == [38, -1]
+
+
+def test_schedule_network_gradient_matches_central_differences():
+    rng = np.random.default_rng(7)
+    n_par = R.N_HIDDEN_PARAMS + 39 * 65
+    theta = rng.normal(0, 0.4, n_par)
+    X = rng.uniform(0, 1, (17, R.N_IN))
+    Y = rng.normal(0, 1, (17, 39))
+    M = (rng.uniform(0, 1, (17, 39)) < 0.5).astype(np.float64)
+    L, g = R.loss_grad(theta, X, Y, M)
+    idx = np.concatenate([rng.choice(n_par, 200, replace=False), np.arange(n_par - 39, n_par)])
+    h = 1e-6
+    for i in idx:
+        tp = theta.copy(); tp[i] += h
+        tm = theta.copy(); tm[i] -= h
+        fd = (R.loss(tp, X, Y, M) - R.loss(tm, X, Y, M)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
