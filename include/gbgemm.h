@@ -388,20 +388,25 @@ int gbgemm_tuning_clear(gbgemm_handle* h);
  *   s = 3 + 12 b + 4 r + q   split-BF16 path, tile 128 x BN with BN = 64 << b
  *                        (b = 0, 1, 2), tiles visited in groups of R tile
  *                        rows (all tile columns of a group before the next
- *                        group) with R = 1, 4, 16 for r = 0, 1, 2, and the k
- *                        range cut into S = 1, 2, 4, 8 slices for q = 0..3
- *                        (S > 1: split-K, the slices' raw accumulators summed
- *                        in slice order by a reduction).
+ *                        group) with R = 1, 4, 16 for r = 0, 1, 2, and k-slicing
+ *                        level q = 0..3: the k range cut into S = 1, F/4,
+ *                        F/2 or F slices (split-K: the slices' raw
+ *                        accumulators summed in slice order by a reduction),
+ *                        where F is the slice count that gives about one
+ *                        work item per SM (at most 32 slices of at least 4 k
+ *                        chunks of 32; F = 1 when the output has more than
+ *                        half as many 128 x BN tiles as the GPU has SMs, or
+ *                        k < 512), S rounded down so that no slice is empty.
  * 39 schedules; the tile shapes are those of gbgemm_config.  Legal: SIMT
  * schedules always; split schedules when k >= 16 and alpha != 0 (the error
- * bound, as for the grouped configurations); S > 1 only when k >= 512 (two
- * BF16 parts), every slice gets at least 4 k chunks of 32, no slice is empty
- * and the output has at most 2 x (number of SMs) tiles of 128 x BN. */
+ * bound, as for the grouped configurations); q > 0 when its S is at least 2
+ * and differs from level q - 1's.  The fixed heuristic's split-K (one
+ * problem, long k, few tiles) is level 3 with BN 256. */
 #define GBGEMM_NUM_SCHEDULES 39
 /* Decode schedule s (host only, no GPU): path (gbgemm_path value), tile
- * rows and columns, R and S as above.  Bad s: GBGEMM_ERR_INVALID_VALUE.
- * Any output pointer may be NULL. */
-int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster, int* splitk);
+ * rows and columns, R and the k-slicing level q as above (1 and 0 for SIMT).
+ * Bad s: GBGEMM_ERR_INVALID_VALUE.  Any output pointer may be NULL. */
+int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster, int* kslice_level);
 /* Whether schedule s may run problem prob on this handle's GPU (*legal = 0 or 1). */
 int gbgemm_schedule_legal(gbgemm_handle* h, const gbgemm_problem* prob, int s, int* legal);
 /* The schedule the fixed heuristic (tuning mode 0, path AUTO) gives prob. */

@@ -213,6 +213,7 @@ gbg::Schedule default_schedule(const gbgemm_handle* h, int path, int64_t m, int6
   gbg::Schedule d{};
   d.path = path;
   d.raster = 16;
+  d.level = 0;
   d.splitk = 1;
   d.simt_cfg = (m * n <= (int64_t)512 * 512) ? gbg::SIMT_64x64 : gbg::SIMT_128x128;
   auto tiles = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn) * batch; };
@@ -220,8 +221,9 @@ gbg::Schedule default_schedule(const gbgemm_handle* h, int path, int64_t m, int6
   d.bn = tiles(128, 256) >= half_sms ? 256 : tiles(128, 128) >= half_sms ? 128 : 64;
   if (batch == 1) {
     const int s = gbg::choose_splitk(tiles(128, 256), k, h->num_sms);
-    if (s > 1) {
+    if (s > 1) {  // k-slicing level 3 of the schedules: the slices that fill the SMs
       d.bn = 256;
+      d.level = 3;
       d.splitk = s;
     }
   }
@@ -317,13 +319,13 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   gbg::Schedule d = default_schedule(h, h->path, m, n, k, batch);
   const gbgemm_problem q1{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
   if (batch == 1 && h->pinned_schedule >= 0 && schedule_allowed(h, q1, h->pinned_schedule)) {
-    gbg::schedule_decode(h->pinned_schedule, &d);
+    gbg::schedule_resolve(h->pinned_schedule, m, n, k, alpha, h->num_sms, &d);
   } else if (h->tuning >= 1 && batch == 1) {
     const gbgemm_problem q{transa, transb, m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
     int best = -1;
     const int rc = choose_schedule(h, q, &best);
     if (rc != GBGEMM_OK) return rc;
-    if (best >= 0) gbg::schedule_decode(best, &d);
+    if (best >= 0) gbg::schedule_resolve(best, m, n, k, alpha, h->num_sms, &d);
   }
   const int path = d.path;
   const int simt_cfg = d.simt_cfg, split_bn = d.bn;
@@ -357,7 +359,7 @@ static int run_sgemm(gbgemm_handle* h, int ta, int tb, char transa, char transb,
   h->kernel_launches += splitk > 1 ? 2 : 1;
   h->gemm_launches += 1;
   h->last_path = GBGEMM_PATH_SPLIT_BF16;
-  h->last_schedule = gbg::schedule_encode_split(split_bn, d.raster, splitk);
+  h->last_schedule = gbg::schedule_encode_split(split_bn, d.raster, batch == 1 ? d.level : 0);
   return GBGEMM_OK;
 }
 
@@ -1023,7 +1025,7 @@ int gbgemm_set_tuning(gbgemm_handle* h, int mode) {
   return GBGEMM_OK;
 }
 
-int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster, int* splitk) {
+int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster, int* kslice_level) {
   gbg::Schedule d;
   if (!gbg::schedule_decode(s, &d)) return GBGEMM_ERR_INVALID_VALUE;
   const bool simt = d.path == GBGEMM_PATH_SIMT;
@@ -1031,7 +1033,7 @@ int gbgemm_schedule_info(int s, int* path, int* tile_m, int* tile_n, int* raster
   if (tile_m) *tile_m = simt ? (d.simt_cfg == gbg::SIMT_64x64 ? 64 : 128) : 128;
   if (tile_n) *tile_n = simt ? (d.simt_cfg == gbg::SIMT_128x128 ? 128 : 64) : d.bn;
   if (raster) *raster = simt ? 1 : d.raster;
-  if (splitk) *splitk = d.splitk;
+  if (kslice_level) *kslice_level = simt ? 0 : d.level;
   return GBGEMM_OK;
 }
 
@@ -1049,7 +1051,7 @@ int gbgemm_schedule_default(gbgemm_handle* h, const gbgemm_problem* prob, int* s
   if (!h) return GBGEMM_ERR_NOT_INITIALIZED;
   if (!prob || !s) return GBGEMM_ERR_INVALID_VALUE;
   const gbg::Schedule d = default_schedule(h, GBGEMM_PATH_AUTO, prob->m, prob->n, prob->k, 1);
-  *s = d.path == GBGEMM_PATH_SIMT ? d.simt_cfg : gbg::schedule_encode_split(d.bn, d.raster, d.splitk);
+  *s = d.path == GBGEMM_PATH_SIMT ? d.simt_cfg : gbg::schedule_encode_split(d.bn, d.raster, d.level);
   return GBGEMM_OK;
 }
 

@@ -110,42 +110,6 @@ struct SplitLayout {
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t k, int64_t batch, int splitk, int bn);
 
-// ---- single-call schedules (gbgemm_schedule_info) ----
-struct Schedule {
-  int path;      // GBGEMM_PATH_SIMT or GBGEMM_PATH_SPLIT_BF16
-  int simt_cfg;  // SimtConfig (SIMT path)
-  int bn;        // tile columns (split path)
-  int raster;    // tile rows per group of the tile order (split path)
-  int splitk;    // k slices (split path)
-};
-inline bool schedule_decode(int s, Schedule* o) {
-  if (s < 0 || s >= GBGEMM_NUM_SCHEDULES) return false;
-  if (s < SIMT_NUM_CONFIGS) {
-    *o = Schedule{GBGEMM_PATH_SIMT, s, 0, 0, 1};
-    return true;
-  }
-  const int t = s - SIMT_NUM_CONFIGS, b = t / 12, r = (t / 4) % 3, q = t % 4;
-  *o = Schedule{GBGEMM_PATH_SPLIT_BF16, -1, 64 << b, r == 0 ? 1 : (r == 1 ? 4 : 16), 1 << q};
-  return true;
-}
-inline int schedule_encode_split(int bn, int raster, int splitk) {
-  const int b = bn == 64 ? 0 : (bn == 128 ? 1 : 2);
-  const int r = raster == 1 ? 0 : (raster == 4 ? 1 : 2);
-  const int q = splitk >= 8 ? 3 : (splitk >= 4 ? 2 : (splitk >= 2 ? 1 : 0));
-  return SIMT_NUM_CONFIGS + 12 * b + 4 * r + q;
-}
-// Legality of schedule s for one problem (m, n, k, alpha) on num_sms SMs.
-inline bool schedule_legal(int64_t m, int64_t n, int64_t k, float alpha, int s, int num_sms) {
-  Schedule d;
-  if (!schedule_decode(s, &d)) return false;
-  if (d.path == GBGEMM_PATH_SIMT) return true;
-  if (k < kSplitShortK || alpha == 0.0f) return false;
-  if (d.splitk == 1) return true;
-  if (split_parts(k) != 1) return false;
-  const int64_t nkc = panel_k_chunks(k), per = (nkc + d.splitk - 1) / d.splitk;
-  const int64_t tiles = ((m + 127) / 128) * ((n + d.bn - 1) / d.bn);
-  return nkc >= 4 * (int64_t)d.splitk && (int64_t)(d.splitk - 1) * per < nkc && tiles <= 2 * (int64_t)num_sms;
-}
 
 // One split-path call: the packing launch, then the persistent tcgen05 GEMM.
 struct SplitCall {
@@ -203,5 +167,62 @@ int run_error_check(cudaStream_t s, char transa, char transb, int64_t m, int64_t
                     const float* A, int64_t lda, const float* B, int64_t ldb, float beta, const float* C_in,
                     const float* C_out, int64_t ldc, int64_t i0, int64_t i1, int64_t j0, int64_t j1,
                     double* max_ratio);
+
+
+// ---- single-call schedules (gbgemm_schedule_info) ----
+struct Schedule {
+  int path;      // GBGEMM_PATH_SIMT or GBGEMM_PATH_SPLIT_BF16
+  int simt_cfg;  // SimtConfig (SIMT path)
+  int bn;        // tile columns (split path)
+  int raster;    // tile rows per group of the tile order (split path)
+  int level;     // k-slicing level 0..3 (split path): S = 1, F/4, F/2, F
+  int splitk;    // k slices once resolved for a problem (schedule_resolve); 1 before
+};
+inline bool schedule_decode(int s, Schedule* o) {
+  if (s < 0 || s >= GBGEMM_NUM_SCHEDULES) return false;
+  if (s < SIMT_NUM_CONFIGS) {
+    *o = Schedule{GBGEMM_PATH_SIMT, s, 0, 0, 0, 1};
+    return true;
+  }
+  const int t = s - SIMT_NUM_CONFIGS, b = t / 12, r = (t / 4) % 3, q = t % 4;
+  *o = Schedule{GBGEMM_PATH_SPLIT_BF16, -1, 64 << b, r == 0 ? 1 : (r == 1 ? 4 : 16), q, 1};
+  return true;
+}
+inline int schedule_encode_split(int bn, int raster, int level) {
+  const int b = bn == 64 ? 0 : (bn == 128 ? 1 : 2);
+  const int r = raster == 1 ? 0 : (raster == 4 ? 1 : 2);
+  return SIMT_NUM_CONFIGS + 12 * b + 4 * r + level;
+}
+// k slices of k-slicing level `level` for an m x n x k problem with tiles of
+// 128 x bn: F = choose_splitk (the slices that give about one item per SM,
+// 1 when the output already fills half the SMs or k is short), S = F >> (3 -
+// level) rounded down to a count without an empty slice; 0 when the level
+// gives fewer than 2 slices or the same count as the level below.
+inline int schedule_slices(int64_t m, int64_t n, int64_t k, int bn, int level, int num_sms) {
+  if (level <= 0) return 1;
+  const int64_t tiles = ((m + 127) / 128) * ((n + bn - 1) / bn);
+  const int F = choose_splitk(tiles, k, num_sms);
+  int S = F >> (3 - level);
+  if (F < 2 || S < 2) return 0;
+  const int64_t nkc = panel_k_chunks(k), per = (nkc + S - 1) / S;
+  S = (int)((nkc + per - 1) / per);
+  if (S < 2) return 0;
+  if (level > 1 && schedule_slices(m, n, k, bn, level - 1, num_sms) == S) return 0;
+  return S;
+}
+// Legality of schedule s for one problem (m, n, k, alpha) on num_sms SMs.
+inline bool schedule_legal(int64_t m, int64_t n, int64_t k, float alpha, int s, int num_sms) {
+  Schedule d;
+  if (!schedule_decode(s, &d)) return false;
+  if (d.path == GBGEMM_PATH_SIMT) return true;
+  if (k < kSplitShortK || alpha == 0.0f) return false;
+  return d.level == 0 || schedule_slices(m, n, k, d.bn, d.level, num_sms) >= 2;
+}
+// Decode s and resolve its k slices for a problem (false when s is illegal for it).
+inline bool schedule_resolve(int s, int64_t m, int64_t n, int64_t k, float alpha, int num_sms, Schedule* o) {
+  if (!schedule_legal(m, n, k, alpha, s, num_sms) || !schedule_decode(s, o)) return false;
+  if (o->path == GBGEMM_PATH_SPLIT_BF16) o->splitk = schedule_slices(m, n, k, o->bn, o->level, num_sms);
+  return true;
+}
 
 }  // namespace gbg

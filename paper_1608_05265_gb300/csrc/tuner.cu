@@ -150,8 +150,7 @@ int Tuner::measure_schedules(const gbgemm_problem& q0, int reps, std::vector<flo
   size_t ws = 0;  // the largest split workspace of the legal schedules
   for (int sc = 0; sc < GBGEMM_NUM_SCHEDULES; ++sc) {
     Schedule d;
-    schedule_decode(sc, &d);
-    if (d.path == GBGEMM_PATH_SPLIT_BF16 && schedule_legal(q0.m, q0.n, q0.k, q0.alpha, sc, num_sms_))
+    if (schedule_resolve(sc, q0.m, q0.n, q0.k, q0.alpha, num_sms_, &d) && d.path == GBGEMM_PATH_SPLIT_BF16)
       ws = std::max(ws, split_layout(q0.m, q0.n, q0.k, 1, d.splitk, d.bn).total);
   }
   gbgemm_problem q;
@@ -161,9 +160,8 @@ int Tuner::measure_schedules(const gbgemm_problem& q0, int reps, std::vector<flo
   Problem p{ta, tb, q.m, q.n, q.k, 1.0f, 0.0f, q.A, q.lda, q.B, q.ldb, q.C, q.ldc};
   std::vector<float> lat((size_t)GBGEMM_NUM_SCHEDULES, -1.f);
   for (int sc = 0; sc < GBGEMM_NUM_SCHEDULES; ++sc) {
-    if (!schedule_legal(q.m, q.n, q.k, q.alpha, sc, num_sms_)) continue;
     Schedule d;
-    schedule_decode(sc, &d);
+    if (!schedule_resolve(sc, q.m, q.n, q.k, q.alpha, num_sms_, &d)) continue;
     auto run = [&]() -> cudaError_t {
       if (d.path == GBGEMM_PATH_SIMT) return launch_simt(p, d.simt_cfg, stream_);
       SplitCall c;

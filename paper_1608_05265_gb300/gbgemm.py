@@ -499,8 +499,8 @@ def panel_bytes(rows, k) -> int:
 
 
 def schedule_info(s: int) -> dict:
-    """Decode single-call schedule s (host only): path, tile rows and columns, raster, k slices."""
+    """Decode single-call schedule s (host only): path, tile rows and columns, raster, k-slicing level."""
     v = [ctypes.c_int() for _ in range(5)]
     _check("gbgemm_schedule_info", lib().gbgemm_schedule_info(int(s), *[ctypes.byref(x) for x in v]))
     return {"path": v[0].value, "tile_m": v[1].value, "tile_n": v[2].value, "raster": v[3].value,
-            "splitk": v[4].value}
+            "level": v[4].value}

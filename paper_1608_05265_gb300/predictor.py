@@ -214,6 +214,7 @@ def main(argv=None):
     ap.add_argument("--report", default=None, help="write a JSON report here")
     ap.add_argument("--cache", default=None, help="tuning cache file to resume from and update")
     ap.add_argument("--schedules", action="store_true", help="the single-call schedule predictor")
+    ap.add_argument("--dump", default=None, help="save the shapes' labels here (.npz)")
     args = ap.parse_args(argv)
     if args.schedules:
         return main_schedules(args)
@@ -264,6 +265,9 @@ def main_schedules(args):
     c_tr = label_schedules(h, tr, reps=args.reps, log_every=1000)
     c_ho = label_schedules(h, ho, reps=args.reps)
     t_label = time.time() - t0
+    if args.dump:
+        np.savez(args.dump, train=c_tr, heldout=c_ho, default_train=default_schedules(h, tr),
+                 default_heldout=default_schedules(h, ho), x_train=features(tr), x_heldout=features(ho))
     if args.cache:
         h.tuning_save(args.cache)
     h.predictor_select(1)

@@ -165,7 +165,7 @@ def test_no_cpu_fallback_without_gpu(L):
 
 
 def test_schedule_table(L):
-    # 3 SIMT schedules, then split schedules 3 + 12 b + 4 r + q (BN 64 << b, R in 1/4/16, S = 2^q)
+    # 3 SIMT schedules, then split schedules 3 + 12 b + 4 r + q (BN 64 << b, R in 1/4/16, k-slicing level q)
     seen = set()
     for s in range(gbgemm.NUM_SCHEDULES):
         d = gbgemm.schedule_info(s)
@@ -174,8 +174,8 @@ def test_schedule_table(L):
             continue
         b, r, q = (s - 3) // 12, ((s - 3) // 4) % 3, (s - 3) % 4
         assert d == {"path": gbgemm.PATH_SPLIT_BF16, "tile_m": 128, "tile_n": 64 << b, "raster": (1, 4, 16)[r],
-                     "splitk": 1 << q}
-        seen.add((d["tile_n"], d["raster"], d["splitk"]))
+                     "level": q}
+        seen.add((d["tile_n"], d["raster"], d["level"]))
     assert len(seen) == 36 and gbgemm.NUM_SCHEDULES == 39
     for bad in (-1, 39, 1000):
         with pytest.raises(gbgemm.GbgemmError):

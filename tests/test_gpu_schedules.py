@@ -29,7 +29,8 @@ def h():
     hd.close()
 
 
-SHAPES = [("N", "T", 300, 260, 640), ("T", "N", 520, 130, 1040), ("N", "N", 129, 257, 96), ("T", "T", 64, 700, 17)]
+SHAPES = [("N", "T", 300, 260, 640), ("T", "N", 520, 130, 1040), ("N", "N", 129, 257, 96), ("T", "T", 64, 700, 17),
+          ("N", "N", 256, 512, 8192)]
 
 
 def test_schedule_tuner_times_legal_schedules_only(h):
@@ -44,12 +45,36 @@ def test_schedule_tuner_times_legal_schedules_only(h):
         assert legal[d]
         for s in range(gbgemm.NUM_SCHEDULES):
             info = gbgemm.schedule_info(s)
-            if info["splitk"] > 1:  # split-K needs two parts (k >= 512) and 4 chunks per slice
-                assert legal[s] == (k >= 512 and (k + 31) // 32 >= 4 * info["splitk"])
-            elif info["path"] == gbgemm.PATH_SPLIT_BF16:
+            if info["path"] == gbgemm.PATH_SIMT:
+                assert legal[s]
+            elif info["level"] == 0:
                 assert legal[s] == (k >= 16)
             else:
-                assert legal[s]
+                assert legal[s] == (slices(m, n, k, info["tile_n"], info["level"]) >= 2), (s, k)
+
+
+def slices(m, n, k, bn, level, sms=152):
+    """k slices of a k-slicing level, restated from the header's definition."""
+    def fill(tiles):
+        if k < 512 or tiles * 2 > sms:
+            return 1
+        nkc = (k + 31) // 32
+        f = min(sms // tiles, nkc // 4, 32)
+        if f < 2:
+            return 1
+        per = (nkc + f - 1) // f
+        return (nkc + per - 1) // per
+    tiles = ((m + 127) // 128) * ((n + bn - 1) // bn)
+    F = fill(tiles)
+    S = F >> (3 - level)
+    if F < 2 or S < 2:
+        return 0
+    nkc = (k + 31) // 32
+    per = (nkc + S - 1) // S
+    S = (nkc + per - 1) // per
+    if S < 2 or (level > 1 and slices(m, n, k, bn, level - 1, sms) == S):
+        return 0
+    return S
 
 
 def test_every_legal_schedule_pinned_is_correct(h):
@@ -119,9 +144,12 @@ def test_schedule_network_kernels_match_the_oracle(h):
 
 
 def test_trained_schedule_predictor_gains_over_the_heuristic(h):
-    """On 48 held-out shapes (seed 5, dimensions up to 4096), every legal
-    schedule is timed; the shipped schedule weights' choices must cost less,
-    in geometric mean, than the fixed heuristic's."""
+    """On 400 held-out shapes (seed 5, never seen in training; m, n, k
+    log-uniform in [8, 16384]), every legal schedule is timed (median of 3);
+    the shipped schedule weights' choices must cost less, in geometric mean,
+    than the fixed heuristic's.  (Small calls time with a few percent of
+    noise, so the set is large enough for the margin measured at training,
+    1.10 against 1.20 on 1000 shapes, to show.)"""
     import os
     from paper_1608_05265_gb300 import gbgemm, predictor
     if not os.path.exists(predictor.DEFAULT_SCHED_WEIGHTS):
@@ -130,8 +158,8 @@ def test_trained_schedule_predictor_gains_over_the_heuristic(h):
     h.predictor_select(1)
     try:
         h.predictor_set(params)
-        shapes = predictor.shape_set(5, 48, hi=4096)
-        lat = predictor.label_schedules(h, shapes, reps=2)
+        shapes = predictor.shape_set(5, 400)
+        lat = predictor.label_schedules(h, shapes, reps=3)
         choice, _ = predictor.predict(h, predictor.features(shapes), predictor.legal_bytes(lat), gbgemm.NUM_SCHEDULES)
     finally:
         h.predictor_select(0)
