@@ -287,30 +287,33 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end: pinned host buffers in, C back to the host, every step ----
     # Each step copies its A, B and C from pinned host memory, multiplies and
-    # reads C back.  Two device buffer sets let step i+1's host-to-device
+    # reads C back.  Three device buffer sets let step i+1's host-to-device
     # copies and step i-1's read-back run on copy streams while step i
     # multiplies: the throughput of a pipelined caller, every byte still moved.
     e2e_steps = max(4, min(args.steps, 12))
     h.set_path(gbgemm.PATH_SPLIT_BF16)
-    sets = [(A, B, C), (torch.empty_like(A), torch.empty_like(B), torch.empty_like(C))]
-    outs = [Cout_h, torch.empty_like(Cout_h).pin_memory()]
+    NSET = 3
+    sets = [(A, B, C)] + [(torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)) for _ in range(NSET - 1)]
+    outs = [Cout_h] + [torch.empty_like(Cout_h).pin_memory() for _ in range(NSET - 1)]
     h2d = [torch.cuda.Stream(device=dev) for _ in range(3)]  # one per input: several copy engines
     d2h = torch.cuda.Stream(device=dev)
-    ev_in = [[torch.cuda.Event() for _ in range(3)] for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_in = [[torch.cuda.Event() for _ in range(3)] for _ in range(NSET)]
+    ev_done = [torch.cuda.Event() for _ in range(NSET)]
+    ev_out = [torch.cuda.Event() for _ in range(NSET)]
     barrier()
     x0 = torch.cuda.Event(enable_timing=True)
     x1 = torch.cuda.Event(enable_timing=True)
     x0.record(stream)
     for hs in h2d:
         hs.wait_event(x0)
-    used = [False, False]
+    used = [False] * NSET
     for it in range(e2e_steps):
-        b = it % 2
-        for hs, dst, src, ev in zip(h2d, sets[b], (A_h, B_h, C_h), ev_in[b]):
+        b = it % NSET
+        for q, (hs, dst, src, ev) in enumerate(zip(h2d, sets[b], (A_h, B_h, C_h), ev_in[b])):
             if used[b]:
-                hs.wait_event(ev_out[b])  # the set's previous result has been read back
+                # A and B of the set may be overwritten once its previous sgemm is done;
+                # C only once that result has been read back
+                hs.wait_event(ev_out[b] if q == 2 else ev_done[b])
             with torch.cuda.stream(hs):
                 dst.copy_(src, non_blocking=True)
                 ev.record(hs)
@@ -329,7 +332,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = max_over_ranks(x0.elapsed_time(x1)) / e2e_steps
     e2e_value = world * flop / (e2e_ms * 1e-3) / 1e12
     assert h.get_device_status() == 0
-    assert np.isfinite(outs[0][:1000].numpy()).all() and np.isfinite(outs[1][:1000].numpy()).all()
+    assert all(np.isfinite(o[:1000].numpy()).all() for o in outs)
     del sets
 
     # ---- roofline of the dominant kernel (the tcgen05 GEMM) ----
@@ -373,7 +376,7 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": config(parallelism=f"replicas x{world}"),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * N * LD * 4,
                     "d2h_bytes_per_step": N * LD * 4, "steps": e2e_steps,
-                    "pipelining": "copies of step i+1 (in) and i-1 (out) overlap step i's sgemm; 2 buffer sets"},
+                    "pipelining": "copies of step i+1 (in) and i-1 (out) overlap step i's sgemm; 3 buffer sets"},
             "gpu_launches": launches,
             "roofline": roofline,
             "simt": {"value": simt_tflops, "unit": UNIT, "ms_per_step": simt_ms, "steps": simt_steps},
