@@ -475,6 +475,23 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  if (warp == kCpfWarp && (int)blockIdx.x < num_items) {
+    // While the packing runs: ask L2 for the C of the tile this CTA most
+    // likely takes first (CTA b usually draws item b), for short tiles with
+    // beta != 0 as below.  C is not written by the packing; a wrong guess
+    // only costs the prefetch.
+    const TileJob J = S.job((int)blockIdx.x);
+    if (J.beta != 0.f && !J.partial && J.nkc <= 16) {
+      const int64_t rows = (J.m - J.m0 < 128) ? J.m - J.m0 : 128;
+      const int64_t ncols = (J.n - J.n0 < J.bn) ? J.n - J.n0 : J.bn;
+      const float* c0 = J.C + J.m0 + J.n0 * J.ldc;
+      for (int64_t j = lane; j < ncols; j += 32) {
+        const char* col = reinterpret_cast<const char*>(c0 + j * J.ldc);
+        for (int64_t off = 0; off < rows * 4; off += 128) prefetch_l2(col + off);
+        prefetch_l2(col + rows * 4 - 4);
+      }
+    }
+  }
   // everything above overlaps the packing launch; the panels and maxima it
   // writes are read only from here on
   wait_prerequisite_grid();
