@@ -167,3 +167,16 @@ def test_trained_schedule_predictor_gains_over_the_heuristic(h):
     learned = predictor.regret(lat, choice)
     default = predictor.regret(lat, predictor.default_schedules(h, shapes))
     assert learned["geomean_ratio"] < default["geomean_ratio"], (learned, default)
+
+
+def test_schedule_cache_roundtrip(h, tmp_path):
+    from paper_1608_05265_gb300 import predictor
+    p = predictor.tuning_problem(("N", "T", 640, 320, 1024, 1, 1, 1))
+    first = h.autotune_schedules(p, reps=2)
+    path = str(tmp_path / "cache.txt")
+    h.tuning_save(path)
+    assert any(line.startswith("S ") for line in open(path))
+    h.tuning_clear()
+    h.tuning_load(path)
+    again = h.autotune_schedules(p, reps=2)  # served from the loaded cache
+    assert np.allclose(first[0], again[0], rtol=1e-4) and first[1] == again[1]
