@@ -180,3 +180,23 @@ def test_schedule_cache_roundtrip(h, tmp_path):
     h.tuning_load(path)
     again = h.autotune_schedules(p, reps=2)  # served from the loaded cache
     assert np.allclose(first[0], again[0], rtol=1e-4) and first[1] == again[1]
+
+
+def test_pinned_schedule_falls_back_where_illegal(h):
+    """A pinned schedule applies only where it is legal: a split-K level on a
+    short-k problem, or a split schedule with k < 16, leaves the call to the
+    tuning mode (here the fixed heuristic), still within the bound; strided
+    batches ignore it."""
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    h.set_path(gbgemm.PATH_AUTO)
+    s_splitk = 3 + 12 * 2 + 4 * 2 + 3  # BN 256, groups of 16 rows, k-slicing level 3
+    try:
+        for (ta, tb, m, n, k, s) in [("N", "N", 200, 180, 64, s_splitk), ("T", "N", 150, 90, 8, 35)]:
+            p = predictor.tuning_problem((ta, tb, m, n, k, 1, 1, 1))
+            assert not h.schedule_legal(p, s)
+            h.set_schedule(s)
+            A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 91, ta, tb, m, n, k, pad=2)
+            check_full(h, gbgemm.PATH_AUTO, ta, tb, m, n, k, 1.25, A, lda, B, ldb, 0.5, C, ldc)
+            assert h.last_schedule() != s and h.last_schedule() == h.schedule_default(p)
+    finally:
+        h.set_schedule(-1)
