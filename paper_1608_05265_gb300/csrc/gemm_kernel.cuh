@@ -53,6 +53,7 @@ constexpr int kStages = 4;                         // ring depth of the general 
 constexpr int kMaxBN = 256;
 constexpr int kNarrowStages = 6;                   // ring depth of the BN <= 128 instance
 constexpr int kNarrowBN = 128;
+constexpr int kPairStages = 6;                     // ring depth of the pair-tile instance (half the B rows per CTA)
 constexpr int kEpiWarps = 16;
 constexpr int kCpfWarp = 2 + kEpiWarps;            // the C prefetch warp
 constexpr int kGemmThreads = 32 * (kCpfWarp + 1);  // 19 warps, charged as 20: 96 registers per thread
@@ -68,10 +69,12 @@ constexpr uint32_t kHintNs = 20000u;
 // still in flight.
 constexpr uint64_t kDrainTimeoutNs = 4000000000ull;
 // Shared memory of a kernel instance: STAGES ring slots of one A block and
-// MAXBN B rows, barriers and the tile queue, 1024-byte alignment.  With tiles
-// of at most 128 columns the same memory holds a six-slot ring.
-template <int STAGES, int MAXBN>
-constexpr int gemm_smem_bytes() { return STAGES * (kBlockBytes + MAXBN * 128) + 1024 + 256; }
+// MAXBN B rows (MAXBN / 2 for pair tiles, whose CTAs hold half the B rows
+// each), barriers and the tile queue, 1024-byte alignment.  With tiles of at
+// most 128 columns the same memory holds a six-slot ring, and so it does for
+// pair tiles.
+template <int STAGES, int MAXBN, bool PAIR = false>
+constexpr int gemm_smem_bytes() { return STAGES * (kBlockBytes + (PAIR ? MAXBN / 2 : MAXBN) * 128) + 1024 + 256; }
 constexpr int kGemmSmemBytes = gemm_smem_bytes<kStages, kMaxBN>();
 
 // The dependent launch of a kernel started with programmatic stream
@@ -177,7 +180,12 @@ struct SingleSched {
   // of slice s, tile (tm, tn) at partial + ((s * tiles_m + tm) * tiles_n + tn) * 128 * bn
   int splitk, slice_chunks;
   float* partial;
-  __device__ __forceinline__ int num_items() const { return tiles_m * tiles_n * batch * splitk; }
+  // pair tiles (clusters of two CTAs, bn = 256, no split-K): item t is a
+  // 256 x 256 tile, tile rows 2 tm2 and 2 tm2 + 1 of pair row tm2
+  int pair;
+  __device__ __forceinline__ int num_items() const {
+    return pair ? ((tiles_m + 1) >> 1) * tiles_n * batch : tiles_m * tiles_n * batch * splitk;
+  }
   __device__ __forceinline__ TileJob job(int t) const {
     const int per = tiles_m * tiles_n;
     const int sl = t % splitk;
@@ -185,12 +193,29 @@ struct SingleSched {
     const int z = t / per;
     int tm, tn;
     tile_coords(t - z * per, tiles_m, tiles_n, raster, tm, tn);
+    return tile_job(z, tm, tn, sl, (int64_t)tn * bn);
+  }
+  // The half of pair tile t that CTA `rank` of the pair computes: tile row
+  // 2 tm2 + rank (the A panel has an even number of row blocks, so the odd
+  // row of a last, half-empty pair reads zero rows), and B rows
+  // [n0 + 128 rank, n0 + 128 rank + 128) for its share of the B operand.
+  // Pair rows go in groups of raster / 2, the same rows of C as the
+  // single-CTA groups of `raster` tile rows.
+  __device__ __forceinline__ TileJob job_pair(int t, int rank) const {
+    const int tiles_m2 = (tiles_m + 1) >> 1;
+    const int per = tiles_m2 * tiles_n;
+    const int z = t / per;
+    int tm2, tn;
+    tile_coords(t - z * per, tiles_m2, tiles_n, raster > 1 ? raster >> 1 : 1, tm2, tn);
+    return tile_job(z, 2 * tm2 + rank, tn, 0, (int64_t)tn * bn + 128 * rank);
+  }
+  __device__ __forceinline__ TileJob tile_job(int z, int tm, int tn, int sl, int64_t b_row0) const {
     const int kc0 = sl * slice_chunks;
     TileJob j;
     j.a_kstride = (size_t)rbA * kBlockBytes;
     j.b_kstride = (size_t)rbB * kBlockBytes;
     j.a_src = panelA + (size_t)z * ps + (size_t)tm * kBlockBytes + (size_t)kc0 * j.a_kstride;
-    j.b_src = panel_rows(panelB + (size_t)z * ps, (int64_t)tn * bn) + (size_t)kc0 * j.b_kstride;
+    j.b_src = panel_rows(panelB + (size_t)z * ps, b_row0) + (size_t)kc0 * j.b_kstride;
     j.nkc = (nkc - kc0 < slice_chunks) ? nkc - kc0 : slice_chunks;
     j.bn = bn;
     j.partial = splitk > 1 ? partial + ((size_t)(sl * tiles_m + tm) * tiles_n + tn) * 128 * bn : nullptr;
@@ -426,11 +451,24 @@ __global__ void __launch_bounds__(256, 4) pack_tasks_kernel(const Sched S) {
 
 // One CTA per SM.  Registers are handed out to whole groups of four warps,
 // so the 19 warps are charged as 20: 96 registers per thread.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
+//
+// PAIR: launched in clusters of two CTAs on two SMs, each pair computing
+// 256 x 256 tiles (SingleSched pair items) with tcgen05 MMAs of
+// cta_group::2.  Each CTA loads its own 128-row A block and half of the
+// tile's 256 B rows, so per SM a k chunk brings 32 KiB instead of 48 KiB and
+// the tensor cores read half as many B bytes from shared memory.  The even
+// CTA (rank 0) issues the MMAs for both; the odd CTA's warp 1 relays each
+// of its landed stages to rank 0's "full" barrier (which then counts two
+// arrivals), its epilogue warps release the accumulator on rank 0's
+// "accumulator empty" barrier (32 arrivals), and rank 0's commits arrive on
+// both CTAs' "empty" and "accumulator full" barriers.  Pairs take items in a
+// fixed order (cluster c: items c, c + clusters, ...), so both CTAs of a
+// pair walk the same tiles without exchanging indices.
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, bool PAIR = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   constexpr uint32_t A_BYTES = kBlockBytes;        // 128 rows x 128 B
-  constexpr uint32_t B_STAGE = MAXBN * 128;        // room for MAXBN rows x 128 B
+  constexpr uint32_t B_STAGE = (PAIR ? MAXBN / 2 : MAXBN) * 128;  // room for the B rows of a stage
   constexpr uint32_t kTmemCols = 2 * MAXBN;        // two accumulator buffers
   constexpr int kStages = STAGES;
   constexpr int kMaxBN = MAXBN;
@@ -456,10 +494,22 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_items = S.num_items();
+  // the CTA's rank in its pair (0: issues the MMAs), the pair's index and count
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
+  const int pair_id = PAIR ? (int)cluster_id_x() : 0;
+  const int num_pairs = PAIR ? (int)num_clusters_x() : 1;
+  auto job_of = [&](int t) -> TileJob {
+    if constexpr (PAIR) return S.job_pair(t, (int)crank);
+    else return S.job(t);
+  };
+  auto wait_bar = [&](uint32_t bar, uint32_t parity) -> bool {
+    return mbar_wait_hint(bar, parity, abort_flag, timeout_ns, kHintNs);
+  };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(accf_bar(b), 1); mbar_init(acce_bar(b), kEpiWarps); }
+    const uint32_t full_count = (PAIR && crank == 0u) ? 2u : 1u;  // rank 0: its own copies + the relay
+    for (int s = 0; s < kStages; ++s) { mbar_init(full_bar(s), full_count); mbar_init(empty_bar(s), 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(accf_bar(b), 1); mbar_init(acce_bar(b), (PAIR ? 2 : 1) * kEpiWarps); }
     mbar_init(drain_bar, 1);
     for (int s = 0; s < kTileQ; ++s) { mbar_init(tqf_bar(s), 1); mbar_init(tqe_bar(s), 2 + kEpiWarps); }
     *abort_flag = 0;
@@ -467,21 +517,31 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_holder)), "r"(kTmemCols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair allocates, together, the same columns in both
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                   ::"r"(smem_u32(tmem_holder)), "r"(kTmemCols) : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                   ::"r"(smem_u32(tmem_holder)), "r"(kTmemCols) : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  // a pair's barriers are initialised on both sides before either side uses the other's
+  if constexpr (PAIR) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
-  if (warp == kCpfWarp && (int)blockIdx.x < num_items) {
+  const int first_item = PAIR ? pair_id : (int)blockIdx.x;
+  if (warp == kCpfWarp && first_item < num_items) {
     // While the packing runs: ask L2 for the C of the tile this CTA most
     // likely takes first (CTA b usually draws item b), for short tiles with
     // beta != 0 as below.  C is not written by the packing; a wrong guess
     // only costs the prefetch.
-    const TileJob J = S.job((int)blockIdx.x);
-    if (J.beta != 0.f && !J.partial && J.nkc <= 16) {
+    const TileJob J = job_of(first_item);
+    if (J.beta != 0.f && !J.partial && J.nkc <= 16 && J.m0 < J.m) {
       const int64_t rows = (J.m - J.m0 < 128) ? J.m - J.m0 : 128;
       const int64_t ncols = (J.n - J.n0 < J.bn) ? J.n - J.n0 : J.bn;
       const float* c0 = J.C + J.m0 + J.n0 * J.ldc;
@@ -504,6 +564,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       uint32_t phase = 0;
       int tq = 0;
       uint32_t tqph = 0;
+      int next_item = first_item;
       int issued_phase[kStages];
       bool issued[kStages];
       for (int s = 0; s < kStages; ++s) { issued[s] = false; issued_phase[s] = 0; }
@@ -513,20 +574,26 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           raise_status(status, abort_flag);
           break;
         }
-        int t = atomicAdd(&S.ctl->tile_next, 1);
+        int t;
+        if constexpr (PAIR) {
+          t = next_item;  // a fixed order, the same in both CTAs of the pair
+          next_item += num_pairs;
+        } else {
+          t = atomicAdd(&S.ctl->tile_next, 1);
+        }
         if (t >= num_items || *abort_flag) t = -1;
         tile_q[tq] = t;
         mbar_arrive(tqf_bar(tq));
         if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
         if (t < 0) break;
-        const TileJob J = S.job(t);
-        const uint32_t b_bytes = (uint32_t)J.bn * 128u;
+        const TileJob J = job_of(t);
+        const uint32_t b_bytes = (uint32_t)(PAIR ? J.bn / 2 : J.bn) * 128u;
         // one ring slot per k chunk, and with three parts one more per pair
         // of chunks (the compact [lo3 | lo3] block, loaded with the even chunk)
         for (int kc = 0; kc < J.nkc && ok; ++kc) {
           const int nparts = (J.parts == 2 && (kc & 1) == 0) ? 2 : 1;
           for (int part = 0; part < nparts; ++part) {
-            if (!mbar_wait_hint(empty_bar(stage), phase ^ 1u, abort_flag, timeout_ns, kHintNs)) {
+            if (!wait_bar(empty_bar(stage), phase ^ 1u)) {
               raise_status(status, abort_flag);
               ok = false;
               break;
@@ -548,6 +615,50 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       volatile int never = 0;
       for (int s = 0; s < kStages; ++s)
         if (issued[s]) (void)mbar_wait(full_bar(s), (uint32_t)issued_phase[s], &never, kDrainTimeoutNs);
+      // With pairs, rank 0's MMA commits release this CTA's slots by arriving
+      // on its "empty" barriers: wait for the releases of the last fills, so
+      // that no such arrival is still on its way when the CTA exits.
+      if constexpr (PAIR) {
+        for (int i = 0; i < kStages; ++i) {
+          if (!wait_bar(empty_bar(stage), phase ^ 1u)) {
+            raise_status(status, abort_flag);
+            break;
+          }
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (PAIR && warp == 1 && crank != 0u) {
+    // ---------------- relay (odd CTA of a pair) ----------------
+    // Tell rank 0's MMA issuer, stage by stage, that this CTA's share of the
+    // stage has landed (rank 0's "full" barrier counts this arrival).
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int tq = 0;
+      uint32_t tqph = 0;
+      bool ok = true;
+      while (ok) {
+        if (!mbar_wait_hint(tqf_bar(tq), tqph, abort_flag, timeout_ns, kHintNs)) {
+          raise_status(status, abort_flag);
+          break;
+        }
+        const int t = tile_q[tq];
+        mbar_arrive(tqe_bar(tq));
+        if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
+        if (t < 0) break;
+        const TileJob J = job_of(t);
+        for (int kc = 0; kc < J.nkc; ++kc) {
+          if (!wait_bar(full_bar(stage), phase)) {
+            raise_status(status, abort_flag);
+            ok = false;
+            break;
+          }
+          mbar_arrive_remote(map_to_rank(full_bar(stage), 0u));
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -569,9 +680,9 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         mbar_arrive(tqe_bar(tq));
         if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
         if (t < 0) break;
-        const TileJob J = S.job(t);
-        const uint32_t idesc = make_idesc_bf16(128, J.bn);
-        if (!mbar_wait_hint(acce_bar(abuf), aphase ^ 1u, abort_flag, timeout_ns, kHintNs)) {
+        const TileJob J = job_of(t);
+        const uint32_t idesc = make_idesc_bf16(PAIR ? 256 : 128, J.bn);
+        if (!wait_bar(acce_bar(abuf), aphase ^ 1u)) {
           raise_status(status, abort_flag);
           break;
         }
@@ -583,7 +694,7 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           // an even chunk also brings the pair's [lo3 | lo3] slot
           const int s0 = stage;
           const uint32_t ph0 = phase;
-          if (!mbar_wait_hint(full_bar(s0), ph0, abort_flag, timeout_ns, kHintNs)) {
+          if (!wait_bar(full_bar(s0), ph0)) {
             raise_status(status, abort_flag);
             ok = false;
             break;
@@ -608,28 +719,42 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
             const uint64_t al = make_desc_sw128(a_addr + 64u + 32u * kk);
             const uint64_t bh = make_desc_sw128(b_addr + 32u * kk);
             const uint64_t bl = make_desc_sw128(b_addr + 64u + 32u * kk);
-            mma_bf16(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_bf16(d_tmem, ah, bl, idesc, 1u);
-            mma_bf16(d_tmem, al, bh, idesc, 1u);
-            if (J.parts == 2) {
-              // with three parts: hi*lo3 + mid*mid + lo3*hi (al, bl above are mid)
-              const uint64_t a3 = make_desc_sw128(a3_addr + 32u * kk);
-              const uint64_t b3 = make_desc_sw128(b3_addr + 32u * kk);
-              mma_bf16(d_tmem, ah, b3, idesc, 1u);
-              mma_bf16(d_tmem, al, bl, idesc, 1u);
-              mma_bf16(d_tmem, a3, bh, idesc, 1u);
+            if constexpr (PAIR) {
+              // pair tiles have two-part panels (k >= 512)
+              mma_bf16_pair(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              mma_bf16_pair(d_tmem, ah, bl, idesc, 1u);
+              mma_bf16_pair(d_tmem, al, bh, idesc, 1u);
+            } else {
+              mma_bf16(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              mma_bf16(d_tmem, ah, bl, idesc, 1u);
+              mma_bf16(d_tmem, al, bh, idesc, 1u);
+              if (J.parts == 2) {
+                // with three parts: hi*lo3 + mid*mid + lo3*hi (al, bl above are mid)
+                const uint64_t a3 = make_desc_sw128(a3_addr + 32u * kk);
+                const uint64_t b3 = make_desc_sw128(b3_addr + 32u * kk);
+                mma_bf16(d_tmem, ah, b3, idesc, 1u);
+                mma_bf16(d_tmem, al, bl, idesc, 1u);
+                mma_bf16(d_tmem, a3, bh, idesc, 1u);
+              }
             }
           }
-          mma_commit(empty_bar(s0));  // frees the slot once these MMAs have read it
-          if (J.parts == 2 && ((kc & 1) == 1 || kc == J.nkc - 1)) mma_commit(empty_bar(s1));
+          if constexpr (PAIR) {
+            mma_commit_pair(empty_bar(s0), 0x3);  // frees the slot in both CTAs once these MMAs have read it
+          } else {
+            mma_commit(empty_bar(s0));  // frees the slot once these MMAs have read it
+            if (J.parts == 2 && ((kc & 1) == 1 || kc == J.nkc - 1)) mma_commit(empty_bar(s1));
+          }
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
-        mma_commit(accf_bar(abuf));      // the tile's accumulator is complete
+        // the tile's accumulator is complete (with pairs: in both CTAs' TMEM)
+        if constexpr (PAIR) mma_commit_pair(accf_bar(abuf), 0x3);
+        else mma_commit(accf_bar(abuf));
         if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
       }
       // Wait until every MMA issued here has finished before TMEM is released.
-      mma_commit(drain_bar);
+      if constexpr (PAIR) mma_commit_pair(drain_bar, 0x1);
+      else mma_commit(drain_bar);
       volatile int never = 0;
       if (!mbar_wait(drain_bar, 0u, &never, kDrainTimeoutNs)) raise_status(status, abort_flag);
     }
@@ -659,8 +784,8 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         break;
       }
       if (t < 0) break;
-      const TileJob J = S.job(t);
-      if (lane == 0) ok = mbar_wait_hint(accf_bar(abuf), aphase, abort_flag, timeout_ns, kHintNs) ? 1 : 0;
+      const TileJob J = job_of(t);
+      if (lane == 0) ok = wait_bar(accf_bar(abuf), aphase) ? 1 : 0;
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
         if (lane == 0) raise_status(status, abort_flag);
@@ -735,7 +860,12 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acce_bar(abuf));
+      if (lane == 0) {
+        // the accumulator buffer is free again: rank 0's MMA issuer waits for
+        // both CTAs' epilogue warps of a pair
+        if (PAIR && crank != 0u) mbar_arrive_remote(map_to_rank(acce_bar(abuf), 0u));
+        else mbar_arrive(acce_bar(abuf));
+      }
       if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
     }
   } else if (warp == kCpfWarp) {
@@ -757,12 +887,12 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       t = __shfl_sync(0xFFFFFFFFu, t, 0);
       if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
       if (!ok || t < 0) break;
-      const TileJob J = S.job(t);
+      const TileJob J = job_of(t);
       // Only short tiles (k <= 512), whose epilogue rather than their MMAs
       // sets the pace, are prefetched: for long ones the C reads overlap the
       // next tile's MMAs anyway, and prefetching several 128 KB tiles ahead
       // would push the operand panels out of L2.
-      if (J.beta == 0.f || J.partial || J.nkc > 16) continue;
+      if (J.beta == 0.f || J.partial || J.nkc > 16 || J.m0 >= J.m) continue;
       const int64_t rows = (J.m - J.m0 < 128) ? J.m - J.m0 : 128;
       const int64_t ncols = (J.n - J.n0 < J.bn) ? J.n - J.n0 : J.bn;
       const float* c0 = J.C + J.m0 + J.n0 * J.ldc;
@@ -776,23 +906,30 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
 
   tc_fence_before();
   __syncthreads();
+  // a pair's CTAs leave together: rank 0's MMAs (which read the odd CTA's
+  // shared memory and write its TMEM) have completed, and no arrival on the
+  // other CTA's barriers is still to come
+  if constexpr (PAIR) cluster_sync_all();
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
   }
 }
 
 // The shared-memory opt-in is a per-device function attribute: set it once
 // for every device a kernel instance is launched on.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, bool PAIR = false>
 cudaError_t ensure_gemm_smem_attr() {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             gemm_smem_bytes<STAGES, MAXBN>());
+    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gemm_smem_bytes<STAGES, MAXBN, PAIR>());
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
@@ -817,6 +954,62 @@ cudaError_t launch_gemm_kernel(const Sched& S, int grid, int* status, cudaStream
   cfg.attrs = attr;
   cfg.numAttrs = dependent ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, split_gemm_kernel<Sched, STAGES, MAXBN>, S, status, (uint64_t)kTimeoutNs);
+}
+
+// The pair-tile instance: clusters of two CTAs.  How many pairs the GPU
+// holds at once (one CTA per SM; a pair needs two SMs of one cluster-capable
+// group) is asked once per device; 0 when clusters of two cannot run.
+template <class Sched>
+int gemm_pair_capacity() {
+  static int cap[64];
+  static bool known[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!known[dev]) {
+    int n = 0;
+    if (ensure_gemm_smem_attr<Sched, kPairStages, kMaxBN, true>() == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2);
+      cfg.blockDim = dim3(kGemmThreads);
+      cfg.dynamicSmemBytes = gemm_smem_bytes<kPairStages, kMaxBN, true>();
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<Sched, kPairStages, kMaxBN, true>, &cfg) != cudaSuccess)
+        n = 0;
+    }
+    (void)cudaGetLastError();  // a failed query leaves the pair instance unused, not an error
+    cap[dev] = n;
+    known[dev] = true;
+  }
+  return cap[dev];
+}
+
+// Launch `pairs` clusters of two CTAs of the pair-tile instance (S.pair set).
+template <class Sched>
+cudaError_t launch_gemm_kernel_pair(const Sched& S, int pairs, int* status, cudaStream_t s, bool dependent) {
+  cudaError_t e = ensure_gemm_smem_attr<Sched, kPairStages, kMaxBN, true>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  cfg.blockDim = dim3(kGemmThreads);
+  cfg.dynamicSmemBytes = gemm_smem_bytes<kPairStages, kMaxBN, true>();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<Sched, kPairStages, kMaxBN, true>, S, status,
+                            (uint64_t)kTimeoutNs);
 }
 
 }  // namespace

@@ -192,6 +192,7 @@ SingleSched make_single_sched(const SplitCall& c, const SplitLayout& L) {
   S.splitk = c.splitk > 1 ? c.splitk : 1;
   S.slice_chunks = (S.nkc + S.splitk - 1) / S.splitk;
   S.partial = c.splitk > 1 ? reinterpret_cast<float*>(ws + L.partial_off) : nullptr;
+  S.pair = 0;
   return S;
 }
 
@@ -236,8 +237,19 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   if (e != cudaSuccess || items == 0) return e;
   const int grid = (int)(items < sms ? items : sms);
   const bool timed = c.gemm_begin && c.gemm_end;
+  // Pair tiles (clusters of two CTAs, 256 x 256 tiles) for the widest tiles
+  // of calls with two-part panels, no k slices and at least two tile rows.
+  const int64_t pair_items = (tm + 1) / 2 * tn * c.batch;
+  const int pair_cap = (!c.pack_only && c.bn == 256 && splitk == 1 && S.parts == 1 && tm >= 2)
+                           ? gemm_pair_capacity<SingleSched>() : 0;
   if (timed && (e = cudaEventRecord(c.gemm_begin, s)) != cudaSuccess) return e;
-  e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, ptasks > 0 && !timed);
+  if (pair_cap > 0) {
+    S.pair = 1;
+    const int pairs = (int)(pair_items < pair_cap ? pair_items : pair_cap);
+    e = launch_gemm_kernel_pair<SingleSched>(S, pairs, c.status, s, ptasks > 0 && !timed);
+  } else {
+    e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, ptasks > 0 && !timed);
+  }
   if (e != cudaSuccess) return e;
   if (timed && (e = cudaEventRecord(c.gemm_end, s)) != cudaSuccess) return e;
   e = cudaGetLastError();
