@@ -180,11 +180,12 @@ struct SingleSched {
   // of slice s, tile (tm, tn) at partial + ((s * tiles_m + tm) * tiles_n + tn) * 128 * bn
   int splitk, slice_chunks;
   float* partial;
-  // pair tiles (clusters of two CTAs, bn = 256, no split-K): item t is a
-  // 256 x 256 tile, tile rows 2 tm2 and 2 tm2 + 1 of pair row tm2
+  // pair tiles (clusters of two CTAs, bn = 256, two-part panels): item t is
+  // a 256 x 256 tile (with split-K: one k slice of it), tile rows 2 tm2 and
+  // 2 tm2 + 1 of pair row tm2
   int pair;
   __device__ __forceinline__ int num_items() const {
-    return pair ? ((tiles_m + 1) >> 1) * tiles_n * batch : tiles_m * tiles_n * batch * splitk;
+    return (pair ? ((tiles_m + 1) >> 1) : tiles_m) * tiles_n * batch * splitk;
   }
   __device__ __forceinline__ TileJob job(int t) const {
     const int per = tiles_m * tiles_n;
@@ -195,19 +196,22 @@ struct SingleSched {
     tile_coords(t - z * per, tiles_m, tiles_n, raster, tm, tn);
     return tile_job(z, tm, tn, sl, (int64_t)tn * bn);
   }
-  // The half of pair tile t that CTA `rank` of the pair computes: tile row
+  // The half of pair item t that CTA `rank` of the pair computes: tile row
   // 2 tm2 + rank (the A panel has an even number of row blocks, so the odd
-  // row of a last, half-empty pair reads zero rows), and B rows
-  // [n0 + 128 rank, n0 + 128 rank + 128) for its share of the B operand.
-  // Pair rows go in groups of raster / 2, the same rows of C as the
-  // single-CTA groups of `raster` tile rows.
+  // row of a last, half-empty pair reads zero rows; its epilogue stores
+  // nothing), B rows [n0 + 128 rank, n0 + 128 rank + 128) for its share of
+  // the B operand, and the item's k slice.  Pair rows go in groups of
+  // raster / 2, the same rows of C as the single-CTA groups of `raster` tile
+  // rows.
   __device__ __forceinline__ TileJob job_pair(int t, int rank) const {
     const int tiles_m2 = (tiles_m + 1) >> 1;
     const int per = tiles_m2 * tiles_n;
+    const int sl = t % splitk;
+    t /= splitk;
     const int z = t / per;
     int tm2, tn;
     tile_coords(t - z * per, tiles_m2, tiles_n, raster > 1 ? raster >> 1 : 1, tm2, tn);
-    return tile_job(z, 2 * tm2 + rank, tn, 0, (int64_t)tn * bn + 128 * rank);
+    return tile_job(z, 2 * tm2 + rank, tn, sl, (int64_t)tn * bn + 128 * rank);
   }
   __device__ __forceinline__ TileJob tile_job(int z, int tm, int tn, int sl, int64_t b_row0) const {
     const int kc0 = sl * slice_chunks;
@@ -801,8 +805,10 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
       constexpr int EC = 32;
       const int cols = (J.bn / (kEpiWarps / 4)) > 32 ? J.bn / (kEpiWarps / 4) : 32;
       const int c_begin = part * cols, c_end = (c_begin + cols < J.bn) ? c_begin + cols : J.bn;
-      if (J.partial) {
-        // split-K slice: the raw accumulator, whole tile, 32 consecutive rows per warp store
+      if (J.partial && J.m0 < J.m) {
+        // split-K slice: the raw accumulator, whole tile, 32 consecutive rows
+        // per warp store (not for the empty odd half of a last pair, which
+        // has no partial tile)
         float* pp = J.partial + q * 32 + lane;
         for (int c0 = c_begin; c0 < c_end; c0 += EC) {
           uint32_t r[EC];

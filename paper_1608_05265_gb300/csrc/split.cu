@@ -238,9 +238,9 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   const int grid = (int)(items < sms ? items : sms);
   const bool timed = c.gemm_begin && c.gemm_end;
   // Pair tiles (clusters of two CTAs, 256 x 256 tiles) for the widest tiles
-  // of calls with two-part panels, no k slices and at least two tile rows.
-  const int64_t pair_items = (tm + 1) / 2 * tn * c.batch;
-  const int pair_cap = (!c.pack_only && c.bn == 256 && splitk == 1 && S.parts == 1 && tm >= 2)
+  // of calls with two-part panels and at least two tile rows.
+  const int64_t pair_items = (tm + 1) / 2 * tn * c.batch * splitk;
+  const int pair_cap = (!c.pack_only && c.bn == 256 && S.parts == 1 && tm >= 2)
                            ? gemm_pair_capacity<SingleSched>() : 0;
   if (timed && (e = cudaEventRecord(c.gemm_begin, s)) != cudaSuccess) return e;
   if (pair_cap > 0) {

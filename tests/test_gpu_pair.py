@@ -5,7 +5,8 @@ with two-part panels (k >= 512), no k slices and at least two tile rows.
 The schedule is pinned to BN 256 without k slicing so that small ragged
 shapes take pair tiles too: an odd number of tile rows (the last pair's
 second half lies past m), ragged tile columns, every transpose, badly scaled
-rows and columns on either CTA of a pair, beta = 0 and a strided batch.
+rows and columns on either CTA of a pair, beta = 0, k slices and a strided
+batch.
 Each is checked against the FP64 oracle under the componentwise bound."""
 
 import numpy as np
@@ -53,6 +54,24 @@ def test_pair_tiles_transposes(h, ta, tb):
     m, n, k = 520, 600, 768
     A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 96, ta, tb, m, n, k, pad=5)
     assert check_full(h, SPLIT, ta, tb, m, n, k, -0.75, A, lda, B, ldb, 2.0, C, ldc, nthreads=4) <= 1.0
+
+
+@pytest.mark.parametrize("m,n,k", [(300, 260, 4096), (129, 300, 8192), (640, 512, 2048)])
+def test_pair_tiles_k_sliced(h, m, n, k):
+    """Pair items that are k slices of a 256 x 256 tile (split-K at full fill,
+    BN 256): each CTA stores its own 128-row partial tile (none for the empty
+    odd half of a last pair) and the reduction sums the slices."""
+    from paper_1608_05265_gb300 import gbgemm, predictor
+    s = 3 + 12 * 2 + 4 * 2 + 3
+    assert gbgemm.schedule_info(s)["level"] == 3
+    A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 94, "T", "N", m, n, k, pad=2)
+    assert h.schedule_legal(predictor.tuning_problem(("T", "N", m, n, k, 1, 1, 1)), s)
+    h.set_schedule(s)
+    try:
+        assert check_full(h, SPLIT, "T", "N", m, n, k, 1.5, A, lda, B, ldb, -0.25, C, ldc, nthreads=4) <= 1.0
+        assert h.last_schedule() == s
+    finally:
+        h.set_schedule(PAIR_SCHEDULE)
 
 
 def test_pair_tiles_badly_scaled_and_beta_zero(h):
