@@ -41,7 +41,7 @@ METRIC = "sgemm TFLOP/s at 8192^3: 3xBF16 tensor vs FP32 SIMT, same GPU, same er
 # DRAM bytes (read + write) of one split_gemm_kernel launch at 8192^3 NN, ld 8200,
 # from one ncu capture of the current kernel (profiles/split_gemm_8192_nn_traffic.md);
 # None until that capture has been taken of this kernel.
-GEMM_TRAFFIC_8192 = 2562395392 + 258318336
+GEMM_TRAFFIC_8192 = None
 UNIT = "TFLOP/s"
 N = 8192
 LD = N + 8
@@ -341,7 +341,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flop / (gemm_avg_ms * 1e-3) / 1e12
     peak = bf16_peak / 3.0
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": GEMM_TRAFFIC_8192, "kernel": "split_gemm_kernel<256>",
+                "traffic": GEMM_TRAFFIC_8192, "kernel": "split_gemm_kernel<SingleSched, 6, 256, pair>",
                 "note": (f"sgemm-equivalent 2mnk per launch / launch time; peak = {peak_src} bf16 dense "
                          f"{bf16_peak:.1f} TFLOP/s / 3 products (sustained {bf16_sust:.1f}/3 = "
                          f"{bf16_sust / 3:.1f}: frac {achieved / (bf16_sust / 3) if bf16_sust else float('nan'):.3f})"),
