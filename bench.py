@@ -41,7 +41,7 @@ METRIC = "sgemm TFLOP/s at 8192^3: 3xBF16 tensor vs FP32 SIMT, same GPU, same er
 # DRAM bytes (read + write) of one split_gemm_kernel launch at 8192^3 NN, ld 8200,
 # from one ncu capture of the current kernel (profiles/split_gemm_8192_nn_traffic.md);
 # None until that capture has been taken of this kernel.
-GEMM_TRAFFIC_8192 = None
+GEMM_TRAFFIC_8192 = 2810343936 + 257446656
 UNIT = "TFLOP/s"
 N = 8192
 LD = N + 8
