@@ -198,9 +198,10 @@ struct SingleSched {
   }
   // The half of pair item t that CTA `rank` of the pair computes: tile row
   // 2 tm2 + rank (the A panel has an even number of row blocks, so the odd
-  // row of a last, half-empty pair reads zero rows; its epilogue stores
-  // nothing), B rows [n0 + 128 rank, n0 + 128 rank + 128) for its share of
-  // the B operand, and the item's k slice.  Pair rows go in groups of
+  // row of a last, half-empty pair reads the panel's padding block, which is
+  // never written; its rows lie past m and its epilogue stores nothing),
+  // B rows [n0 + 128 rank, n0 + 128 rank + 128) for its share of the B
+  // operand, and the item's k slice.  Pair rows go in groups of
   // raster / 2, the same rows of C as the single-CTA groups of `raster` tile
   // rows.
   __device__ __forceinline__ TileJob job_pair(int t, int rank) const {
