@@ -180,9 +180,9 @@ struct SingleSched {
   // of slice s, tile (tm, tn) at partial + ((s * tiles_m + tm) * tiles_n + tn) * 128 * bn
   int splitk, slice_chunks;
   float* partial;
-  // pair tiles (clusters of two CTAs, bn = 256, two-part panels): item t is
-  // a 256 x 256 tile (with split-K: one k slice of it), tile rows 2 tm2 and
-  // 2 tm2 + 1 of pair row tm2
+  // pair tiles (clusters of two CTAs, bn = 256): item t is a 256 x 256 tile
+  // (with split-K: one k slice of it), tile rows 2 tm2 and 2 tm2 + 1 of pair
+  // row tm2
   int pair;
   __device__ __forceinline__ int num_items() const {
     return (pair ? ((tiles_m + 1) >> 1) : tiles_m) * tiles_n * batch * splitk;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256, 4) pack_tasks_kernel(const Sched S) {
 // both CTAs' "empty" and "accumulator full" barriers.  Pairs take items in a
 // fixed order (cluster c: items c, c + clusters, ...), so both CTAs of a
 // pair walk the same tiles without exchanging indices.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, bool PAIR = false>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, bool PAIR = false, bool THREE = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
   constexpr uint32_t A_BYTES = kBlockBytes;        // 128 rows x 128 B
@@ -654,14 +654,31 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
         if (++tq == kTileQ) { tq = 0; tqph ^= 1u; }
         if (t < 0) break;
         const TileJob J = job_of(t);
-        for (int kc = 0; kc < J.nkc; ++kc) {
-          if (!wait_bar(full_bar(stage), phase)) {
-            raise_status(status, abort_flag);
-            ok = false;
-            break;
+        if constexpr (THREE) {
+          // every slot in the producer's fill order: one per k chunk and the
+          // [lo3 | lo3] slot after each even chunk
+          for (int kc = 0; kc < J.nkc && ok; ++kc) {
+            const int nparts = (J.parts == 2 && (kc & 1) == 0) ? 2 : 1;
+            for (int part = 0; part < nparts; ++part) {
+              if (!wait_bar(full_bar(stage), phase)) {
+                raise_status(status, abort_flag);
+                ok = false;
+                break;
+              }
+              mbar_arrive_remote(map_to_rank(full_bar(stage), 0u));
+              if (++stage == kStages) { stage = 0; phase ^= 1u; }
+            }
           }
-          mbar_arrive_remote(map_to_rank(full_bar(stage), 0u));
-          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        } else {
+          for (int kc = 0; kc < J.nkc; ++kc) {
+            if (!wait_bar(full_bar(stage), phase)) {
+              raise_status(status, abort_flag);
+              ok = false;
+              break;
+            }
+            mbar_arrive_remote(map_to_rank(full_bar(stage), 0u));
+            if (++stage == kStages) { stage = 0; phase ^= 1u; }
+          }
         }
       }
     }
@@ -725,10 +742,17 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
             const uint64_t bh = make_desc_sw128(b_addr + 32u * kk);
             const uint64_t bl = make_desc_sw128(b_addr + 64u + 32u * kk);
             if constexpr (PAIR) {
-              // pair tiles have two-part panels (k >= 512)
               mma_bf16_pair(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               mma_bf16_pair(d_tmem, ah, bl, idesc, 1u);
               mma_bf16_pair(d_tmem, al, bh, idesc, 1u);
+              if constexpr (THREE) {
+                // with three parts: hi*lo3 + mid*mid + lo3*hi (al, bl above are mid)
+                const uint64_t a3 = make_desc_sw128(a3_addr + 32u * kk);
+                const uint64_t b3 = make_desc_sw128(b3_addr + 32u * kk);
+                mma_bf16_pair(d_tmem, ah, b3, idesc, 1u);
+                mma_bf16_pair(d_tmem, al, bl, idesc, 1u);
+                mma_bf16_pair(d_tmem, a3, bh, idesc, 1u);
+              }
             } else {
               mma_bf16(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               mma_bf16(d_tmem, ah, bl, idesc, 1u);
@@ -745,6 +769,9 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
           }
           if constexpr (PAIR) {
             mma_commit_pair(empty_bar(s0), 0x3);  // frees the slot in both CTAs once these MMAs have read it
+            if constexpr (THREE) {
+              if ((kc & 1) == 1 || kc == J.nkc - 1) mma_commit_pair(empty_bar(s1), 0x3);
+            }
           } else {
             mma_commit(empty_bar(s0));  // frees the slot once these MMAs have read it
             if (J.parts == 2 && ((kc & 1) == 1 || kc == J.nkc - 1)) mma_commit(empty_bar(s1));
@@ -928,14 +955,14 @@ split_gemm_kernel(const Sched S, int* status, uint64_t timeout_ns) {
 
 // The shared-memory opt-in is a per-device function attribute: set it once
 // for every device a kernel instance is launched on.
-template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, bool PAIR = false>
+template <class Sched, int STAGES = kStages, int MAXBN = kMaxBN, bool PAIR = false, bool THREE = false>
 cudaError_t ensure_gemm_smem_attr() {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(split_gemm_kernel<Sched, STAGES, MAXBN, PAIR, THREE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              gemm_smem_bytes<STAGES, MAXBN, PAIR>());
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
@@ -963,10 +990,11 @@ cudaError_t launch_gemm_kernel(const Sched& S, int grid, int* status, cudaStream
   return cudaLaunchKernelEx(&cfg, split_gemm_kernel<Sched, STAGES, MAXBN>, S, status, (uint64_t)kTimeoutNs);
 }
 
-// The pair-tile instance: clusters of two CTAs.  How many pairs the GPU
-// holds at once (one CTA per SM; a pair needs two SMs of one cluster-capable
-// group) is asked once per device; 0 when clusters of two cannot run.
-template <class Sched>
+// The pair-tile instances: clusters of two CTAs, THREE for three-part panels
+// (k < 512).  How many pairs the GPU holds at once (one CTA per SM; a pair
+// needs two SMs of one cluster-capable group) is asked once per device and
+// instance; 0 when clusters of two cannot run.
+template <class Sched, bool THREE = false>
 int gemm_pair_capacity() {
   static int cap[64];
   static bool known[64] = {};
@@ -974,7 +1002,7 @@ int gemm_pair_capacity() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (!known[dev]) {
     int n = 0;
-    if (ensure_gemm_smem_attr<Sched, kPairStages, kMaxBN, true>() == cudaSuccess) {
+    if (ensure_gemm_smem_attr<Sched, kPairStages, kMaxBN, true, THREE>() == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(2);
       cfg.blockDim = dim3(kGemmThreads);
@@ -986,7 +1014,8 @@ int gemm_pair_capacity() {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<Sched, kPairStages, kMaxBN, true>, &cfg) != cudaSuccess)
+      if (cudaOccupancyMaxActiveClusters(&n, split_gemm_kernel<Sched, kPairStages, kMaxBN, true, THREE>, &cfg) !=
+          cudaSuccess)
         n = 0;
     }
     (void)cudaGetLastError();  // a failed query leaves the pair instance unused, not an error
@@ -996,10 +1025,10 @@ int gemm_pair_capacity() {
   return cap[dev];
 }
 
-// Launch `pairs` clusters of two CTAs of the pair-tile instance (S.pair set).
-template <class Sched>
+// Launch `pairs` clusters of two CTAs of a pair-tile instance (S.pair set).
+template <class Sched, bool THREE = false>
 cudaError_t launch_gemm_kernel_pair(const Sched& S, int pairs, int* status, cudaStream_t s, bool dependent) {
-  cudaError_t e = ensure_gemm_smem_attr<Sched, kPairStages, kMaxBN, true>();
+  cudaError_t e = ensure_gemm_smem_attr<Sched, kPairStages, kMaxBN, true, THREE>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * pairs));
@@ -1015,7 +1044,7 @@ cudaError_t launch_gemm_kernel_pair(const Sched& S, int pairs, int* status, cuda
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = dependent ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<Sched, kPairStages, kMaxBN, true>, S, status,
+  return cudaLaunchKernelEx(&cfg, split_gemm_kernel<Sched, kPairStages, kMaxBN, true, THREE>, S, status,
                             (uint64_t)kTimeoutNs);
 }
 

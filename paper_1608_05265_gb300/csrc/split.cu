@@ -238,15 +238,20 @@ cudaError_t launch_split_call(const SplitCall& c, cudaStream_t s) {
   const int grid = (int)(items < sms ? items : sms);
   const bool timed = c.gemm_begin && c.gemm_end;
   // Pair tiles (clusters of two CTAs, 256 x 256 tiles) for the widest tiles
-  // of calls with two-part panels and at least two tile rows.
+  // of calls with at least two tile rows; with three-part panels (k < 512)
+  // only from 8 k chunks: below that a tile's MMAs take less time than its
+  // epilogue, and pairing two CTAs' epilogues (and the fixed tile order) cost
+  // more than the halved operand loads gain (k = 128: 21% slower at 16384^2).
   const int64_t pair_items = (tm + 1) / 2 * tn * c.batch * splitk;
-  const int pair_cap = (!c.pack_only && c.bn == 256 && S.parts == 1 && tm >= 2)
-                           ? gemm_pair_capacity<SingleSched>() : 0;
+  const bool pair_ok = !c.pack_only && c.bn == 256 && tm >= 2 && (S.parts == 1 || S.nkc >= 8);
+  const int pair_cap = !pair_ok ? 0
+                       : S.parts == 2 ? gemm_pair_capacity<SingleSched, true>() : gemm_pair_capacity<SingleSched>();
   if (timed && (e = cudaEventRecord(c.gemm_begin, s)) != cudaSuccess) return e;
   if (pair_cap > 0) {
     S.pair = 1;
     const int pairs = (int)(pair_items < pair_cap ? pair_items : pair_cap);
-    e = launch_gemm_kernel_pair<SingleSched>(S, pairs, c.status, s, ptasks > 0 && !timed);
+    e = S.parts == 2 ? launch_gemm_kernel_pair<SingleSched, true>(S, pairs, c.status, s, ptasks > 0 && !timed)
+                     : launch_gemm_kernel_pair<SingleSched>(S, pairs, c.status, s, ptasks > 0 && !timed);
   } else {
     e = launch_gemm_kernel<SingleSched>(S, grid, c.status, s, ptasks > 0 && !timed);
   }

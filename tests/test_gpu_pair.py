@@ -1,7 +1,8 @@
 """Pair tiles on the split path: clusters of two CTAs that compute 256 x 256
 tiles with tcgen05 MMAs of cta_group::2 (each CTA loads its own 128-row A
 block and half of the tile's B rows).  Calls take them for the widest tiles
-with two-part panels (k >= 512), no k slices and at least two tile rows.
+(256 columns) with at least two tile rows: with two-part panels (k >= 512),
+with or without k slices, and with three-part panels from 8 k chunks.
 The schedule is pinned to BN 256 without k slicing so that small ragged
 shapes take pair tiles too: an odd number of tile rows (the last pair's
 second half lies past m), ragged tile columns, every transpose, badly scaled
@@ -43,6 +44,8 @@ def h():
     (129, 513, 1024, 0),    # one pair, one row in its odd half; 1-column last tile
     (1000, 777, 555, 8),    # 8 tile rows, 4 pairs, k not a multiple of 32
     (640, 1030, 2048, 1),   # 5 tile rows, 5 tile columns
+    (300, 700, 300, 3),     # three-part panels (k < 512): six products per k step
+    (129, 513, 260, 0),     # three-part, k not a multiple of 32, one pair
 ])
 def test_pair_tiles_ragged(h, m, n, k, pad):
     A, lda, B, ldb, C, ldc = synth.gemm_problem("uniform", 95, "N", "N", m, n, k, pad=pad)
@@ -82,6 +85,16 @@ def test_pair_tiles_badly_scaled_and_beta_zero(h):
     Bt = synth.normal_rowscaled_matrix(97, 2, n, k, n, elo=-60, ehi=60)  # op(B) = Bt^T: columns scaled
     C = np.full(m * n, np.nan, dtype=np.float32)  # beta = 0: NaNs in C must not reach the result
     assert check_full(h, SPLIT, "N", "T", m, n, k, 1.0, A, m, Bt, n, 0.0, C, m, nthreads=4) <= 1.0
+
+
+def test_pair_tiles_three_part_badly_scaled(h):
+    """k < 512 (three-part panels, the compact lo3 slots relayed as well) with
+    rows of op(A) and columns of op(B) scaled by 2^+-60."""
+    m, n, k = 384, 512, 300
+    A = synth.normal_rowscaled_matrix(93, 0, m, k, m, elo=-60, ehi=60)
+    Bt = synth.normal_rowscaled_matrix(93, 2, n, k, n, elo=-60, ehi=60)
+    C = synth.uniform_matrix(93, 4, m, n, m)
+    assert check_full(h, SPLIT, "N", "T", m, n, k, 1.0, A, m, Bt, n, 0.5, C, m, nthreads=4) <= 1.0
 
 
 def test_pair_tiles_strided_batch(h):
